@@ -1,0 +1,154 @@
+"""FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never calls it, and shares no code with it.
+
+The C source (``oracle.c``) is compiled on first use with
+``gcc -O2 -ffp-contract=off`` so that every FP64 operation is individually
+rounded in the order written.  This module only marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` next to the source if missing or stale."""
+    stale = (not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Beam(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [
+        (k, ctypes.POINTER(ctypes.c_double)) for k in ("px", "py", "pz", "dx", "dy", "dz", "E", "w")
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("weighted", ctypes.c_double),
+                ("hsum", ctypes.c_uint64), ("hxor", ctypes.c_uint64),
+                ("tests", ctypes.c_int64), ("node_tests", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            d = ctypes.c_double
+            L.oracle_ln.argtypes = [d]
+            L.oracle_ln.restype = d
+            L.oracle_sigma.argtypes = [d]
+            L.oracle_sigma.restype = d
+            L.oracle_s.argtypes = [d, d, d]
+            L.oracle_s.restype = d
+            L.oracle_sigma_max.argtypes = []
+            L.oracle_sigma_max.restype = d
+            L.oracle_splitmix64.argtypes = [ctypes.c_uint64]
+            L.oracle_splitmix64.restype = ctypes.c_uint64
+            pb = ctypes.POINTER(Beam)
+            L.oracle_pair_hit.argtypes = [pb, ctypes.c_int64, pb, ctypes.c_int64, ctypes.c_int64, d, d]
+            L.oracle_pair_hit.restype = ctypes.c_int
+            L.oracle_pair_detail.argtypes = [pb, ctypes.c_int64, pb, ctypes.c_int64, ctypes.c_int64,
+                                             d, d, ctypes.POINTER(ctypes.c_double)]
+            L.oracle_pair_detail.restype = ctypes.c_int
+            pu = ctypes.POINTER(ctypes.c_uint32)
+            pr = ctypes.POINTER(Result)
+            L.oracle_bruteforce.argtypes = [pb, pb, ctypes.c_int64, d, d, pu, ctypes.c_int64, pr]
+            L.oracle_bruteforce.restype = ctypes.c_int
+            L.oracle_tree.argtypes = [pb, pb, ctypes.c_int64, d, d, ctypes.c_int, ctypes.c_int, pu,
+                                      ctypes.c_int64, pr]
+            L.oracle_tree.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def ln(x: float) -> float:
+    return lib().oracle_ln(float(x))
+
+
+def sigma(s: float) -> float:
+    """Eq. BWcross [m^2]."""
+    return lib().oracle_sigma(float(s))
+
+
+def s_invariant(E1: float, E2: float, cos_phi: float) -> float:
+    return lib().oracle_s(float(E1), float(E2), float(cos_phi))
+
+
+def sigma_max() -> float:
+    return lib().oracle_sigma_max()
+
+
+def splitmix64(x: int) -> int:
+    return lib().oracle_splitmix64(ctypes.c_uint64(x & 0xFFFFFFFFFFFFFFFF))
+
+
+_KEYS = ("px", "py", "pz", "dx", "dy", "dz", "E", "w")
+
+
+def _beam(b: dict) -> tuple[Beam, list]:
+    keep = [np.ascontiguousarray(b[k], dtype=np.float64) for k in _KEYS]
+    n = len(keep[0])
+    for a in keep:
+        assert a.shape == (n,)
+    ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in keep]
+    return Beam(n, *ptrs), keep
+
+
+def pair_detail(a: dict, i: int, b: dict, j: int, step: int, dt: float, kappa: float):
+    """(hit, s, sigma, r2, tstar, d2, vv) for one pair."""
+    A, ka = _beam(a)
+    B, kb = _beam(b)
+    out = (ctypes.c_double * 6)()
+    hit = lib().oracle_pair_detail(ctypes.byref(A), i, ctypes.byref(B), j, step, dt, kappa, out)
+    return (bool(hit),) + tuple(out)
+
+
+def _run(fn, a, b, step, dt, kappa, extra, cap):
+    A, ka = _beam(a)
+    B, kb = _beam(b)
+    res = Result()
+    for _ in range(3):
+        hits = np.zeros((max(cap, 1), 2), dtype=np.uint32)
+        rc = fn(ctypes.byref(A), ctypes.byref(B), int(step), float(dt), float(kappa), *extra,
+                hits.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), cap, ctypes.byref(res))
+        if rc != 0:
+            raise RuntimeError(f"oracle failed rc={rc}")
+        if res.count <= cap:
+            return hits[: res.count].copy(), res.as_dict()
+        cap = int(res.count)
+    raise RuntimeError("oracle capacity loop")
+
+
+def bruteforce(a: dict, b: dict, step: int, dt: float, kappa: float, cap: int = 1 << 16):
+    """All N_A x N_B pairs.  Returns (hits[n,2] uint32 lexicographic, result dict)."""
+    return _run(lib().oracle_bruteforce, a, b, step, dt, kappa, (), cap)
+
+
+def tree(a: dict, b: dict, step: int, dt: float, kappa: float, leaf_size: int = 8,
+         nthreads: int = 1, cap: int = 1 << 16):
+    """The paper's k-d hierarchy with depth-first dual traversal; same output."""
+    return _run(lib().oracle_tree, a, b, step, dt, kappa, (int(leaf_size), int(nthreads)), cap)

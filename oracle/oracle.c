@@ -1,0 +1,526 @@
+/*
+ * oracle.c -- FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see oracle.h).
+ *
+ * Plain definitions, slow on purpose, no blocking or fusion beyond what the
+ * definition states.  Build with:  gcc -O2 -ffp-contract=off -fPIC -shared
+ * (contraction off so that every a*b+c is two rounded operations, on x86-64
+ * and on aarch64 alike).
+ *
+ * What is computed, and where the paper defines it:
+ *   - sigma(s): Eq. BWcross (Sec. 1), with beta = sqrt(1 - 1/s).  Evaluated
+ *     in the algebraically equal form
+ *        (pi/2) r_e^2 (1/s) [ (3 - b^4) ln((1+b)^2 s) - 2 b (2 - b^2) ],
+ *     using (1+b)/(1-b) = (1+b)^2 / (1-b^2) = (1+b)^2 s, which avoids the
+ *     1 - b cancellation near b -> 1.
+ *   - s and the threshold s > 1: the definition below Eq. BWcross and
+ *     Eq. eq.Cond (Sec. 1); sigma is zero at and below threshold.
+ *   - the collision criterion (reading of the method stated in the design
+ *     notes): time-synchronous closest approach of the two straight-line
+ *     photons within the step, t* in [0, dt), hit iff d^2 < r^2 with
+ *     r^2 = kappa sigma / pi (sigma in m^2 -> r in um via 1e12).
+ *   - the hierarchy: the k-d tree of Sec. 2.1 (binary, each cut balances the
+ *     particle counts, the cut axis cycles x, y, z), over boxes that include
+ *     the distance travelled in the step (Sec. 2.1), tested pairwise with the
+ *     axis-aligned overlap test Eq. CollDet, traversed depth first (Sec. 2.2).
+ *     The tree only prunes; its hit set must equal brute force.
+ *   - yield: weights multiply (Sec. 2.2, rate proportional to n_I n_II).
+ *   - checksum: splitmix64 (Steele, Lea, Flood 2014; Vigna's published
+ *     constants) of the packed pair, summed mod 2^64 and xor-ed.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018; c exact */
+#define O_C 0.299792458              /* um / fs */
+#define O_RE 2.8179403262e-15        /* classical electron radius [m] */
+#define O_MEC2 0.51099895000         /* electron rest energy [MeV] */
+#define O_PI 3.14159265358979323846
+
+/* ln 2 split: the high part has 32 significant bits so e * hi is exact */
+#define O_LN2_HI 0.6931471803691238
+#define O_LN2_LO 1.9082149292705877e-10
+#define O_SQRT_HALF 0.70710678118654752440
+
+double oracle_ln(double x) {
+  if (x != x || x < 0.0) return NAN;
+  if (x == 0.0) return -INFINITY;
+  if (isinf(x)) return x;
+  int e;
+  double m = frexp(x, &e); /* x = m 2^e, m in [1/2, 1), exact */
+  if (m < O_SQRT_HALF) {
+    m = m * 2.0;
+    e = e - 1;
+  }
+  /* m in [sqrt(1/2), sqrt(2)); f in (-0.1716, 0.1716) */
+  double f = (m - 1.0) / (m + 1.0);
+  double z = f * f;
+  /* ln m = 2 atanh f = 2 f sum_k z^k / (2k + 1), k = 0..11; the first
+   * omitted term is below 2^-60 relative */
+  double p = 1.0 / 23.0;
+  p = p * z + 1.0 / 21.0;
+  p = p * z + 1.0 / 19.0;
+  p = p * z + 1.0 / 17.0;
+  p = p * z + 1.0 / 15.0;
+  p = p * z + 1.0 / 13.0;
+  p = p * z + 1.0 / 11.0;
+  p = p * z + 1.0 / 9.0;
+  p = p * z + 1.0 / 7.0;
+  p = p * z + 1.0 / 5.0;
+  p = p * z + 1.0 / 3.0;
+  p = p * z + 1.0;
+  double lnm = (2.0 * f) * p;
+  double de = (double)e;
+  return de * O_LN2_HI + (de * O_LN2_LO + lnm);
+}
+
+double oracle_sigma(double s) {
+  if (!(s > 1.0)) return 0.0; /* threshold, Eq. eq.Cond */
+  double inv = 1.0 / s;       /* = 1 - beta^2 */
+  double b = sqrt((s - 1.0) / s);
+  double b2 = b * b;
+  double opb = 1.0 + b;
+  double lg = oracle_ln((opb * opb) * s); /* ln((1+b)/(1-b)) */
+  double br = (3.0 - b2 * b2) * lg - (2.0 * b) * (2.0 - b2);
+  double pref = ((0.5 * O_PI) * O_RE) * O_RE;
+  return (pref * inv) * br;
+}
+
+double oracle_s(double E1, double E2, double cos_phi) {
+  return ((E1 * E2) * (1.0 - cos_phi)) / ((2.0 * O_MEC2) * O_MEC2);
+}
+
+double oracle_sigma_max(void) {
+  /* golden-section search for the single maximum, which lies in (1.2, 4) */
+  double lo = 1.2, hi = 4.0, g = 0.5 * (sqrt(5.0) - 1.0);
+  double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+  double f1 = oracle_sigma(x1), f2 = oracle_sigma(x2);
+  for (int it = 0; it < 200; ++it) {
+    if (f1 < f2) {
+      lo = x1; x1 = x2; f1 = f2;
+      x2 = lo + g * (hi - lo); f2 = oracle_sigma(x2);
+    } else {
+      hi = x2; x2 = x1; f2 = f1;
+      x1 = hi - g * (hi - lo); f1 = oracle_sigma(x1);
+    }
+  }
+  return f1 > f2 ? f1 : f2;
+}
+
+uint64_t oracle_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/* ---- the per-pair definition ------------------------------------------ */
+
+/* position at t = step * dt, closed form p0 + (c t) d */
+static inline void pos_at(const oracle_beam *bm, int64_t i, double ct, double P[3]) {
+  P[0] = bm->px[i] + ct * bm->dx[i];
+  P[1] = bm->py[i] + ct * bm->dy[i];
+  P[2] = bm->pz[i] + ct * bm->dz[i];
+}
+
+/* out (optional): s, sigma, r2, tstar, d2, vv */
+static int decide(const double Pi[3], const double di[3], double Ei, const double Pj[3],
+                  const double dj[3], double Ej, double dt, double kappa, double *out) {
+  double cs = di[0] * dj[0] + di[1] * dj[1] + di[2] * dj[2];
+  double s = oracle_s(Ei, Ej, cs);
+  if (out) { out[0] = s; out[1] = 0.0; out[2] = 0.0; out[3] = NAN; out[4] = NAN; out[5] = NAN; }
+  if (!(s > 1.0)) return 0;
+  double vx = O_C * (di[0] - dj[0]);
+  double vy = O_C * (di[1] - dj[1]);
+  double vz = O_C * (di[2] - dj[2]);
+  double vv = vx * vx + vy * vy + vz * vz;
+  if (out) out[5] = vv;
+  if (vv == 0.0) return 0;
+  double px = Pi[0] - Pj[0], py = Pi[1] - Pj[1], pz = Pi[2] - Pj[2];
+  double pv = px * vx + py * vy + pz * vz;
+  double ts = -pv / vv;
+  if (out) out[3] = ts;
+  else if (!(ts >= 0.0) || !(ts < dt)) return 0; /* same predicate, decided early */
+  double qx = px + ts * vx, qy = py + ts * vy, qz = pz + ts * vz;
+  double d2 = qx * qx + qy * qy + qz * qz;
+  double sg = oracle_sigma(s);
+  double r2 = ((1e12 * kappa) * sg) / O_PI;
+  if (out) { out[1] = sg; out[2] = r2; out[4] = d2; }
+  if (!(ts >= 0.0) || !(ts < dt)) return 0; /* half-open window [0, dt) */
+  return d2 < r2;
+}
+
+int oracle_pair_detail(const oracle_beam *a, int64_t i, const oracle_beam *b, int64_t j,
+                       int64_t step, double dt, double kappa, double out[6]) {
+  double ct = O_C * ((double)step * dt);
+  double Pi[3], Pj[3];
+  pos_at(a, i, ct, Pi);
+  pos_at(b, j, ct, Pj);
+  double di[3] = {a->dx[i], a->dy[i], a->dz[i]};
+  double dj[3] = {b->dx[j], b->dy[j], b->dz[j]};
+  return decide(Pi, di, a->E[i], Pj, dj, b->E[j], dt, kappa, out);
+}
+
+int oracle_pair_hit(const oracle_beam *a, int64_t i, const oracle_beam *b, int64_t j,
+                    int64_t step, double dt, double kappa) {
+  return oracle_pair_detail(a, i, b, j, step, dt, kappa, NULL);
+}
+
+/* ---- result accumulation ---------------------------------------------- */
+
+typedef struct {
+  uint64_t *key;
+  int64_t n, cap;
+  int64_t tests, node_tests;
+} hitvec;
+
+static int hv_push(hitvec *h, uint64_t k) {
+  if (h->n == h->cap) {
+    int64_t nc = h->cap ? 2 * h->cap : 1024;
+    uint64_t *p = (uint64_t *)realloc(h->key, (size_t)nc * sizeof(uint64_t));
+    if (!p) return -1;
+    h->key = p;
+    h->cap = nc;
+  }
+  h->key[h->n++] = k;
+  return 0;
+}
+
+static int cmp_u64(const void *x, const void *y) {
+  uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+  return a < b ? -1 : (a > b);
+}
+
+/* sort, write (i, j) pairs up to cap, fill the result in lexicographic order */
+static void finish(hitvec *h, const oracle_beam *a, const oracle_beam *b, uint32_t *hits,
+                   int64_t cap, oracle_result *res) {
+  qsort(h->key, (size_t)h->n, sizeof(uint64_t), cmp_u64);
+  res->count = h->n;
+  res->weighted = 0.0;
+  res->hsum = 0;
+  res->hxor = 0;
+  for (int64_t k = 0; k < h->n; ++k) {
+    uint64_t key = h->key[k];
+    uint32_t i = (uint32_t)(key >> 32), j = (uint32_t)(key & 0xffffffffu);
+    double wi = a->w ? a->w[i] : 1.0, wj = b->w ? b->w[j] : 1.0;
+    res->weighted += wi * wj;
+    uint64_t hm = oracle_splitmix64(key);
+    res->hsum += hm;
+    res->hxor ^= hm;
+    if (hits && k < cap) {
+      hits[2 * k] = i;
+      hits[2 * k + 1] = j;
+    }
+  }
+  res->tests = h->tests;
+  res->node_tests = h->node_tests;
+}
+
+/* ---- positions of one beam at one step -------------------------------- */
+
+typedef struct {
+  int64_t n;
+  double *P;  /* 3n, xyz interleaved */
+  double *d;  /* 3n */
+  const double *E;
+} posed;
+
+static int pose(const oracle_beam *bm, int64_t step, double dt, posed *o) {
+  o->n = bm->n;
+  o->P = (double *)malloc((size_t)(bm->n > 0 ? bm->n : 1) * 3 * sizeof(double));
+  o->d = (double *)malloc((size_t)(bm->n > 0 ? bm->n : 1) * 3 * sizeof(double));
+  if (!o->P || !o->d) return -1;
+  double ct = O_C * ((double)step * dt);
+  for (int64_t i = 0; i < bm->n; ++i) {
+    pos_at(bm, i, ct, o->P + 3 * i);
+    o->d[3 * i] = bm->dx[i];
+    o->d[3 * i + 1] = bm->dy[i];
+    o->d[3 * i + 2] = bm->dz[i];
+  }
+  o->E = bm->E;
+  return 0;
+}
+
+static void unpose(posed *o) {
+  free(o->P);
+  free(o->d);
+}
+
+int oracle_bruteforce(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                      double kappa, uint32_t *hits, int64_t cap, oracle_result *res) {
+  posed A, B;
+  if (pose(a, step, dt, &A) || pose(b, step, dt, &B)) return -1;
+  hitvec h = {0};
+  for (int64_t i = 0; i < a->n; ++i)
+    for (int64_t j = 0; j < b->n; ++j)
+      if (decide(A.P + 3 * i, A.d + 3 * i, A.E[i], B.P + 3 * j, B.d + 3 * j, B.E[j], dt, kappa,
+                 NULL))
+        if (hv_push(&h, ((uint64_t)i << 32) | (uint64_t)j)) return -1;
+  h.tests = a->n * b->n;
+  finish(&h, a, b, hits, cap, res);
+  free(h.key);
+  unpose(&A);
+  unpose(&B);
+  return 0;
+}
+
+/* ---- the k-d hierarchy (Sec. 2.1) -------------------------------------- */
+
+typedef struct {
+  double lo[3], hi[3];
+  int64_t left, right; /* children, -1 for a leaf */
+  int64_t first, count; /* leaf: particles idx[first .. first+count) */
+} kdnode;
+
+typedef struct {
+  kdnode *node;
+  int64_t nn;
+  int64_t *idx;     /* particle array sorted by leaf affiliation */
+  double *lo, *hi;  /* per-particle swept box, 3n each */
+  double *cen;      /* per-particle box centre, 3n */
+  int leaf_size;
+} kdtree;
+
+static void swap_i64(int64_t *a, int64_t *b) {
+  int64_t t = *a;
+  *a = *b;
+  *b = t;
+}
+
+/* place the k-th smallest (by cen[axis], ties by index) at idx[k] */
+static void select_kth(int64_t *idx, int64_t lo, int64_t hi, int64_t k, const double *cen,
+                       int axis) {
+  while (hi - lo > 1) {
+    int64_t mid = lo + (hi - lo) / 2;
+    /* median of three as pivot */
+    int64_t c3[3] = {idx[lo], idx[mid], idx[hi - 1]};
+    for (int x = 0; x < 3; ++x)
+      for (int y = x + 1; y < 3; ++y) {
+        double vx = cen[3 * c3[x] + axis], vy = cen[3 * c3[y] + axis];
+        if (vy < vx || (vy == vx && c3[y] < c3[x])) swap_i64(&c3[x], &c3[y]);
+      }
+    int64_t piv = c3[1];
+    double pv = cen[3 * piv + axis];
+    /* three-way partition around (pv, piv) */
+    int64_t l = lo, r = hi - 1, m = lo;
+    while (m <= r) {
+      int64_t q = idx[m];
+      double v = cen[3 * q + axis];
+      int less = v < pv || (v == pv && q < piv);
+      int greater = v > pv || (v == pv && q > piv);
+      if (less) {
+        swap_i64(&idx[l], &idx[m]);
+        ++l;
+        ++m;
+      } else if (greater) {
+        swap_i64(&idx[m], &idx[r]);
+        --r;
+      } else {
+        ++m;
+      }
+    }
+    if (k < l)
+      hi = l;
+    else if (k > r)
+      lo = r + 1;
+    else
+      return;
+  }
+}
+
+static int64_t kd_build_rec(kdtree *t, int64_t first, int64_t count, int depth) {
+  int64_t me = t->nn++;
+  kdnode *nd = &t->node[me];
+  for (int c = 0; c < 3; ++c) {
+    nd->lo[c] = INFINITY;
+    nd->hi[c] = -INFINITY;
+  }
+  for (int64_t k = first; k < first + count; ++k) {
+    int64_t p = t->idx[k];
+    for (int c = 0; c < 3; ++c) {
+      if (t->lo[3 * p + c] < nd->lo[c]) nd->lo[c] = t->lo[3 * p + c];
+      if (t->hi[3 * p + c] > nd->hi[c]) nd->hi[c] = t->hi[3 * p + c];
+    }
+  }
+  nd->first = first;
+  nd->count = count;
+  if (count <= t->leaf_size) {
+    nd->left = nd->right = -1;
+    return me;
+  }
+  int axis = depth % 3; /* the cut direction cycles after each cut */
+  int64_t half = count / 2; /* balance the particle counts */
+  select_kth(t->idx, first, first + count, first + half, t->cen, axis);
+  int64_t l = kd_build_rec(t, first, half, depth + 1);
+  int64_t r = kd_build_rec(t, first + half, count - half, depth + 1);
+  t->node[me].left = l;
+  t->node[me].right = r;
+  return me;
+}
+
+static int kd_build(kdtree *t, const posed *p, double L, double h, int leaf_size) {
+  int64_t n = p->n;
+  size_t n1 = (size_t)(n > 0 ? n : 1);
+  t->idx = (int64_t *)malloc(n1 * sizeof(int64_t));
+  t->lo = (double *)malloc(n1 * 3 * sizeof(double));
+  t->hi = (double *)malloc(n1 * 3 * sizeof(double));
+  t->cen = (double *)malloc(n1 * 3 * sizeof(double));
+  t->node = (kdnode *)malloc(n1 * 2 * sizeof(kdnode));
+  t->leaf_size = leaf_size < 1 ? 1 : leaf_size;
+  t->nn = 0;
+  if (!t->idx || !t->lo || !t->hi || !t->cen || !t->node) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    t->idx[i] = i;
+    for (int c = 0; c < 3; ++c) {
+      double s0 = p->P[3 * i + c];
+      double s1 = s0 + L * p->d[3 * i + c]; /* end of the step's travel */
+      double mn = s0 < s1 ? s0 : s1, mx = s0 < s1 ? s1 : s0;
+      t->lo[3 * i + c] = mn - h;
+      t->hi[3 * i + c] = mx + h;
+      t->cen[3 * i + c] = 0.5 * (mn + mx);
+    }
+  }
+  if (n > 0) kd_build_rec(t, 0, n, 0);
+  return 0;
+}
+
+static void kd_free(kdtree *t) {
+  free(t->idx);
+  free(t->lo);
+  free(t->hi);
+  free(t->cen);
+  free(t->node);
+}
+
+/* Eq. CollDet with closed boxes (the symmetric six comparisons) */
+static inline int overlap(const kdnode *x, const kdnode *y) {
+  return x->lo[0] <= y->hi[0] && y->lo[0] <= x->hi[0] && x->lo[1] <= y->hi[1] &&
+         y->lo[1] <= x->hi[1] && x->lo[2] <= y->hi[2] && y->lo[2] <= x->hi[2];
+}
+
+typedef struct {
+  const kdtree *ta, *tb;
+  const posed *A, *B;
+  double dt, kappa;
+  hitvec h;
+  int err;
+} trav;
+
+static void visit(trav *w, int64_t ia, int64_t ib) {
+  const kdnode *na = &w->ta->node[ia], *nb = &w->tb->node[ib];
+  w->h.node_tests++;
+  if (!overlap(na, nb)) return;
+  int la = na->left < 0, lb = nb->left < 0;
+  if (la && lb) {
+    for (int64_t x = na->first; x < na->first + na->count; ++x) {
+      int64_t i = w->ta->idx[x];
+      for (int64_t y = nb->first; y < nb->first + nb->count; ++y) {
+        int64_t j = w->tb->idx[y];
+        w->h.tests++;
+        if (decide(w->A->P + 3 * i, w->A->d + 3 * i, w->A->E[i], w->B->P + 3 * j,
+                   w->B->d + 3 * j, w->B->E[j], w->dt, w->kappa, NULL))
+          if (hv_push(&w->h, ((uint64_t)i << 32) | (uint64_t)j)) w->err = 1;
+      }
+    }
+    return;
+  }
+  /* descend the side that is not a leaf; of two inner nodes the larger */
+  if (la || (!lb && nb->count > na->count)) {
+    visit(w, ia, nb->left);
+    visit(w, ia, nb->right);
+  } else {
+    visit(w, na->left, ib);
+    visit(w, na->right, ib);
+  }
+}
+
+typedef struct {
+  trav *w;
+  const int64_t *roots;
+  int64_t nroots;
+  int tid, nthreads;
+} job;
+
+static void *run_job(void *arg) {
+  job *j = (job *)arg;
+  for (int64_t k = j->tid; k < j->nroots; k += j->nthreads) visit(j->w, j->roots[k], 0);
+  return NULL;
+}
+
+int oracle_tree(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                double kappa, int leaf_size, int nthreads, uint32_t *hits, int64_t cap,
+                oracle_result *res) {
+  posed A, B;
+  if (pose(a, step, dt, &A) || pose(b, step, dt, &B)) return -1;
+  /* inflate each swept box by half the largest collision radius, with a
+   * relative and an absolute margin far above FP64 rounding */
+  double smax = oracle_sigma_max() * (1.0 + 1e-6);
+  double rmax = sqrt(((1e12 * kappa) * smax) / O_PI) * (1.0 + 1e-6);
+  double h = 0.5 * rmax + 1e-9;
+  double L = O_C * dt;
+  kdtree ta, tb;
+  if (kd_build(&ta, &A, L, h, leaf_size) || kd_build(&tb, &B, L, h, leaf_size)) return -1;
+  hitvec all = {0};
+  int err = 0;
+  if (a->n > 0 && b->n > 0) {
+    if (nthreads <= 1) {
+      trav w = {&ta, &tb, &A, &B, dt, kappa, {0}, 0};
+      visit(&w, 0, 0);
+      all = w.h;
+      err = w.err;
+    } else {
+      /* subtrees of A at the first level with >= 8 nthreads nodes */
+      int64_t cap_r = 16 * (int64_t)nthreads + 2, nr = 1;
+      int64_t *roots = (int64_t *)malloc((size_t)cap_r * 2 * sizeof(int64_t));
+      int64_t *next = roots + cap_r;
+      roots[0] = 0;
+      while (nr < 8 * nthreads) {
+        int64_t nn = 0, grew = 0;
+        for (int64_t k = 0; k < nr; ++k) {
+          const kdnode *nd = &ta.node[roots[k]];
+          if (nd->left >= 0 && nn + 2 <= cap_r) {
+            next[nn++] = nd->left;
+            next[nn++] = nd->right;
+            grew = 1;
+          } else {
+            next[nn++] = roots[k];
+          }
+        }
+        memcpy(roots, next, (size_t)nn * sizeof(int64_t));
+        nr = nn;
+        if (!grew || nn + 2 > cap_r) break;
+      }
+      trav *ws = (trav *)calloc((size_t)nthreads, sizeof(trav));
+      job *js = (job *)calloc((size_t)nthreads, sizeof(job));
+      pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+      for (int t = 0; t < nthreads; ++t) {
+        ws[t] = (trav){&ta, &tb, &A, &B, dt, kappa, {0}, 0};
+        js[t] = (job){&ws[t], roots, nr, t, nthreads};
+        pthread_create(&th[t], NULL, run_job, &js[t]);
+      }
+      for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+      for (int t = 0; t < nthreads; ++t) {
+        for (int64_t k = 0; k < ws[t].h.n; ++k)
+          if (hv_push(&all, ws[t].h.key[k])) err = 1;
+        all.tests += ws[t].h.tests;
+        all.node_tests += ws[t].h.node_tests;
+        err |= ws[t].err;
+        free(ws[t].h.key);
+      }
+      free(ws);
+      free(js);
+      free(th);
+      free(roots);
+    }
+  }
+  finish(&all, a, b, hits, cap, res);
+  free(all.key);
+  kd_free(&ta);
+  kd_free(&tb);
+  unpose(&A);
+  unpose(&B);
+  return err ? -1 : 0;
+}

@@ -1,0 +1,68 @@
+/*
+ * oracle.h -- FP64 CPU oracle for Breit-Wheeler collision detection between
+ * two photon beams.  TEST INFRASTRUCTURE ONLY: the tests, the smoke check and
+ * the benchmark's CPU-baseline leg call it; the product path never does.
+ *
+ * It shares no code with the CUDA path.  Every function is the plain
+ * definition, evaluated in IEEE double with no FMA contraction
+ * (compile with -ffp-contract=off), in the operation order written here.
+ *
+ * Units: um, fs, MeV; cross sections in m^2.
+ */
+#ifndef TRILENS_ORACLE_H
+#define TRILENS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int64_t n;
+  const double *px, *py, *pz; /* position at t = 0 [um] */
+  const double *dx, *dy, *dz; /* unit direction */
+  const double *E;            /* energy [MeV] */
+  const double *w;            /* weight (real photons per macro-photon) */
+} oracle_beam;
+
+typedef struct {
+  int64_t count;    /* |H_k|, hits found (may exceed the caller's capacity) */
+  double weighted;  /* sum over hits of w_i * w_j */
+  uint64_t hsum;    /* sum of splitmix64((i << 32) | j) mod 2^64 */
+  uint64_t hxor;    /* xor of the same */
+  int64_t tests;    /* photon pairs given the full narrow-phase test */
+  int64_t node_tests; /* box-pair overlap tests (tree only) */
+} oracle_result;
+
+/* natural log by argument reduction to [sqrt(1/2), sqrt(2)) and the odd
+ * atanh series ln m = 2 (f + f^3/3 + ... + f^23/23), f = (m-1)/(m+1) */
+double oracle_ln(double x);
+/* Eq. BWcross: total Breit-Wheeler cross section [m^2]; 0 for s <= 1 */
+double oracle_sigma(double s);
+/* the invariant s of the text below Eq. BWcross */
+double oracle_s(double E1, double E2, double cos_phi);
+/* maximum of oracle_sigma over s (golden-section search) */
+double oracle_sigma_max(void);
+/* the full per-pair decision for step k (positions propagated in closed form) */
+int oracle_pair_hit(const oracle_beam *a, int64_t i, const oracle_beam *b, int64_t j,
+                    int64_t step, double dt, double kappa);
+/* the same decision with the pieces it computed (for diagnostics/tests) */
+int oracle_pair_detail(const oracle_beam *a, int64_t i, const oracle_beam *b, int64_t j,
+                       int64_t step, double dt, double kappa, double out[6]);
+uint64_t oracle_splitmix64(uint64_t x);
+
+/* All pairs.  Hits (i, j) written as uint32 pairs in lexicographic order,
+ * at most cap of them; res->count is the true number. */
+int oracle_bruteforce(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                      double kappa, uint32_t *hits, int64_t cap, oracle_result *res);
+/* Paper's k-d hierarchy (median cuts, cycling axis) per beam over swept
+ * boxes, dual depth-first traversal; same output contract as brute force.
+ * nthreads > 1 splits the traversal over subtrees of beam A. */
+int oracle_tree(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                double kappa, int leaf_size, int nthreads, uint32_t *hits, int64_t cap,
+                oracle_result *res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

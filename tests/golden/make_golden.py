@@ -1,0 +1,43 @@
+"""Write tests/golden/oracle_values.json from the FP64 CPU oracle only.
+
+Run:  python tests/golden/make_golden.py
+Values: hit count, weighted yield and the order-free checksums of single
+steps of the seeded synthetic workloads.  They let the GPU tests compare
+full-size steps without recomputing the oracle, and pin the oracle's FP64
+results across host architectures (x86-64 here, aarch64 on the GPU host).
+"""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_1608_01125_gb300 import synth  # noqa: E402
+
+
+def main():
+    out = {"_about": "FP64 oracle results; written by tests/golden/make_golden.py", "cases": []}
+    wl = synth.tiny_headon()
+    a, b = synth.beams(wl)
+    _, r = oracle.bruteforce(a, b, 0, wl.dt, wl.kappa)
+    out["cases"].append({"workload": wl.name, "n": wl.a.n, "seed": wl.seed, "step": 0,
+                         "method": "bruteforce", **{k: r[k] for k in ("count", "weighted")},
+                         "hsum": str(r["hsum"]), "hxor": str(r["hxor"])})
+    wl = synth.headon_1m()
+    a, b = synth.beams(wl)
+    for step in (0, 1, 7, 40):
+        _, r = oracle.tree(a, b, step, wl.dt, wl.kappa, nthreads=os.cpu_count() or 1,
+                           cap=1 << 22)
+        out["cases"].append({"workload": wl.name, "n": wl.a.n, "seed": wl.seed, "step": step,
+                             "method": "tree", **{k: r[k] for k in ("count", "weighted")},
+                             "hsum": str(r["hsum"]), "hxor": str(r["hxor"])})
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_values.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path)
+
+
+if __name__ == "__main__":
+    main()
