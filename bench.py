@@ -1,0 +1,362 @@
+"""Benchmark: exact Breit-Wheeler collision detection, 2 x 1,048,576 photons.
+
+One benchmark step = one full run of the head-on workload: 64 time steps of
+5 fs, each a hierarchy build of both beams plus the collision step (dual
+traversal, FP32 narrow phase, FP64 band re-test, yield), inputs resident in
+HBM.  The metric counts photon-pair tests in the all-pairs sense: each time
+step answers N_A * N_B pair queries.  Collided pairs/s and the narrow-phase
+tests actually evaluated per second are reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the path has no exchange step); the value is the units of all ranks over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1608_01125_gb300 import synth  # noqa: E402
+
+METRIC = "photon-pair tests/s at 2x1M (N_A*N_B pair queries per time step)"
+UNIT = "pair-tests/s"
+FALLBACK_HBM_GBS = 6800.0
+PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "band", "yield")
+
+
+def algorithmic_bytes(phase: str, na: int, nb: int, key_bits: tuple, hits: float, band: float):
+    """Bytes one launch of a phase must move at least (per beam launches use
+    that beam's size; traversal and later phases cover both beams)."""
+    n = na + nb
+    if phase == "propagate":   # 7 doubles in; float4 x2 + key + index out
+        return 56 + 32 + 12, "photon"
+    if phase == "sort":        # per pass: key + index read and written
+        return 24, "photon-pass"
+    if phase == "gather":      # index, random float4 x2 read, float4 x2 written
+        return 4 + 32 + 32, "photon"
+    if phase == "emit":        # keys read, child refs + counts + parent written
+        return 8 + 16 + 4, "photon"
+    if phase == "refit":       # sorted SoA read, parent, two child boxes per node
+        return 32 + 4 + 24 + 4, "photon"
+    if phase == "traverse":    # node records and sorted SoA of both trees once + output pairs
+        return 64 + 32, "photon"
+    return 8, "pair"
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1608_01125_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources have not changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = src_hash()
+    for line in open(p):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("phase") == kernel and f.get("src") == cur and "bytes_per_launch" in f:
+            return float(f["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "power_w_median": statistics.median(float(r[3]) for r in rows if _isnum(r[3])),
+                "samples": len(rows), "reasons": reasons}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ------------------------------------------------------------------ oracle leg
+
+
+def oracle_sample(wl, a, b, steps, threads):
+    import oracle
+    t0 = time.perf_counter()
+    hits = 0
+    for k in steps:
+        _, r = oracle.tree(a, b, k, wl.dt, wl.kappa, nthreads=threads, cap=1 << 22)
+        hits += r["count"]
+    return time.perf_counter() - t0, hits
+
+
+def cpu_baseline(wl, a, b):
+    threads = os.cpu_count() or 1
+    steps = list(range(0, wl.steps, 16))  # 4 of the 64 time steps, evenly spaced
+    dt, _ = oracle_sample(wl, a, b, steps, threads)
+    value = wl.a.n * wl.b.n * len(steps) / dt
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 k-d-tree oracle, time steps {steps} of the {wl.steps}-step run, "
+                      f"{threads} threads, {dt:.1f} s"}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    a, b = synth.beams(wl)
+    threads = os.cpu_count() or 1
+    steps = list(range(0, wl.steps, 16))
+    for _ in range(args.warmup):
+        oracle_sample(wl, a, b, steps[:1], threads)
+    total = 0.0
+    for _ in range(args.steps):
+        dt, _ = oracle_sample(wl, a, b, steps, threads)
+        total += dt
+    units = wl.a.n * wl.b.n * len(steps) * args.steps
+    value = units / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": config_of(wl, "oracle on the host cores; no GPU"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step = time steps {steps} of the {wl.steps}-step run"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, l2):
+    return {"workload": wl.name, "photons_per_beam": wl.a.n, "time_steps": wl.steps,
+            "dt_fs": wl.dt, "kappa": wl.kappa, "precision": "fp32 + fp64 band",
+            "l2": l2, "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ GPU leg
+
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1608_01125_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    a_np, b_np = synth.beams(wl, seed=wl.seed + rank)
+    A = binding.to_device(a_np, dev)
+    B = binding.to_device(b_np, dev)
+    col = binding.Collider(A, B, wl.dt, wl.kappa, precision=binding.FP32_BAND, stream=stream)
+
+    def one_run():
+        hits = tests = band = 0
+        for k in range(wl.steps):
+            col.build(k)
+            hits += col.collide(k)
+            st = col.stats()
+            tests += st["narrow_tests"]
+            band += st["band"]
+        return hits, tests, band
+
+    for _ in range(max(args.warmup, 0)):
+        one_run()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    col.timing(True)
+    col.phase_ms(reset=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = []
+    hits = tests = band = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h, t, bd = one_run()
+            e1.record(stream)
+            evs.append((e0, e1))
+            hits += h
+            tests += t
+            band += bd
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    phase_ms, launches = col.phase_ms(reset=True)
+    col.timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    K = args.steps
+    units_rank = wl.a.n * wl.b.n * wl.steps * K
+    value = world * units_rank / (ms / 1e3)
+
+    # end to end through the public API with host buffers: every step copies
+    # the two beams from pinned host memory, runs, and reads the yield back
+    pinned = {k: {kk: v.cpu().pin_memory() for kk, v in D.items()} for k, D in (("a", A), ("b", B))}
+    h2d = sum(v.numel() * v.element_size() for D in pinned.values() for v in D.values())
+    e2e_ms = []
+    for i in range(args.warmup + K):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for key, D in (("a", A), ("b", B)):
+            for kk, v in D.items():
+                v.copy_(pinned[key][kk], non_blocking=True)
+        col.reset_yield()
+        for k in range(wl.steps):
+            col.build(k)
+            col.collide(k)
+        cnt, wsum = col.yield_()  # device -> host read of the result
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = world * wl.a.n * wl.b.n * wl.steps / (statistics.mean(e2e_ms) / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_src = read_peaks()
+    # dominant phase and its roofline
+    dom = max(phase_ms, key=lambda p: phase_ms[p])
+    per_unit, unit_name = algorithmic_bytes(dom, wl.a.n, wl.b.n, None, hits / K, band / K)
+    n_launch = max(launches[dom], 1)
+    if dom == "sort":
+        units_per_launch = (wl.a.n + wl.b.n) / 2  # one pass of one beam
+        algo = per_unit * units_per_launch
+        n_pass = max(launches[dom] - 2 * 2 * wl.steps * (K), 1)  # passes exclude hist + scan
+        launch_ms = phase_ms[dom] / n_launch
+    elif dom in ("propagate", "gather", "emit", "refit"):
+        algo = per_unit * (wl.a.n + wl.b.n) / 2
+        launch_ms = phase_ms[dom] / n_launch
+    else:
+        algo = per_unit * (wl.a.n + wl.b.n) + 8.0 * (hits + band) / (K * wl.steps)
+        launch_ms = phase_ms[dom] / n_launch
+    achieved = algo / (launch_ms / 1e3) / 1e9
+    cpu = cpu_baseline(wl, a_np, b_np) if (world == 1 and not args.no_cpu_baseline) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": config_of(wl, "flushed (256 MiB write) before every timed step"),
+        "collided_pairs_per_s": world * hits / (ms / 1e3),
+        "narrow_tests_per_s": world * tests / (ms / 1e3),
+        "hits_per_run": hits / K, "narrow_tests_per_run": tests / K, "band_per_run": band / K,
+        "phase_ms_per_run": {p: phase_ms[p] / K for p in PHASES},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": read_traffic(dom), "algorithmic_bytes_per_launch": algo,
+                     "launch_ms": launch_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 16},
+        "gpu_launches": int(sum(launches.values())),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--photons", type=int, default=1 << 20)
+    args = ap.parse_args()
+    wl = synth.headon_1m(n=args.photons)
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

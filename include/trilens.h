@@ -1,0 +1,149 @@
+/*
+ * trilens.h -- C ABI of the GB300 (sm_103a) Breit-Wheeler collision library.
+ *
+ * Two beams of photons (macro-photons) move on straight lines.  Each time
+ * step the library builds, for each beam, a bounding-volume hierarchy over
+ * the boxes swept by its photons during the step (Sec. 2.1: a BV grows by the
+ * distance its particles travel in one step, so collisions are found before
+ * they happen), traverses the two hierarchies against each other with the
+ * axis-aligned overlap test (Eq. CollDet; depth-first descent, Sec. 2.2), and
+ * tests the surviving photon pairs.  A pair (i in A, j in B) collides in step
+ * k when
+ *     s = E_i E_j (1 - cos Phi) / (2 m_e^2 c^4) > 1           (Eq. eq.Cond)
+ *     t* = time of the pair's closest approach, 0 <= t* - t_k < dt
+ *     d(t*)^2 < r^2 = kappa sigma(s) / pi,  sigma from Eq. BWcross
+ * and contributes w_i w_j to the pair yield (Sec. 2.2: rates scale with
+ * n_I n_II).  Decisions are those of the FP64 definition, bit for bit: in
+ * TRILENS_FP32_BAND mode the FP32 fast path only decides pairs that its
+ * rigorous error bound puts on one side; the rest are re-tested in FP64.
+ *
+ * Units: positions um, time fs, energies MeV, sigma m^2, c = 0.299792458 um/fs.
+ *
+ * Conventions shared by every call:
+ *  - Return value: TRILENS_OK (0) or a negative TRILENS_ERR_* code; the last
+ *    code and a message are kept per context (trilens_last_error).
+ *  - Memory: "device" pointers are CUDA device memory on the context's
+ *    device, "host" pointers are ordinary host memory.  The caller owns every
+ *    array it passes and keeps input arrays alive and unchanged for the life
+ *    of the context; the library owns all workspace it allocates.
+ *  - Streams: work is enqueued on the stream given to trilens_create (a
+ *    cudaStream_t; NULL = legacy default stream).  Calls that return host
+ *    values synchronise that stream.
+ *  - Photon indices in hit lists are the caller's input indices.
+ */
+#ifndef TRILENS_H
+#define TRILENS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *trilens_stream_t; /* == cudaStream_t */
+typedef struct trilens_ctx trilens_ctx;       /* opaque, library-owned */
+
+enum trilens_status {
+  TRILENS_OK = 0,
+  TRILENS_ERR_INVALID = -1,  /* bad argument, detected on the host */
+  TRILENS_ERR_CAPACITY = -2, /* caller's hit buffer too small; *n_hits = size needed */
+  TRILENS_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  TRILENS_ERR_TIMEOUT = -4,  /* a bounded device wait reached spin_limit */
+  TRILENS_ERR_STACK = -5,    /* traversal overflowed after the automatic retries */
+  TRILENS_ERR_NOMEM = -6     /* device allocation failed */
+};
+
+enum trilens_precision {
+  TRILENS_FP64 = 0,      /* every narrow-phase pair decided in FP64 */
+  TRILENS_FP32_BAND = 1  /* FP32 decision with FP64 re-test of the band */
+};
+
+enum trilens_yield_mode { TRILENS_YIELD_EXACT = 0, TRILENS_YIELD_SURROGATE = 1 };
+
+/* One beam: structure of arrays, FP64, device memory, length n.
+ * p = position at t = 0 [um]; d = unit direction (used as given, never
+ * renormalised); E = energy [MeV]; w = weight (real photons per
+ * macro-photon), NULL means 1 for every photon.  Sec. 2.2 (macro-particles). */
+typedef struct {
+  int64_t n;
+  const double *px, *py, *pz;
+  const double *dx, *dy, *dz;
+  const double *E;
+  const double *w;
+} trilens_beam;
+
+/* Stepping and tuning parameters.  Tuning fields set to 0 pick defaults. */
+typedef struct {
+  double dt_fs;        /* time step [fs], > 0 */
+  double kappa;        /* cross-section amplification, > 0 (r^2 = kappa sigma / pi) */
+  int32_t precision;   /* enum trilens_precision */
+  int32_t leaf_bucket; /* photons per hierarchy leaf, 1..32 (0: 4) */
+  int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (0: 256) */
+  int32_t block_shape; /* traversal warps per block, 1..16 (0: 4) */
+  int64_t spin_limit;  /* iteration limit of every device wait (0: 1<<22) */
+} trilens_params;
+
+/* Per-step counters of the last trilens_collide_step call. */
+typedef struct {
+  int64_t step;
+  int64_t count;        /* |H_k|: colliding pairs found in the step */
+  double weighted;      /* sum over H_k of w_i w_j (FP64) */
+  uint64_t hsum;        /* sum of splitmix64((i << 32) | j) mod 2^64 over H_k */
+  uint64_t hxor;        /* xor of the same (order-free checksum pair) */
+  int64_t narrow_tests; /* photon pairs given the narrow-phase test */
+  int64_t node_tests;   /* box-pair overlap tests during traversal */
+  int64_t leaf_pairs;   /* overlapping leaf pairs */
+  int64_t band;         /* pairs re-tested in FP64 (FP32_BAND mode) */
+  int64_t retries;      /* internal buffer regrowths in this step */
+} trilens_step_stats;
+
+/* Create a context for beams a and b (both kept by pointer; arrays must stay
+ * valid).  Allocates the workspace for both beams.  Returns INVALID for
+ * n < 0, n >= 2^27, missing arrays, dt <= 0, kappa <= 0 or tuning fields out
+ * of range; NOMEM if the workspace does not fit. */
+int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam *b,
+                   const trilens_params *p, trilens_stream_t stream);
+
+/* Build both hierarchies for step `step` (t_k = step * dt): propagate
+ * positions in closed form p0 + c t_k d (FP64), form the FP32 swept boxes
+ * (Sec. 2.1), Morton-sort them and emit the hierarchy (Sec. 2.1, 2.2).
+ * Asynchronous.  INVALID if step < 0. */
+int trilens_build(trilens_ctx *c, int64_t step);
+
+/* Collide the hierarchies built for `step` (trilens_build must have been
+ * called with the same step).  Appends the step's counters to the cumulative
+ * yield.  If hits != NULL (device, 2*cap uint32: (i_A, j_B) pairs, order
+ * unspecified), up to cap pairs are written; if more exist the call returns
+ * CAPACITY and stores the required size in *n_hits.  n_hits (host) may be
+ * NULL.  Synchronises the stream (to check device status and regrow internal
+ * buffers). */
+int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t cap,
+                         int64_t *n_hits);
+
+/* Counters of the last collided step (host struct). */
+int trilens_step_stats_get(trilens_ctx *c, trilens_step_stats *out);
+
+/* Cumulative yield since creation or the last reset: number of colliding
+ * pairs and sum of w_i w_j (host doubles).  mode EXACT returns the exact
+ * totals; level_L is ignored for EXACT. */
+int trilens_yield(trilens_ctx *c, int32_t mode, int32_t level_L, double *count,
+                  double *weighted);
+
+/* Zero the cumulative yield. */
+int trilens_reset_yield(trilens_ctx *c);
+
+/* Free the context and its workspace.  NULL is ignored. */
+void trilens_destroy(trilens_ctx *c);
+
+/* Message for a status code (static string). */
+const char *trilens_status_str(int code);
+
+/* Last error message recorded in a context (static until the next call). */
+const char *trilens_last_error(trilens_ctx *c);
+
+/* Library version string. */
+const char *trilens_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRILENS_H */

@@ -1,0 +1,55 @@
+/*
+ * trilens_debug.h -- fault-injection hooks of the trilens library, for tests.
+ *
+ * They make the library's bounded device waits expire on purpose, on the
+ * host's request, so that tests can check that an expired wait is reported
+ * as TRILENS_ERR_TIMEOUT and the context stays usable -- without faulting or
+ * hanging a GPU.  The paper describes no such mechanism; it is part of the
+ * library's own error handling (every device wait carries an iteration
+ * limit).
+ */
+#ifndef TRILENS_DEBUG_H
+#define TRILENS_DEBUG_H
+#include <stdint.h>
+#include "trilens.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* on != 0: in the next builds, the first tile of the radix sort's first pass
+ * withholds its published digit counts, so the second tile's look-back wait
+ * runs to the spin limit, records a timeout and continues.  The following
+ * trilens_collide_step then returns TRILENS_ERR_TIMEOUT.  on = 0 restores
+ * normal operation.  INVALID for a NULL context. */
+int trilens_debug_stall_sort(trilens_ctx *c, int on);
+
+/* Replace the context's spin limit (iterations of every bounded device wait,
+ * >= 1).  INVALID for a NULL context or limit < 1. */
+int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit);
+
+/* Evaluate the device FP64 functions of the exact decision element-wise:
+ * which = 0: sigma(x) of Eq. BWcross [m^2] (0 for x <= 1); which = 1: the
+ * natural log of x (x >= 1 finite; the only arguments the decision uses).
+ * x and out are device arrays of n doubles; asynchronous on `stream`.
+ * INVALID for n < 0, NULL arrays with n > 0 or another `which`. */
+int trilens_debug_eval64(const double *x, double *out, int64_t n, int32_t which,
+                         trilens_stream_t stream);
+
+/* Per-phase device time.  on != 0 records CUDA events around every kernel
+ * phase on the context's stream (cheap, but adds event records).  The
+ * phases, in order: 0 propagate+Morton, 1 radix sort, 2 gather, 3 hierarchy
+ * emit, 4 refit, 5 frontier expansion, 6 traversal+narrow phase, 7 FP64 band
+ * re-test, 8 yield reduction. */
+int trilens_debug_timing(trilens_ctx *c, int on);
+
+/* Copy the accumulated milliseconds of the 9 phases into out[0..8], the
+ * launches of each phase into launches[0..8] (either may be NULL), then zero
+ * them if reset != 0.  Accumulated at each trilens_collide_step (which
+ * synchronises). */
+int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

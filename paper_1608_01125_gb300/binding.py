@@ -1,0 +1,278 @@
+"""Python binding of the trilens C ABI (``include/trilens.h``).
+
+Argument marshalling only: device memory and streams come from PyTorch, every
+step of the collision path runs in the CUDA library ``libtrilens.so``.  There
+is no fallback: if the library or a CUDA device is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtrilens.so")
+
+OK = 0
+ERR_INVALID = -1
+ERR_CAPACITY = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+ERR_STACK = -5
+ERR_NOMEM = -6
+
+FP64 = 0
+FP32_BAND = 1
+YIELD_EXACT = 0
+YIELD_SURROGATE = 1
+
+BEAM_KEYS = ("px", "py", "pz", "dx", "dy", "dz", "E", "w")
+
+
+class TrilensError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"trilens error {code}: {msg}")
+        self.code = code
+
+
+class Beam(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in BEAM_KEYS]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dt_fs", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("leaf_bucket", ctypes.c_int32),
+                ("stack_depth", ctypes.c_int32), ("block_shape", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("count", ctypes.c_int64), ("weighted", ctypes.c_double),
+                ("hsum", ctypes.c_uint64), ("hxor", ctypes.c_uint64),
+                ("narrow_tests", ctypes.c_int64), ("node_tests", ctypes.c_int64),
+                ("leaf_pairs", ctypes.c_int64), ("band", ctypes.c_int64),
+                ("retries", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+#: kernel phases reported by Collider.phase_ms (trilens_debug_phase_ms order)
+PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "band", "yield")
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libtrilens.so`` (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.trilens_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Beam), ctypes.POINTER(Beam),
+                                     ctypes.POINTER(Params), vp]
+        L.trilens_create.restype = ctypes.c_int
+        L.trilens_build.argtypes = [vp, i64]
+        L.trilens_build.restype = ctypes.c_int
+        L.trilens_collide_step.argtypes = [vp, i64, vp, i64, ctypes.POINTER(i64)]
+        L.trilens_collide_step.restype = ctypes.c_int
+        L.trilens_step_stats_get.argtypes = [vp, ctypes.POINTER(StepStats)]
+        L.trilens_step_stats_get.restype = ctypes.c_int
+        L.trilens_yield.argtypes = [vp, i32, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        L.trilens_yield.restype = ctypes.c_int
+        L.trilens_reset_yield.argtypes = [vp]
+        L.trilens_reset_yield.restype = ctypes.c_int
+        L.trilens_destroy.argtypes = [vp]
+        L.trilens_destroy.restype = None
+        L.trilens_status_str.argtypes = [ctypes.c_int]
+        L.trilens_status_str.restype = ctypes.c_char_p
+        L.trilens_last_error.argtypes = [vp]
+        L.trilens_last_error.restype = ctypes.c_char_p
+        L.trilens_version.argtypes = []
+        L.trilens_version.restype = ctypes.c_char_p
+        L.trilens_debug_stall_sort.argtypes = [vp, ctypes.c_int]
+        L.trilens_debug_stall_sort.restype = ctypes.c_int
+        L.trilens_debug_set_spin_limit.argtypes = [vp, i64]
+        L.trilens_debug_set_spin_limit.restype = ctypes.c_int
+        L.trilens_debug_eval64.argtypes = [vp, vp, i64, i32, vp]
+        L.trilens_debug_eval64.restype = ctypes.c_int
+        L.trilens_debug_timing.argtypes = [vp, ctypes.c_int]
+        L.trilens_debug_timing.restype = ctypes.c_int
+        L.trilens_debug_phase_ms.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.c_int]
+        L.trilens_debug_phase_ms.restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def status_str(code: int) -> str:
+    return lib().trilens_status_str(code).decode()
+
+
+def _check(rc: int, ctx=None):
+    if rc != OK:
+        msg = status_str(rc)
+        if ctx is not None:
+            detail = lib().trilens_last_error(ctx)
+            if detail:
+                msg += f" ({detail.decode()})"
+        raise TrilensError(rc, msg)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("trilens needs a CUDA device; none is available")
+    return torch
+
+
+def to_device(beam: dict, device="cuda") -> dict:
+    """Copy a numpy beam (see synth.py) to contiguous float64 device tensors."""
+    torch = _torch()
+    return {k: torch.from_numpy(np.ascontiguousarray(beam[k], dtype=np.float64)).to(device)
+            for k in BEAM_KEYS}
+
+
+def beam_struct(t: dict) -> Beam:
+    n = int(t["px"].numel())
+    ptrs = []
+    for k in BEAM_KEYS:
+        v = t.get(k)
+        if v is None:
+            ptrs.append(None)
+            continue
+        assert v.is_cuda and v.dtype.is_floating_point and v.element_size() == 8
+        assert v.is_contiguous() and v.numel() == n
+        ptrs.append(v.data_ptr() if n > 0 else None)
+    return Beam(n, *ptrs)
+
+
+class Collider:
+    """One context: two resident beams, built and collided step by step."""
+
+    def __init__(self, beam_a: dict, beam_b: dict, dt_fs: float, kappa: float,
+                 precision: int = FP32_BAND, leaf_bucket: int = 0, stack_depth: int = 0,
+                 block_shape: int = 0, spin_limit: int = 0, stream=None):
+        torch = _torch()
+        self._torch = torch
+        self.a = beam_a if _is_dev(beam_a) else to_device(beam_a)
+        self.b = beam_b if _is_dev(beam_b) else to_device(beam_b)
+        self.params = Params(float(dt_fs), float(kappa), int(precision), int(leaf_bucket),
+                             int(stack_depth), int(block_shape), int(spin_limit))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ba, self._bb = beam_struct(self.a), beam_struct(self.b)
+        h = ctypes.c_void_p()
+        _check(lib().trilens_create(ctypes.byref(h), ctypes.byref(self._ba), ctypes.byref(self._bb),
+                                    ctypes.byref(self.params), ctypes.c_void_p(self.stream.cuda_stream)))
+        self.ctx = h
+
+    def build(self, step: int):
+        _check(lib().trilens_build(self.ctx, int(step)), self.ctx)
+
+    def collide(self, step: int, hits=None) -> int:
+        """Collide the built step; with a (cap, 2) uint32-sized int32 tensor,
+        also return the hit pairs in it.  Returns the step's hit count."""
+        n = ctypes.c_int64(0)
+        if hits is None:
+            rc = lib().trilens_collide_step(self.ctx, int(step), None, 0, ctypes.byref(n))
+        else:
+            assert hits.is_cuda and hits.element_size() == 4 and hits.is_contiguous()
+            cap = hits.numel() // 2
+            rc = lib().trilens_collide_step(self.ctx, int(step), ctypes.c_void_p(hits.data_ptr()),
+                                            cap, ctypes.byref(n))
+        if rc == ERR_CAPACITY:
+            raise TrilensError(rc, f"hit buffer too small, need {n.value}")
+        _check(rc, self.ctx)
+        return int(n.value)
+
+    def step_hits(self, step: int, cap: int | None = None):
+        """Build and collide `step`; return (hits[n, 2] int64 numpy, stats)."""
+        torch = self._torch
+        self.build(step)
+        cap = cap or 1 << 16
+        while True:
+            buf = torch.empty((cap, 2), dtype=torch.int32, device=self.a["px"].device)
+            try:
+                n = self.collide(step, buf)
+                break
+            except TrilensError as e:
+                if e.code != ERR_CAPACITY:
+                    raise
+                self.build(step)
+                cap = int(str(e).rsplit(" ", 1)[-1]) + 16
+                # the failed call already counted this step in the yield
+                self.reset_yield()
+        self.stream.synchronize()
+        h = buf[:n].cpu().numpy().view(np.uint32).astype(np.int64)
+        return h, self.stats()
+
+    def stats(self) -> dict:
+        s = StepStats()
+        _check(lib().trilens_step_stats_get(self.ctx, ctypes.byref(s)), self.ctx)
+        return s.as_dict()
+
+    def yield_(self, mode: int = YIELD_EXACT, level_L: int = 0):
+        c, w = ctypes.c_double(), ctypes.c_double()
+        _check(lib().trilens_yield(self.ctx, mode, level_L, ctypes.byref(c), ctypes.byref(w)),
+               self.ctx)
+        return c.value, w.value
+
+    def reset_yield(self):
+        _check(lib().trilens_reset_yield(self.ctx), self.ctx)
+
+    def debug_stall_sort(self, on: bool):
+        _check(lib().trilens_debug_stall_sort(self.ctx, int(bool(on))), self.ctx)
+
+    def timing(self, on: bool = True):
+        _check(lib().trilens_debug_timing(self.ctx, int(bool(on))), self.ctx)
+
+    def phase_ms(self, reset: bool = False) -> tuple[dict, dict]:
+        ms = (ctypes.c_double * 9)()
+        ln = (ctypes.c_int64 * 9)()
+        _check(lib().trilens_debug_phase_ms(self.ctx, ms, ln, int(bool(reset))), self.ctx)
+        return dict(zip(PHASES, list(ms))), dict(zip(PHASES, list(ln)))
+
+    def debug_set_spin_limit(self, limit: int):
+        _check(lib().trilens_debug_set_spin_limit(self.ctx, int(limit)), self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().trilens_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _is_dev(b: dict) -> bool:
+    v = b.get("px")
+    return hasattr(v, "is_cuda") and v.is_cuda
+
+
+def eval64(x, which: str = "sigma", stream=None):
+    """Device FP64 sigma(s) or ln(x) of the exact decision, element-wise on a
+    float64 CUDA tensor (for bit-exact comparison with a CPU implementation)."""
+    torch = _torch()
+    assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+    out = torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().trilens_debug_eval64(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      x.numel(), 0 if which == "sigma" else 1,
+                                      ctypes.c_void_p(st.cuda_stream)))
+    return out

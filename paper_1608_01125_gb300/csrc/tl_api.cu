@@ -1,0 +1,617 @@
+// tl_api.cu -- host runtime behind the C ABI declared in include/trilens.h:
+// context and workspace, per-step build and collide sequencing on the
+// caller's stream, device status checks and buffer regrowth.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "tl_common.cuh"
+#include "trilens.h"
+#include "trilens_debug.h"
+
+namespace tl {
+cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t sb, int nonempty,
+                             const unsigned *build_status, cudaStream_t s);
+cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
+                          int level, int blocks, cudaStream_t s);
+cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm);
+cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
+                            unsigned long long list_n, int from_frontier, int blocks, int warps,
+                            cudaStream_t s);
+cudaError_t launch_band(const TravArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_yield(const TravArgs &a, void *partials, int blocks, cudaStream_t s);
+size_t partial_bytes();
+}  // namespace tl
+
+static const int kMaxLevels = 24;
+
+struct trilens_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  trilens_params p{};
+  TLBeam beam[2]{};
+  // derived constants
+  double L64 = 0, rmax = 0, sigma_max = 0;
+  float L_lo = 0, L_hi = 0, half = 0;
+  TLNarrowConst nk{};
+  int bits[2]{}, key_bits[2]{};
+  double bounds[2][12]{};
+  // build workspace
+  tl::BuildBufs w[2]{};
+  int sel[2]{};
+  int64_t built_step = -1;
+  // traversal workspace
+  int n_sm = 0, trav_warps = 4, trav_blocks = 0, expand_blocks = 0;
+  unsigned front_target = 0, front_cap = 0;
+  uint2 *front[2]{};
+  uint2 *spill[2]{};
+  unsigned long long spill_cap = 0;
+  uint2 *hits = nullptr;
+  unsigned long long hit_cap = 0;
+  uint2 *band = nullptr;
+  unsigned long long band_cap = 0;
+  TLCounters *ctr = nullptr;
+  TLCounters *ctr_host = nullptr;  // pinned
+  void *partials = nullptr;
+  int yield_blocks = 0;
+  unsigned *build_status = nullptr;  // device status of the builds (sort waits)
+  unsigned *build_status_host = nullptr;
+  double *bounds_dev = nullptr;
+  // results
+  trilens_step_stats last{};
+  double tot_count = 0, tot_weighted = 0;
+  int debug_stall_sort = 0;
+  // per-phase timing (events on the context's stream) and launch counts
+  int timing = 0;
+  cudaEvent_t ev[9][2][2]{};   // [phase][beam or 0][start, end]
+  bool ev_pending[9][2]{};
+  double phase_ms[9]{};
+  int64_t phase_launches[9]{};
+  char msg[512] = {0};
+};
+
+enum { PH_PROP = 0, PH_SORT, PH_GATHER, PH_EMIT, PH_REFIT, PH_EXPAND, PH_TRAV, PH_BAND, PH_YIELD };
+
+static void tmark(trilens_ctx *c, int ph, int k, int end) {
+  if (!c->timing) return;
+  cudaEventRecord(c->ev[ph][k][end], c->stream);
+  if (end) c->ev_pending[ph][k] = true;
+}
+
+// add the elapsed time of every recorded phase (the stream is synchronised)
+static void tcollect(trilens_ctx *c) {
+  for (int ph = 0; ph < 9; ++ph)
+    for (int k = 0; k < 2; ++k)
+      if (c->ev_pending[ph][k]) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[ph][k][0], c->ev[ph][k][1]) == cudaSuccess)
+          c->phase_ms[ph] += ms;
+        c->ev_pending[ph][k] = false;
+      }
+}
+
+static int fail(trilens_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? TRILENS_ERR_NOMEM : TRILENS_ERR_CUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+  } while (0)
+
+// ---- host-side constants (plain double; used only for conservative bounds)
+
+static double host_sigma(double s) {
+  if (!(s > 1.0)) return 0.0;
+  double b = sqrt((s - 1.0) / s);
+  double lg = log((1.0 + b) * (1.0 + b) * s);
+  return 0.5 * TL_PI * TL_RE * TL_RE / s * ((3.0 - b * b * b * b) * lg - 2.0 * b * (2.0 - b * b));
+}
+
+static double host_sigma_max() {
+  double lo = 1.2, hi = 4.0, g = 0.5 * (sqrt(5.0) - 1.0);
+  for (int it = 0; it < 200; ++it) {
+    double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+    if (host_sigma(x1) < host_sigma(x2)) lo = x1;
+    else hi = x2;
+  }
+  return host_sigma(0.5 * (lo + hi));
+}
+
+static float round_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, INFINITY);
+  return f;
+}
+static float round_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = nextafterf(f, -INFINITY);
+  return f;
+}
+
+// ---- allocation helpers
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+static void free_beam(tl::BuildBufs &w) {
+  cudaFree(w.pos_u);
+  cudaFree(w.dir_u);
+  cudaFree(w.pos);
+  cudaFree(w.dir);
+  cudaFree(w.key[0]);
+  cudaFree(w.key[1]);
+  cudaFree(w.val[0]);
+  cudaFree(w.val[1]);
+  cudaFree(w.nodes);
+  cudaFree(w.parent_leaf);
+  cudaFree(w.parent_node);
+  cudaFree(w.visit);
+  cudaFree(w.sort_status);
+  cudaFree(w.sort_hist);
+  cudaFree(w.sort_tile);
+  memset(&w, 0, sizeof(w));
+}
+
+static int alloc_beam(trilens_ctx *c, tl::BuildBufs &w, int64_t n) {
+  size_t m = (size_t)std::max<int64_t>(n, 1);
+  CK(dalloc(&w.pos_u, m));
+  CK(dalloc(&w.dir_u, m));
+  CK(dalloc(&w.pos, m));
+  CK(dalloc(&w.dir, m));
+  CK(dalloc(&w.key[0], m));
+  CK(dalloc(&w.key[1], m));
+  CK(dalloc(&w.val[0], m));
+  CK(dalloc(&w.val[1], m));
+  CK(dalloc(&w.nodes, m));
+  CK(dalloc(&w.parent_leaf, m));
+  CK(dalloc(&w.parent_node, m));
+  CK(dalloc(&w.visit, m));
+  w.sort_tiles = (int64_t)((m + 4095) / 4096);
+  CK(dalloc(&w.sort_status, (size_t)w.sort_tiles * 256));
+  CK(dalloc(&w.sort_hist, 8 * 256));
+  CK(dalloc(&w.sort_tile, 8));
+  return TRILENS_OK;
+}
+
+static int grow(trilens_ctx *c, uint2 **buf, unsigned long long *cap, unsigned long long need) {
+  unsigned long long nc = std::max<unsigned long long>(need + need / 4 + 1024, *cap * 2);
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  CK(dalloc(buf, (size_t)nc));
+  *cap = nc;
+  return TRILENS_OK;
+}
+
+// ---- C ABI
+
+extern "C" {
+
+const char *trilens_version(void) { return "trilens-gb300 0.1 (sm_103a)"; }
+
+const char *trilens_status_str(int code) {
+  switch (code) {
+    case TRILENS_OK: return "ok";
+    case TRILENS_ERR_INVALID: return "invalid argument";
+    case TRILENS_ERR_CAPACITY: return "hit buffer too small";
+    case TRILENS_ERR_CUDA: return "CUDA error";
+    case TRILENS_ERR_TIMEOUT: return "device wait reached its spin limit";
+    case TRILENS_ERR_STACK: return "traversal overflow after retries";
+    case TRILENS_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown status";
+  }
+}
+
+const char *trilens_last_error(trilens_ctx *c) { return c ? c->msg : "no context"; }
+
+static bool beam_ok(const trilens_beam *b) {
+  if (!b || b->n < 0 || b->n >= (1ll << 27)) return false;
+  if (b->n == 0) return true;
+  return b->px && b->py && b->pz && b->dx && b->dy && b->dz && b->E;
+}
+
+void trilens_destroy(trilens_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  free_beam(c->w[0]);
+  free_beam(c->w[1]);
+  cudaFree(c->front[0]);
+  cudaFree(c->front[1]);
+  cudaFree(c->spill[0]);
+  cudaFree(c->spill[1]);
+  cudaFree(c->hits);
+  cudaFree(c->band);
+  cudaFree(c->ctr);
+  cudaFree(c->partials);
+  cudaFree(c->build_status);
+  cudaFree(c->bounds_dev);
+  cudaFreeHost(c->ctr_host);
+  cudaFreeHost(c->build_status_host);
+  for (int ph = 0; ph < 9; ++ph)
+    for (int k = 0; k < 2; ++k)
+      for (int e = 0; e < 2; ++e)
+        if (c->ev[ph][k][e]) cudaEventDestroy(c->ev[ph][k][e]);
+  delete c;
+}
+
+int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam *b,
+                   const trilens_params *p, trilens_stream_t stream) {
+  if (!out) return TRILENS_ERR_INVALID;
+  *out = nullptr;
+  if (!beam_ok(a) || !beam_ok(b) || !p) return TRILENS_ERR_INVALID;
+  if (!(p->dt_fs > 0.0) || !(p->kappa > 0.0) || !isfinite(p->dt_fs) || !isfinite(p->kappa))
+    return TRILENS_ERR_INVALID;
+  if (p->precision != TRILENS_FP64 && p->precision != TRILENS_FP32_BAND) return TRILENS_ERR_INVALID;
+  if (p->leaf_bucket < 0 || p->leaf_bucket > 32) return TRILENS_ERR_INVALID;
+  if (p->stack_depth != 0 && (p->stack_depth < 64 || p->stack_depth > 4096))
+    return TRILENS_ERR_INVALID;
+  if (p->block_shape < 0 || p->block_shape > 16) return TRILENS_ERR_INVALID;
+  if (p->spin_limit < 0) return TRILENS_ERR_INVALID;
+
+  trilens_ctx *c = new trilens_ctx();
+  CK(cudaGetDevice(&c->device));
+  c->stream = (cudaStream_t)stream;
+  c->p = *p;
+  if (c->p.leaf_bucket == 0) c->p.leaf_bucket = 4;
+  if (c->p.stack_depth == 0) c->p.stack_depth = 256;
+  if (c->p.block_shape == 0) c->p.block_shape = 4;
+  if (c->p.spin_limit == 0) c->p.spin_limit = 1ll << 22;
+  const trilens_beam *bs[2] = {a, b};
+  for (int k = 0; k < 2; ++k) {
+    TLBeam &t = c->beam[k];
+    t.n = bs[k]->n;
+    t.px = bs[k]->px; t.py = bs[k]->py; t.pz = bs[k]->pz;
+    t.dx = bs[k]->dx; t.dy = bs[k]->dy; t.dz = bs[k]->dz;
+    t.E = bs[k]->E; t.w = bs[k]->w;
+  }
+  int rc;
+  // constants
+  c->L64 = TL_C * c->p.dt_fs;
+  c->sigma_max = host_sigma_max() * (1.0 + 1e-6);
+  c->rmax = sqrt(1e12 * c->p.kappa * c->sigma_max / TL_PI) * (1.0 + 1e-6);
+  c->L_lo = round_down(c->L64);
+  c->L_hi = round_up(c->L64);
+  c->half = round_up(0.5 * c->rmax * (1.0 + 1e-6) + 1e-9);
+  {
+    const double u = ldexp(1.0, -24);
+    TLNarrowConst &nk = c->nk;
+    nk.L = (float)c->L64;
+    nk.L_in = round_down((double)nk.L * (1.0 - 8.0 * u));
+    nk.L_out = round_up((double)nk.L * (1.0 + 8.0 * u));
+    nk.r2max = round_up(1e12 * c->p.kappa * c->sigma_max * (1.0 + 1e-5) / TL_PI);
+    nk.kr = (float)(1e12 * c->p.kappa / TL_PI);
+    nk.inv2mc4 = (float)(1.0 / (2.0 * TL_MEC2 * TL_MEC2));
+    nk.pref = (float)(0.5 * TL_PI * TL_RE * TL_RE);
+  }
+  // workspace
+  CK(dalloc(&c->bounds_dev, 24));
+  CK(dalloc(&c->build_status, 1));
+  CK(cudaMallocHost((void **)&c->build_status_host, sizeof(unsigned)));
+  CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
+  for (int k = 0; k < 2; ++k) {
+    if ((rc = alloc_beam(c, c->w[k], c->beam[k].n))) {
+      trilens_destroy(c);
+      return rc;
+    }
+    c->w[k].build_status = c->build_status;
+    int64_t n = std::max<int64_t>(c->beam[k].n, 2);
+    int lg = 0;
+    while ((1ll << lg) < n) ++lg;
+    c->bits[k] = std::min(21, std::max(4, (lg + 2) / 3 + 4));
+    c->key_bits[k] = 3 * c->bits[k];
+    // one-time bounds of p0 and d for the Morton box
+    CK(tl::launch_beam_bounds(c->beam[k], c->bounds_dev, c->stream));
+    CK(cudaMemcpyAsync(c->bounds[k], c->bounds_dev, sizeof(double) * 12, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  int dev_sm = 0;
+  CK(cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, c->device));
+  c->n_sm = dev_sm;
+  c->trav_warps = c->p.block_shape;
+  int bps = 0;
+  CK(tl::traverse_config(c->p.precision == TRILENS_FP64, c->trav_warps, c->p.stack_depth, &bps));
+  if (bps < 1) {
+    trilens_destroy(c);
+    return TRILENS_ERR_INVALID;
+  }
+  c->trav_blocks = bps * c->n_sm;
+  c->expand_blocks = 2 * c->n_sm;
+  c->front_target = (unsigned)std::min<long long>(8ll * c->trav_blocks * c->trav_warps, 1 << 22);
+  c->front_cap = 4 * c->front_target + 64;
+  CK(dalloc(&c->front[0], c->front_cap));
+  CK(dalloc(&c->front[1], c->front_cap));
+  c->spill_cap = 1 << 20;
+  CK(dalloc(&c->spill[0], c->spill_cap));
+  CK(dalloc(&c->spill[1], c->spill_cap));
+  c->hit_cap = std::max<unsigned long long>(1 << 16, 2ull * (c->beam[0].n + c->beam[1].n));
+  CK(dalloc(&c->hits, c->hit_cap));
+  c->band_cap = std::max<unsigned long long>(1 << 16, (c->beam[0].n + c->beam[1].n) / 4);
+  CK(dalloc(&c->band, c->band_cap));
+  CK(dalloc(&c->ctr, 1));
+  CK(cudaMallocHost((void **)&c->ctr_host, sizeof(TLCounters)));
+  c->yield_blocks = 4 * c->n_sm;
+  CK(cudaMalloc(&c->partials, tl::partial_bytes() * c->yield_blocks));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = c;
+  return TRILENS_OK;
+}
+
+int trilens_build(trilens_ctx *c, int64_t step) {
+  if (!c) return TRILENS_ERR_INVALID;
+  if (step < 0) return fail(c, TRILENS_ERR_INVALID, "step < 0");
+  CK(cudaSetDevice(c->device));
+  const double ct = TL_C * ((double)step * c->p.dt_fs);
+  const double T = ct + 0.5 * c->L64;
+  for (int k = 0; k < 2; ++k) {
+    const int64_t n = c->beam[k].n;
+    if (n <= 0) continue;
+    float lo[3], scale[3];
+    const double maxq = (double)((1u << c->bits[k]) - 1u);
+    for (int a = 0; a < 3; ++a) {
+      const double *bd = c->bounds[k];
+      double l = bd[a] + T * bd[3 + a];        // min p0 + T min d
+      double h = bd[6 + a] + T * bd[9 + a];    // max p0 + T max d
+      lo[a] = (float)l;
+      scale[a] = h > l ? (float)(maxq / (h - l)) : 0.0f;
+    }
+    tl::BuildBufs &w = c->w[k];
+    tmark(c, PH_PROP, k, 0);
+    CK(tl::launch_propagate(c->beam[k], ct, (float)c->L64, lo, scale, c->bits[k], w, c->stream));
+    tmark(c, PH_PROP, k, 1);
+    CK(cudaMemsetAsync(w.visit, 0, sizeof(uint32_t) * (size_t)n, c->stream));
+    tmark(c, PH_SORT, k, 0);
+    CK(tl::launch_sort(w, n, c->key_bits[k], c->p.spin_limit, c->debug_stall_sort,
+                       c->build_status, &c->sel[k], c->stream));
+    tmark(c, PH_SORT, k, 1);
+    tmark(c, PH_GATHER, k, 0);
+    CK(tl::launch_gather(w, n, c->sel[k], c->stream));
+    tmark(c, PH_GATHER, k, 1);
+    tmark(c, PH_EMIT, k, 0);
+    CK(tl::launch_karras(w, n, c->sel[k], c->p.leaf_bucket, c->stream));
+    tmark(c, PH_EMIT, k, 1);
+    tmark(c, PH_REFIT, k, 0);
+    CK(tl::launch_refit(w, n, c->L_lo, c->L_hi, c->half, c->stream));
+    tmark(c, PH_REFIT, k, 1);
+    c->phase_launches[PH_PROP] += 1;
+    c->phase_launches[PH_SORT] += n > 1 ? 2 + (c->key_bits[k] + 7) / 8 : 0;
+    c->phase_launches[PH_GATHER] += 1;
+    c->phase_launches[PH_EMIT] += 1;
+    c->phase_launches[PH_REFIT] += 1;
+  }
+  c->built_step = step;
+  return TRILENS_OK;
+}
+
+static tl::TravArgs trav_args(trilens_ctx *c, double ct) {
+  tl::TravArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int k = 0; k < 2; ++k) {
+    TLTree &t = k ? a.B : a.A;
+    t.pos = c->w[k].pos;
+    t.dir = c->w[k].dir;
+    t.nodes = c->w[k].nodes;
+    t.n = c->beam[k].n;
+    t.super = (uint32_t)(t.n > 1 ? t.n - 1 : 0);
+  }
+  a.mA = c->beam[0];
+  a.mB = c->beam[1];
+  a.ct = ct;
+  a.dt = c->p.dt_fs;
+  a.kappa = c->p.kappa;
+  a.nk = c->nk;
+  a.fp64 = c->p.precision == TRILENS_FP64;
+  a.ctr = c->ctr;
+  a.hits = c->hits;
+  a.hit_cap = c->hit_cap;
+  a.band = c->band;
+  a.band_cap = c->band_cap;
+  a.spill = c->spill[0];
+  a.spill_cap = c->spill_cap;
+  a.stack_depth = c->p.stack_depth;
+  a.build_status = c->build_status;
+  return a;
+}
+
+int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t cap,
+                         int64_t *n_hits) {
+  if (!c) return TRILENS_ERR_INVALID;
+  if (step != c->built_step) return fail(c, TRILENS_ERR_INVALID, "step %lld not built", (long long)step);
+  if (cap < 0 || (hits == nullptr && cap > 0)) return fail(c, TRILENS_ERR_INVALID, "bad hit buffer");
+  CK(cudaSetDevice(c->device));
+  const double ct = TL_C * ((double)step * c->p.dt_fs);
+  const int nonempty = c->beam[0].n > 0 && c->beam[1].n > 0;
+  int retries = 0;
+  TLCounters &h = *c->ctr_host;
+  while (true) {
+    tl::TravArgs a = trav_args(c, ct);
+    tmark(c, PH_EXPAND, 0, 0);
+    CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super, nonempty, c->build_status,
+                            c->stream));
+    for (int lvl = 0; lvl < kMaxLevels; ++lvl)
+      CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, lvl,
+                           c->expand_blocks, c->stream));
+    tmark(c, PH_EXPAND, 0, 1);
+    c->phase_launches[PH_EXPAND] += 1 + kMaxLevels;
+    tmark(c, PH_TRAV, 0, 0);
+    CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->trav_blocks,
+                           c->trav_warps, c->stream));
+    tmark(c, PH_TRAV, 0, 1);
+    c->phase_launches[PH_TRAV] += 1;
+    CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int sp = 0, passes = 0;
+    while (h.spill > 0 && !(h.status & TL_ST_SPILL_OVF) && passes < 64) {
+      // descend the pairs that did not fit on a stack, writing new overflow
+      // to the other spill list
+      const unsigned long long nlist = h.spill;
+      tl::TravArgs a2 = a;
+      a2.spill = c->spill[sp ^ 1];
+      CK(cudaMemsetAsync(&c->ctr->spill, 0, sizeof(unsigned long long), c->stream));
+      CK(cudaMemsetAsync(&c->ctr->cursor, 0, sizeof(unsigned), c->stream));
+      tmark(c, PH_TRAV, 1, 0);
+      CK(tl::launch_traverse(a2, c->front[0], c->front[1], c->spill[sp], nlist, 0, c->trav_blocks,
+                             c->trav_warps, c->stream));
+      tmark(c, PH_TRAV, 1, 1);
+      c->phase_launches[PH_TRAV] += 1;
+      CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      tcollect(c);
+      sp ^= 1;
+      ++passes;
+    }
+    if (h.spill > 0 && !(h.status & TL_ST_SPILL_OVF))
+      return fail(c, TRILENS_ERR_STACK, "traversal still overflowing after %d passes", passes);
+    if (!a.fp64) {
+      tmark(c, PH_BAND, 0, 0);
+      CK(tl::launch_band(a, c->n_sm * 4, c->stream));
+      tmark(c, PH_BAND, 0, 1);
+      c->phase_launches[PH_BAND] += 1;
+    }
+    tmark(c, PH_YIELD, 0, 0);
+    CK(tl::launch_yield(a, c->partials, c->yield_blocks, c->stream));
+    tmark(c, PH_YIELD, 0, 1);
+    c->phase_launches[PH_YIELD] += 1;
+    CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->build_status_host, c->build_status, sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    tcollect(c);
+    const unsigned st = h.status | *c->build_status_host;
+    if (st & TL_ST_TIMEOUT) {
+      CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit=%lld",
+                  (long long)c->p.spin_limit);
+    }
+    bool again = false;
+    int rc;
+    if (st & TL_ST_BAND_OVF) {
+      if ((rc = grow(c, &c->band, &c->band_cap, h.band))) return rc;
+      again = true;
+    }
+    if (st & TL_ST_HIT_OVF) {
+      if ((rc = grow(c, &c->hits, &c->hit_cap, h.hits + (again ? h.band : 0)))) return rc;
+      again = true;
+    }
+    if (st & TL_ST_SPILL_OVF) {
+      cudaFree(c->spill[1]);
+      c->spill[1] = nullptr;
+      unsigned long long cap = c->spill_cap;
+      if ((rc = grow(c, &c->spill[0], &cap, std::max(h.spill, c->spill_cap * 2)))) return rc;
+      CK(dalloc(&c->spill[1], cap));
+      c->spill_cap = cap;
+      again = true;
+    }
+    if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
+    if (!again) break;
+    if (++retries > 8) return fail(c, TRILENS_ERR_STACK, "buffers kept overflowing");
+  }
+  trilens_step_stats &s = c->last;
+  s.step = step;
+  s.count = (int64_t)h.count;
+  s.weighted = h.weighted;
+  s.hsum = h.hsum;
+  s.hxor = h.hxor;
+  s.narrow_tests = (int64_t)h.narrow_tests;
+  s.node_tests = (int64_t)h.node_tests;
+  s.leaf_pairs = (int64_t)h.leaf_pairs;
+  s.band = (int64_t)h.band;
+  s.retries = retries;
+  c->tot_count += (double)h.count;
+  c->tot_weighted += h.weighted;
+  if (n_hits) *n_hits = (int64_t)h.count;
+  if (hits && cap > 0) {
+    const unsigned long long ncopy = std::min<unsigned long long>(h.count, (unsigned long long)cap);
+    if (ncopy)
+      CK(cudaMemcpyAsync(hits, c->hits, sizeof(uint2) * ncopy, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (hits && (int64_t)h.count > cap)
+    return fail(c, TRILENS_ERR_CAPACITY, "need %llu hit slots", (unsigned long long)h.count);
+  return TRILENS_OK;
+}
+
+int trilens_step_stats_get(trilens_ctx *c, trilens_step_stats *out) {
+  if (!c || !out) return TRILENS_ERR_INVALID;
+  *out = c->last;
+  return TRILENS_OK;
+}
+
+int trilens_yield(trilens_ctx *c, int32_t mode, int32_t level_L, double *count,
+                  double *weighted) {
+  (void)level_L;
+  if (!c || !count || !weighted) return TRILENS_ERR_INVALID;
+  if (mode != TRILENS_YIELD_EXACT) return fail(c, TRILENS_ERR_INVALID, "yield mode %d", mode);
+  *count = c->tot_count;
+  *weighted = c->tot_weighted;
+  return TRILENS_OK;
+}
+
+int trilens_reset_yield(trilens_ctx *c) {
+  if (!c) return TRILENS_ERR_INVALID;
+  c->tot_count = 0;
+  c->tot_weighted = 0;
+  return TRILENS_OK;
+}
+
+// Test hook (not in the public header): make the first tile of the next
+// builds' first sort pass withhold its published counts so that the next tile's
+// bounded wait expires.  Used to check that an expired wait becomes
+// TRILENS_ERR_TIMEOUT instead of a hang.
+int trilens_debug_stall_sort(trilens_ctx *c, int on) {
+  if (!c) return TRILENS_ERR_INVALID;
+  c->debug_stall_sort = on;
+  return TRILENS_OK;
+}
+
+int trilens_debug_timing(trilens_ctx *c, int on) {
+  if (!c) return TRILENS_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  if (on && !c->ev[0][0][0])
+    for (int ph = 0; ph < 9; ++ph)
+      for (int k = 0; k < 2; ++k)
+        for (int e = 0; e < 2; ++e) CK(cudaEventCreate(&c->ev[ph][k][e]));
+  c->timing = on ? 1 : 0;
+  return TRILENS_OK;
+}
+
+int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int reset) {
+  if (!c) return TRILENS_ERR_INVALID;
+  for (int ph = 0; ph < 9; ++ph) {
+    if (out) out[ph] = c->phase_ms[ph];
+    if (launches) launches[ph] = c->phase_launches[ph];
+    if (reset) {
+      c->phase_ms[ph] = 0.0;
+      c->phase_launches[ph] = 0;
+    }
+  }
+  return TRILENS_OK;
+}
+
+int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit) {
+  if (!c || limit < 1) return TRILENS_ERR_INVALID;
+  c->p.spin_limit = limit;
+  return TRILENS_OK;
+}
+
+}  // extern "C"

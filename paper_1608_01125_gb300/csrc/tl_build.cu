@@ -1,0 +1,329 @@
+// tl_build.cu -- per-step hierarchy build for one beam.
+//
+//   propagate   positions in closed form (FP64), FP32 SoA, Morton key of the
+//               swept box's centre (one pass over the FP64 input)
+//   gather      SoA into Morton order
+//   karras      inner nodes of the binary radix tree over the sorted keys
+//               (Karras 2012, "Maximizing parallelism in the construction of
+//               BVHs, octrees and k-d trees"), leaf buckets of <= B photons
+//   refit       bottom-up union of swept boxes (Sec. 2.1: each box covers the
+//               travel of its photons during the step), one atomic arrival
+//               counter per node, no waiting
+#include "tl_common.cuh"
+
+namespace tl {
+
+// ---------------------------------------------------------------- bounds
+
+__device__ __forceinline__ long long ord64(double x) {
+  long long i = __double_as_longlong(x);
+  return i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
+}
+
+// min and max over the beam of p0 and d per axis (12 ordered int64s:
+// min px py pz dx dy dz, then max ...).  Used only to pick the Morton
+// quantisation box; no result depends on it.
+__global__ void k_beam_bounds(TLBeam b, long long *out) {
+  long long mn[6], mx[6];
+  for (int c = 0; c < 6; ++c) {
+    mn[c] = 0x7fffffffffffffffLL;
+    mx[c] = -0x7fffffffffffffffLL - 1;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[6] = {b.px[i], b.py[i], b.pz[i], b.dx[i], b.dy[i], b.dz[i]};
+    for (int c = 0; c < 6; ++c) {
+      long long o = ord64(v[c]);
+      mn[c] = min(mn[c], o);
+      mx[c] = max(mx[c], o);
+    }
+  }
+  for (int c = 0; c < 6; ++c) {
+    for (int off = 16; off; off >>= 1) {
+      mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
+      mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int c = 0; c < 6; ++c) {
+      atomicMin(&out[c], mn[c]);
+      atomicMax(&out[6 + c], mx[c]);
+    }
+  }
+}
+
+__global__ void k_bounds_init(long long *out) {
+  int c = threadIdx.x;
+  if (c < 6) out[c] = 0x7fffffffffffffffLL;
+  else if (c < 12) out[c] = -0x7fffffffffffffffLL - 1;
+}
+
+__global__ void k_bounds_decode(const long long *in, double *out) {
+  int c = threadIdx.x;
+  if (c < 12) {
+    long long i = in[c];
+    i = i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
+    out[c] = __longlong_as_double(i);
+  }
+}
+
+cudaError_t launch_beam_bounds(const TLBeam &b, double *out12, cudaStream_t s) {
+  // out12 is device memory of 24 doubles: the first 12 receive the result,
+  // the last 12 are scratch for the ordered integers
+  long long *tmp = reinterpret_cast<long long *>(out12 + 12);
+  k_bounds_init<<<1, 32, 0, s>>>(tmp);
+  if (b.n > 0) {
+    int64_t nb = (b.n + 255) / 256;
+    int blocks = (int)(nb < 1024 ? nb : 1024);
+    k_beam_bounds<<<blocks, 256, 0, s>>>(b, tmp);
+  }
+  k_bounds_decode<<<1, 32, 0, s>>>(tmp, out12);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Morton
+
+// spread the low 21 bits of x to every third bit (bit interleaving by masks)
+__device__ __forceinline__ unsigned long long spread3(unsigned long long x) {
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ unsigned quant(float c, float lo, float scale, unsigned maxq) {
+  float f = (c - lo) * scale;
+  f = fminf(fmaxf(f, 0.0f), (float)maxq);
+  return (unsigned)f;
+}
+
+// One thread per photon: P = p0 + (c t_k) d in FP64 (the definition's
+// operation order), rounded to the FP32 SoA; key of the swept segment's
+// centre P + (L/2) d quantised in the beam's box.
+__global__ void __launch_bounds__(256) k_propagate(TLBeam b, double ct, float halfL, float3 lo,
+                                                   float3 scale, unsigned maxq, float4 *pos_u,
+                                                   float4 *dir_u, unsigned long long *key,
+                                                   uint32_t *val) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= b.n) return;
+  const double dx = b.dx[i], dy = b.dy[i], dz = b.dz[i];
+  const double Px = __dadd_rn(b.px[i], __dmul_rn(ct, dx));
+  const double Py = __dadd_rn(b.py[i], __dmul_rn(ct, dy));
+  const double Pz = __dadd_rn(b.pz[i], __dmul_rn(ct, dz));
+  float4 p = make_float4(__double2float_rn(Px), __double2float_rn(Py), __double2float_rn(Pz),
+                         __double2float_rn(b.E[i]));
+  float4 d = make_float4(__double2float_rn(dx), __double2float_rn(dy), __double2float_rn(dz),
+                         __int_as_float((int)i));
+  pos_u[i] = p;
+  dir_u[i] = d;
+  const float cx = fmaf(halfL, d.x, p.x), cy = fmaf(halfL, d.y, p.y), cz = fmaf(halfL, d.z, p.z);
+  const unsigned qx = quant(cx, lo.x, scale.x, maxq), qy = quant(cy, lo.y, scale.y, maxq),
+                 qz = quant(cz, lo.z, scale.z, maxq);
+  key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+  val[i] = (uint32_t)i;
+}
+
+cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
+                             const float box_scale[3], int bits, BuildBufs &w, cudaStream_t s) {
+  if (b.n <= 0) return cudaSuccess;
+  unsigned maxq = (1u << bits) - 1u;
+  int blocks = (int)((b.n + 255) / 256);
+  k_propagate<<<blocks, 256, 0, s>>>(b, ct, 0.5f * L, make_float3(box_lo[0], box_lo[1], box_lo[2]),
+                                     make_float3(box_scale[0], box_scale[1], box_scale[2]), maxq,
+                                     w.pos_u, w.dir_u, w.key[0], w.val[0]);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- gather
+
+__global__ void __launch_bounds__(256) k_gather(int64_t n, const uint32_t *__restrict__ val,
+                                                const float4 *__restrict__ pos_u,
+                                                const float4 *__restrict__ dir_u,
+                                                float4 *__restrict__ pos, float4 *__restrict__ dir,
+                                                const unsigned *build_status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n || (*build_status & TL_ST_TIMEOUT)) return;
+  uint32_t src = val[i];
+  pos[i] = pos_u[src];
+  dir[i] = dir_u[src];
+}
+
+cudaError_t launch_gather(BuildBufs &w, int64_t n, int sel, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather<<<(int)((n + 255) / 256), 256, 0, s>>>(n, w.val[sel], w.pos_u, w.dir_u, w.pos, w.dir,
+                                                  w.build_status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Karras
+
+// common prefix length of sorted keys i and j; equal keys fall back to the
+// indices (so every key is distinct); -1 outside [0, n)
+__device__ __forceinline__ int kdelta(const unsigned long long *__restrict__ key, int64_t n,
+                                      int64_t i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  unsigned long long a = key[i], b = key[j];
+  if (a != b) return __clzll((long long)(a ^ b));
+  return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+__device__ __forceinline__ void empty_box(float4 &b1, float4 &b2) {
+  // box 1 of the super root: lo = +inf, hi = -inf never overlaps
+  const float inf = __int_as_float(0x7f800000);
+  b1.z = inf;
+  b1.w = inf;
+  b2 = make_float4(inf, -inf, -inf, -inf);
+}
+
+__global__ void __launch_bounds__(256) k_karras(const unsigned long long *__restrict__ key,
+                                                int64_t n, int bucket, TLNode *nodes,
+                                                uint32_t *parent_leaf, uint32_t *parent_node,
+                                                const unsigned *build_status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (*build_status & TL_ST_TIMEOUT) return;  // keys unsorted: the build is abandoned
+  const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
+  if (i == 0) {
+    // the super root: one child (the whole beam) in slot 0, slot 1 empty
+    TLNode sr;
+    sr.b0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    sr.b1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    empty_box(sr.b1, sr.b2);
+    int ref0 = (n <= bucket) ? (int)(TL_FLAG | 0u) : 0;
+    sr.c = make_int4(ref0, (int)TL_NONE, (int)n, 0);
+    // boxes are written by the refit; write refs and the empty slot now
+    nodes[super] = sr;
+    if (n > 1) parent_node[0] = (super << 1) | 0u;
+    else parent_leaf[0] = (super << 1) | 0u;
+  }
+  if (i >= n - 1) return;
+  int dl = kdelta(key, n, i, i - 1), dr = kdelta(key, n, i, i + 1);
+  int64_t d = dr > dl ? 1 : -1;
+  int dmin = dr > dl ? dl : dr;
+  int64_t lmax = 2;
+  while (kdelta(key, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int64_t l = 0;
+  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+    if (kdelta(key, n, i, i + (l + t) * d) > dmin) l += t;
+  int64_t j = i + l * d;
+  int dnode = kdelta(key, n, i, j);
+  int64_t s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (kdelta(key, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+  int64_t first = i < j ? i : j, last = i < j ? j : i;
+  int64_t cl = gamma - first + 1, cr = last - gamma;
+  int refl = cl <= bucket ? (int)(TL_FLAG | (uint32_t)first) : (int)gamma;
+  int refr = cr <= bucket ? (int)(TL_FLAG | (uint32_t)(gamma + 1)) : (int)(gamma + 1);
+  nodes[i].c = make_int4(refl, refr, (int)cl, (int)cr);
+  if (first == gamma) parent_leaf[gamma] = ((uint32_t)i << 1) | 0u;
+  else parent_node[gamma] = ((uint32_t)i << 1) | 0u;
+  if (last == gamma + 1) parent_leaf[gamma + 1] = ((uint32_t)i << 1) | 1u;
+  else parent_node[gamma + 1] = ((uint32_t)i << 1) | 1u;
+}
+
+cudaError_t launch_karras(BuildBufs &w, int64_t n, int sel, int bucket, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int64_t threads = n > 1 ? n - 1 : 1;
+  k_karras<<<(int)((threads + 255) / 256), 256, 0, s>>>(w.key[sel], n, bucket, w.nodes,
+                                                        w.parent_leaf, w.parent_node,
+                                                        w.build_status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- refit
+
+// Swept box of one photon in FP32 interval arithmetic with directed
+// rounding.  The FP64 position of the definition lies within |P32| 2^-23 of
+// P32 (and likewise the direction), the segment is P + lambda L d for
+// lambda in [0, 1] with L in [L_lo, L_hi], and half = r_max / 2 plus margin.
+__device__ __forceinline__ void seg_axis(float p, float dc, float Llo, float Lhi, float half,
+                                         float &lo, float &hi) {
+  const float ep = __fmaf_ru(fabsf(p), 1.1920928955078125e-7f, 1e-30f);
+  const float plo = __fsub_rd(p, ep), phi = __fadd_ru(p, ep);
+  const float ed = __fmaf_ru(fabsf(dc), 1.1920928955078125e-7f, 1e-30f);
+  const float dlo = __fsub_rd(dc, ed), dhi = __fadd_ru(dc, ed);
+  const float ldlo = dlo >= 0.f ? __fmul_rd(Llo, dlo) : __fmul_rd(Lhi, dlo);
+  const float ldhi = dhi >= 0.f ? __fmul_ru(Lhi, dhi) : __fmul_ru(Llo, dhi);
+  const float qlo = __fadd_rd(plo, ldlo), qhi = __fadd_ru(phi, ldhi);
+  lo = __fsub_rd(fminf(plo, qlo), half);
+  hi = __fadd_ru(fmaxf(phi, qhi), half);
+}
+
+__device__ __forceinline__ void write_slot(TLNode *nodes, uint32_t node, uint32_t slot,
+                                           const TLBox &b) {
+  float *f = reinterpret_cast<float *>(&nodes[node]);
+  float *o = f + (slot ? 6 : 0);
+  __stcg(o + 0, b.lx);
+  __stcg(o + 1, b.ly);
+  __stcg(o + 2, b.lz);
+  __stcg(o + 3, b.hx);
+  __stcg(o + 4, b.hy);
+  __stcg(o + 5, b.hz);
+}
+
+__device__ __forceinline__ TLBox read_slot(const TLNode *nodes, uint32_t node, uint32_t slot) {
+  const float *f = reinterpret_cast<const float *>(&nodes[node]) + (slot ? 6 : 0);
+  TLBox b;
+  b.lx = __ldcg(f + 0);
+  b.ly = __ldcg(f + 1);
+  b.lz = __ldcg(f + 2);
+  b.hx = __ldcg(f + 3);
+  b.hy = __ldcg(f + 4);
+  b.hz = __ldcg(f + 5);
+  return b;
+}
+
+__global__ void __launch_bounds__(256) k_refit(int64_t n, const float4 *__restrict__ pos,
+                                               const float4 *__restrict__ dir, float Llo, float Lhi,
+                                               float half, TLNode *nodes,
+                                               const uint32_t *__restrict__ parent_leaf,
+                                               const uint32_t *__restrict__ parent_node,
+                                               uint32_t *visit, unsigned *build_status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n || (*build_status & TL_ST_TIMEOUT)) return;
+  const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
+  const float4 p = pos[i], d = dir[i];
+  TLBox b;
+  seg_axis(p.x, d.x, Llo, Lhi, half, b.lx, b.hx);
+  seg_axis(p.y, d.y, Llo, Lhi, half, b.ly, b.hy);
+  seg_axis(p.z, d.z, Llo, Lhi, half, b.lz, b.hz);
+  uint32_t ref = parent_leaf[i];
+  // a valid hierarchy is at most 64 + 27 levels deep; the bound and the index
+  // check only guard against a corrupted one
+  for (int depth = 0;; ++depth) {
+    const uint32_t node = ref >> 1, slot = ref & 1u;
+    if (node > super || depth > 160) {
+      atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+      return;
+    }
+    write_slot(nodes, node, slot, b);
+    if (node == super) return;
+    __threadfence();
+    if (atomicAdd(&visit[node], 1u) == 0u) return;  // the sibling finishes this node
+    __threadfence();
+    const TLBox o = read_slot(nodes, node, slot ^ 1u);
+    b.lx = fminf(b.lx, o.lx);
+    b.ly = fminf(b.ly, o.ly);
+    b.lz = fminf(b.lz, o.lz);
+    b.hx = fmaxf(b.hx, o.hx);
+    b.hy = fmaxf(b.hy, o.hy);
+    b.hz = fmaxf(b.hz, o.hz);
+    ref = parent_node[node];
+  }
+}
+
+cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float half,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_refit<<<(int)((n + 255) / 256), 256, 0, s>>>(n, w.pos, w.dir, Llo, Lhi, half, w.nodes,
+                                                 w.parent_leaf, w.parent_node, w.visit,
+                                                 w.build_status);
+  return cudaGetLastError();
+}
+
+}  // namespace tl

@@ -1,0 +1,156 @@
+// tl_common.cuh -- types shared by the library's CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define TL_C 0.299792458            /* um / fs, exact */
+#define TL_RE 2.8179403262e-15      /* classical electron radius [m], CODATA 2018 */
+#define TL_MEC2 0.51099895000       /* electron rest energy [MeV], CODATA 2018 */
+#define TL_PI 3.14159265358979323846
+
+// Child / stack references.  Bit 31 clear: an inner node index.  Bit 31 set:
+// in a node's child slot, FLAG | first photon of a leaf bucket; on a stack,
+// FLAG | (parent << 1 | slot) naming the bucket through its parent's slot.
+#define TL_FLAG 0x80000000u
+#define TL_NONE 0xFFFFFFFFu
+
+// One inner node of a hierarchy: the boxes of both children (box 0 in
+// b0.xyz/b0.w,b1.xy; box 1 in b1.zw,b2), child references and the photon
+// count under each child.  64 bytes, one line pair per pop.
+struct __align__(16) TLNode {
+  float4 b0;  // lo0.x lo0.y lo0.z hi0.x
+  float4 b1;  // hi0.y hi0.z lo1.x lo1.y
+  float4 b2;  // lo1.z hi1.x hi1.y hi1.z
+  int4 c;     // child0 child1 cnt0 cnt1
+};
+
+struct TLBox {
+  float lx, ly, lz, hx, hy, hz;
+};
+
+__device__ __forceinline__ TLBox tl_child_box(const TLNode &n, int slot) {
+  TLBox b;
+  if (slot == 0) {
+    b.lx = n.b0.x; b.ly = n.b0.y; b.lz = n.b0.z; b.hx = n.b0.w; b.hy = n.b1.x; b.hz = n.b1.y;
+  } else {
+    b.lx = n.b1.z; b.ly = n.b1.w; b.lz = n.b2.x; b.hx = n.b2.y; b.hy = n.b2.z; b.hz = n.b2.w;
+  }
+  return b;
+}
+
+// Eq. CollDet with closed boxes: the symmetric six comparisons.
+__device__ __forceinline__ bool tl_overlap(const TLBox &a, const TLBox &b) {
+  return a.lx <= b.hx && b.lx <= a.hx && a.ly <= b.hy && b.ly <= a.hy && a.lz <= b.hz &&
+         b.lz <= a.hz;
+}
+
+// device status bits (OR-ed into TLCounters::status)
+enum {
+  TL_ST_HIT_OVF = 1,
+  TL_ST_BAND_OVF = 2,
+  TL_ST_SPILL_OVF = 4,
+  TL_ST_FRONT_OVF = 8,
+  TL_ST_TIMEOUT = 16,
+  TL_ST_LEAFQ = 32
+};
+
+// Per-step device counters; zeroed by the step's init kernel.
+struct TLCounters {
+  unsigned long long hits;         // colliding pairs found (may exceed capacity)
+  unsigned long long band;         // FP32 band pairs queued for FP64
+  unsigned long long spill;        // stack overflow pairs written to the spill list
+  unsigned long long narrow_tests; // photon pairs tested
+  unsigned long long node_tests;   // box pair tests
+  unsigned long long leaf_pairs;   // overlapping bucket pairs
+  unsigned int counts[32];         // frontier size after each expansion level
+  unsigned int frozen;             // frontier expansion finished
+  unsigned int final_level;        // level whose frontier the traversal reads
+  unsigned int cursor;             // traversal work cursor
+  unsigned int status;             // TL_ST_* bits
+  unsigned int reduce_done;        // blocks finished in the yield reduction
+  unsigned int pad[3];
+  // results of the yield reduction for this step
+  unsigned long long count;
+  double weighted;
+  unsigned long long hsum, hxor;
+};
+
+// Cumulative totals across steps.
+struct TLTotals {
+  double count;
+  double weighted;
+  unsigned long long steps;
+  unsigned long long pad;
+};
+
+// FP64 input beam on the device.
+struct TLBeam {
+  const double *px, *py, *pz, *dx, *dy, *dz, *E, *w;
+  int64_t n;
+};
+
+// Per-beam hierarchy produced by the build.
+struct TLTree {
+  const float4 *pos;    // sorted: x y z E (FP32)
+  const float4 *dir;    // sorted: dx dy dz, w = input index (int bits)
+  const TLNode *nodes;  // n - 1 inner nodes, then the super root at index n - 1
+  uint32_t super;       // index of the super root (max(n - 1, 0))
+  int64_t n;
+};
+
+// Conservative constants of the FP32 narrow phase (see tl_narrow.cuh).
+struct TLNarrowConst {
+  float L;        // c dt [um], rounded to nearest
+  float L_in;     // L (1 - 8u): t* surely inside when tau + err < L_in
+  float L_out;    // L (1 + 8u): surely outside when tau - err >= L_out
+  float r2max;    // upper bound on r^2 over all s [um^2]
+  float kr;       // 1e12 kappa / pi in FP32
+  float inv2mc4;  // 1 / (2 m_e^2 c^4) [MeV^-2]
+  float pref;     // (pi/2) r_e^2 [m^2]
+};
+
+// Build-time launch helpers (defined in the .cu files).
+namespace tl {
+struct BuildBufs {
+  float4 *pos_u, *dir_u;      // unsorted SoA32
+  float4 *pos, *dir;          // sorted SoA32
+  unsigned long long *key[2];
+  uint32_t *val[2];
+  TLNode *nodes;
+  uint32_t *parent_leaf, *parent_node;
+  uint32_t *visit;
+  // sort scratch
+  uint32_t *sort_status;  // tiles * 256 per pass
+  uint32_t *sort_hist;    // 8 * 256 global digit counts
+  uint32_t *sort_tile;    // 8 tile counters
+  int64_t sort_tiles;
+  unsigned *build_status;  // shared status word of the context's builds
+};
+
+// Arguments of the traversal kernels (tl_traverse.cu).
+struct TravArgs {
+  TLTree A, B;        // FP32 hierarchies
+  TLBeam mA, mB;      // FP64 input beams
+  double ct, dt, kappa;
+  TLNarrowConst nk;
+  int fp64;           // 1: every photon pair decided by the FP64 definition
+  TLCounters *ctr;
+  uint2 *hits;
+  unsigned long long hit_cap;
+  uint2 *band;
+  unsigned long long band_cap;
+  uint2 *spill;
+  unsigned long long spill_cap;
+  int stack_depth;
+  const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal
+};
+
+cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
+                             const float box_scale[3], int bits, BuildBufs &w, cudaStream_t s);
+cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
+                        int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s);
+cudaError_t launch_gather(BuildBufs &w, int64_t n, int sel, cudaStream_t s);
+cudaError_t launch_karras(BuildBufs &w, int64_t n, int sel, int bucket, cudaStream_t s);
+cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float half, cudaStream_t s);
+cudaError_t launch_beam_bounds(const TLBeam &b, double *out12, cudaStream_t s);
+}  // namespace tl

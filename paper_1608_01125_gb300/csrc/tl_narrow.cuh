@@ -1,0 +1,94 @@
+// tl_narrow.cuh -- FP32 narrow phase with a rigorous error band.
+//
+// For a photon pair the FP32 path computes the same quantities as the FP64
+// definition (tl_exact.cuh) -- s, the closest-approach parameter
+// tau = c t* = -(dP . dD)/|dD|^2 with dD = d_i - d_j, the offset
+// q = dP + tau dD, d^2 = |q|^2 and r^2 = 1e12 kappa sigma(s)/pi -- together
+// with bounds on how far each FP32 value can be from the FP64 one.  It
+// returns a decision only when the bound puts the pair on one side of every
+// test; otherwise the pair goes to the FP64 re-test.  So the FP32 path
+// returns exactly the FP64 hit set.
+//
+// Error model (u = 2^-24, first order, then every bound doubled so that
+// second-order terms, the rounding of the bound's own evaluation and the FP64
+// definition's ~1e-16 relative error are covered):
+//   inputs  P32 = P64 (1+e), |e| <= u per coordinate; d32, E32 likewise
+//   dP      |d dP|  <= 2u SA,           SA = sum_c |Pa_c| + |Pb_c|
+//   dD      |d dD|  <= 4u
+//   q       |dq|    <= 2u SA + 4u (|q|/|dD| + |tau|) + 7.02u |tau||dD| + 4.01u |q|
+//   d^2     |d d2|  <= 2|q| dq + dq^2 + 3.01u d2
+//   tau     |dtau|  <= 2u SA/|dD| + 4u |q|/|dD|^2 + 12u |tau|/|dD| + 7.02u |tau| + 3.01u |q|/|dD|
+//   s       |ds|    <= 9u s + 6u E_i E_j / (2 m^2 c^4)   (cos error <= 5u absolute)
+//   sigma   relative: evaluation terms (logf within 1 ulp, sqrtf and the
+//           divisions correctly rounded) plus |g(s)| ds/s with the
+//           logarithmic slope |g| = |s sigma'/sigma| <= s/(s-1) + 1.
+#pragma once
+#include "tl_common.cuh"
+
+enum { TL_MISS = 0, TL_HIT = 1, TL_BAND = 2 };
+
+__device__ __forceinline__ int tl_narrow32(const float4 pa, const float4 da, const float4 pb,
+                                           const float4 db, const TLNarrowConst &k) {
+  const float u = 5.9604644775390625e-8f;  // 2^-24
+  // --- threshold (Eq. eq.Cond) -------------------------------------------
+  const float cs = fmaf(da.x, db.x, fmaf(da.y, db.y, da.z * db.z));
+  const float omc = 1.0f - cs;
+  const float eek = (pa.w * pb.w) * k.inv2mc4;
+  const float s = eek * omc;
+  const float es = 2.0f * (9.0f * u * s + 6.0f * u * eek);
+  const float thr = 9.5367431640625e-7f;  // 2^-20
+  if (s + es <= 1.0f - thr) return TL_MISS;  // surely s64 <= 1 (covers parallel pairs)
+  const bool above = (s - es) >= 1.0f + thr;
+
+  // --- closest approach -----------------------------------------------------
+  const float dpx = pa.x - pb.x, dpy = pa.y - pb.y, dpz = pa.z - pb.z;
+  const float ddx = da.x - db.x, ddy = da.y - db.y, ddz = da.z - db.z;
+  const float dd = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+  if (!(dd > 1e-20f)) return TL_BAND;  // nearly parallel yet maybe above threshold
+  const float pd = fmaf(dpx, ddx, fmaf(dpy, ddy, dpz * ddz));
+  const float rdd = __frcp_rn(dd);
+  const float tau = -pd * rdd;
+  const float qx = fmaf(tau, ddx, dpx), qy = fmaf(tau, ddy, dpy), qz = fmaf(tau, ddz, dpz);
+  const float d2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+
+  const float SA = (fabsf(pa.x) + fabsf(pb.x)) + (fabsf(pa.y) + fabsf(pb.y)) +
+                   (fabsf(pa.z) + fabsf(pb.z));
+  const float nq = sqrtf(d2);
+  const float nd = sqrtf(dd);
+  const float rnd = 1.0f / nd;
+  const float at = fabsf(tau);
+  const float dq =
+      2.0f * (2.0f * u * SA + 4.0f * u * (nq * rnd + at) + 7.1f * u * at * nd + 4.1f * u * nq);
+  const float ed2 = 2.0f * nq * dq + dq * dq + 2.0f * 3.1f * u * d2;
+  const float et = 2.0f * (2.0f * u * SA * rnd + 4.0f * u * nq * rdd + 12.0f * u * at * rnd +
+                           7.1f * u * at + 3.1f * u * nq * rnd);
+
+  // window 0 <= t* < dt (half open)
+  if (tau + et < 0.0f || tau - et >= k.L_out) return TL_MISS;
+  const bool win_in = (tau - et > 0.0f) && (tau + et < k.L_in);
+  // farther than the largest radius of any s
+  if (d2 - ed2 >= k.r2max) return TL_MISS;
+  if (!above) return TL_BAND;  // too close to threshold for the FP32 sigma
+
+  // --- sigma(s) (Eq. BWcross) in FP32 with its bound -------------------------
+  const float inv = 1.0f / s;
+  const float b2 = (s - 1.0f) * inv;
+  const float b = sqrtf(b2);
+  const float opb = 1.0f + b;
+  const float lg = logf((opb * opb) * s);
+  const float t1 = (3.0f - b2 * b2) * lg;
+  const float t2 = (2.0f * b) * (2.0f - b2);
+  const float br = t1 - t2;
+  const float sig = (k.pref * inv) * br;
+  const float ebr = 6.0f * u * fabsf(t1) + 27.0f * u + 6.0f * u * fabsf(lg) +
+                    8.5f * u * fabsf(t2) + u * fabsf(br);
+  const float sm1 = s - es - 1.0f;  // lower bound of s - 1 (> 0 here)
+  const float xs = es / sm1;        // relative size of the s error near threshold
+  if (!(xs < 0.5f) || !(br > 0.0f)) return TL_BAND;
+  const float g = s / sm1 + 1.0f;
+  const float er = 2.0f * (ebr / br + 5.0f * u + g * (es / s));
+  const float r2 = sig * k.kr;
+  if (d2 - ed2 >= r2 * (1.0f + er)) return TL_MISS;
+  if (win_in && d2 + ed2 < r2 * (1.0f - er)) return TL_HIT;
+  return TL_BAND;
+}

@@ -1,0 +1,219 @@
+// tl_sort.cu -- stable LSD radix sort of (64-bit key, 32-bit value) pairs.
+//
+// 8-bit digits.  One histogram pass counts every digit of every pass at once;
+// then one kernel per digit pass ranks a 4096-key tile in shared memory
+// (warp match-any ranking keeps the order of equal digits), obtains the
+// tile's global offsets by decoupled look-back over the preceding tiles'
+// published digit counts (Merrill & Garland 2016, "Single-pass parallel
+// prefix scan with decoupled look-back"; as used by one-sweep radix sorting,
+// Adinets & Merrill 2022), and writes the tile out digit by digit.
+// Tiles are numbered in the order blocks start (an atomic counter), so a
+// tile only ever waits on tiles whose blocks are already running.  Every wait
+// is bounded by spin_limit; on expiry the tile records TL_ST_TIMEOUT and
+// proceeds (the result is then invalid, and the host reports the error).
+#include "tl_common.cuh"
+
+namespace tl {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
+constexpr int kRadix = 256;
+constexpr uint32_t kAgg = 1u << 30;     // tile aggregate published
+constexpr uint32_t kPre = 2u << 30;     // inclusive prefix published
+constexpr uint32_t kValMask = kAgg - 1u;
+
+__global__ void __launch_bounds__(256) k_sort_hist(const unsigned long long *__restrict__ key,
+                                                   int64_t n, int passes, uint32_t *hist) {
+  __shared__ uint32_t sh[8][kRadix];
+  for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long k = key[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&hist[i], v);
+  }
+}
+
+// exclusive scan of each pass's 256 digit counts, in place (one block of 256)
+__global__ void k_sort_scan(uint32_t *hist, int passes) {
+  __shared__ uint32_t s[kRadix];
+  for (int p = 0; p < passes; ++p) {
+    uint32_t v = hist[p * kRadix + threadIdx.x];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < kRadix; off <<= 1) {
+      uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    hist[p * kRadix + threadIdx.x] = s[threadIdx.x] - v;
+    __syncthreads();
+  }
+}
+
+struct SortSmem {
+  unsigned long long keys[kSortTile];
+  uint32_t vals[kSortTile];
+  uint32_t wcnt[8][kRadix];  // per-warp digit counts, then per-warp offsets
+  uint32_t dexcl[kRadix];    // tile-local exclusive digit offsets
+  uint32_t gbase[kRadix];    // global destination of each digit's first key
+  uint32_t scan[kRadix];
+  uint32_t tile;
+};
+
+__global__ void __launch_bounds__(256) k_sort_pass(
+    const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
+    unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
+    const uint32_t *__restrict__ digit_base, uint32_t *status, uint32_t *tile_ctr,
+    long long spin_limit, int debug_stall, unsigned int *st_flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) sm.tile = atomicAdd(tile_ctr, 1u);
+  for (int i = tid; i < 8 * kRadix; i += kSortThreads) (&sm.wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = sm.tile;
+  const int64_t base = (int64_t)tile * kSortTile;
+  const unsigned lt = (1u << lane) - 1u;
+
+  unsigned long long k[kSortItems];
+  uint32_t v[kSortItems];
+  uint32_t rank[kSortItems];
+  uint32_t dig[kSortItems];
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const int64_t idx = base + warp * (32 * kSortItems) + it * 32 + lane;
+    const bool valid = idx < n;
+    k[it] = valid ? kin[idx] : 0ull;
+    v[it] = valid ? vin[idx] : 0u;
+    dig[it] = valid ? (uint32_t)((k[it] >> shift) & 255u) : 256u;
+  }
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    const unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+    uint32_t before = 0;
+    if (dig[it] < 256u) before = sm.wcnt[warp][dig[it]];
+    __syncwarp();
+    if (dig[it] < 256u && lane == __ffs(peers) - 1) sm.wcnt[warp][dig[it]] = before + __popc(peers);
+    rank[it] = before + __popc(peers & lt);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per-digit exclusive offsets across warps; tile total per digit
+  uint32_t cnt;
+  {
+    const int d = tid;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      uint32_t t = sm.wcnt[w][d];
+      sm.wcnt[w][d] = run;
+      run += t;
+    }
+    cnt = run;
+    // publish the tile aggregate, then look back over preceding tiles
+    uint32_t *my = status + (int64_t)tile * kRadix + d;
+    uint32_t excl = 0;
+    if (tile == 0) {
+      if (!debug_stall) atomicExch(my, kPre | cnt);
+    } else {
+      atomicExch(my, kAgg | cnt);
+      int64_t j = (int64_t)tile - 1;
+      long long spins = 0;
+      while (j >= 0) {
+        const uint32_t sv = *(volatile uint32_t *)(status + j * kRadix + d);
+        const uint32_t flag = sv & ~kValMask;
+        if (flag == 0u) {
+          if (++spins > spin_limit) {
+            atomicOr(st_flags, (unsigned)TL_ST_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+          continue;
+        }
+        excl += sv & kValMask;
+        if (flag == kPre) break;
+        --j;
+      }
+      atomicExch(my, kPre | ((excl + cnt) & kValMask));
+    }
+    sm.gbase[d] = digit_base[d] + excl;
+    sm.scan[d] = cnt;
+  }
+  __syncthreads();
+  // tile-local exclusive scan over digits (Hillis-Steele in shared memory)
+  for (int off = 1; off < kRadix; off <<= 1) {
+    uint32_t t = tid >= off ? sm.scan[tid - off] : 0u;
+    __syncthreads();
+    sm.scan[tid] += t;
+    __syncthreads();
+  }
+  sm.dexcl[tid] = sm.scan[tid] - cnt;
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kSortItems; ++it) {
+    if (dig[it] < 256u) {
+      const uint32_t pos = sm.dexcl[dig[it]] + sm.wcnt[warp][dig[it]] + rank[it];
+      sm.keys[pos] = k[it];
+      sm.vals[pos] = v[it];
+    }
+  }
+  __syncthreads();
+  const int64_t rem = n - base;
+  const int tcount = rem < kSortTile ? (int)rem : kSortTile;
+  for (int j = tid; j < tcount; j += kSortThreads) {
+    const unsigned long long kk = sm.keys[j];
+    const uint32_t d = (uint32_t)((kk >> shift) & 255u);
+    const uint32_t g = sm.gbase[d] + (uint32_t)j - sm.dexcl[d];
+    if ((int64_t)g < n) {  // always true unless a wait expired (then the result is discarded)
+      kout[g] = kk;
+      vout[g] = sm.vals[j];
+    }
+  }
+}
+
+// Sort w.key[0]/w.val[0] by the low key_bits bits.  *out_sel receives the
+// buffer index holding the result.
+cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
+                        int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s) {
+  *out_sel = 0;
+  if (n <= 1) return cudaSuccess;
+  const int passes = (key_bits + 7) / 8;
+  const int64_t tiles = (n + kSortTile - 1) / kSortTile;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(w.sort_hist, 0, sizeof(uint32_t) * 8 * kRadix, s))) return e;
+  if ((e = cudaMemsetAsync(w.sort_tile, 0, sizeof(uint32_t) * 8, s))) return e;
+  {
+    int64_t nb = (n + 255) / 256;
+    int blocks = (int)(nb < 2048 ? nb : 2048);
+    k_sort_hist<<<blocks, 256, 0, s>>>(w.key[0], n, passes, w.sort_hist);
+    k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_hist, passes);
+  }
+  static bool attr_done = false;
+  if (!attr_done) {
+    if ((e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(SortSmem))))
+      return e;
+    attr_done = true;
+  }
+  int sel = 0;
+  for (int p = 0; p < passes; ++p) {
+    if ((e = cudaMemsetAsync(w.sort_status, 0, sizeof(uint32_t) * kRadix * tiles, s))) return e;
+    k_sort_pass<<<(unsigned)tiles, kSortThreads, sizeof(SortSmem), s>>>(
+        w.key[sel], w.val[sel], w.key[sel ^ 1], w.val[sel ^ 1], n, 8 * p, w.sort_hist + p * kRadix,
+        w.sort_status, w.sort_tile + p, spin_limit, debug_stall && p == 0, status);
+    if ((e = cudaGetLastError())) return e;
+    sel ^= 1;
+  }
+  *out_sel = sel;
+  return cudaSuccess;
+}
+
+}  // namespace tl

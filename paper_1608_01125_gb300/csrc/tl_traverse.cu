@@ -1,0 +1,487 @@
+// tl_traverse.cu -- dual-hierarchy traversal, narrow phase, FP64 band
+// re-test and the per-step yield reduction.
+//
+// The two hierarchies are traversed against each other (Sec. 2.2: depth-first
+// descent; a failed overlap test, Eq. CollDet, skips the whole subtree pair).
+// A few breadth-first expansion levels first turn the root pair into a
+// frontier of node pairs; then persistent warps take frontier pairs and
+// descend depth first with a stack of node pairs in shared memory.  Each
+// iteration a warp pops up to 8 pairs and tests the up-to-4 child
+// combinations of each with one lane per combination; survivors are pushed
+// (or, when both sides are leaf buckets, queued) with ballot/popc
+// compaction.  Queued bucket pairs are flattened over the warp's lanes, one
+// photon pair per lane, and given the narrow-phase test; hits leave with one
+// atomic per warp.
+#include "tl_common.cuh"
+#include "tl_exact.cuh"
+#include "tl_narrow.cuh"
+
+namespace tl {
+
+
+// One side of a child pair: the child `slot` of an inner node, or a bucket
+// itself (slot ignored) when ref names a bucket.
+struct Side {
+  TLBox box;
+  uint32_t sref;   // stack reference of this child
+  uint32_t first;  // first photon (buckets)
+  uint32_t cnt;    // photons under it
+  bool bucket;
+};
+
+__device__ __forceinline__ Side side_of(const TLTree &T, uint32_t ref, int slot) {
+  Side s;
+  uint32_t node, sl;
+  if (!(ref & TL_FLAG)) {
+    node = ref;
+    sl = (uint32_t)slot;
+  } else {
+    node = (ref & ~TL_FLAG) >> 1;
+    sl = ref & 1u;
+  }
+  const TLNode *nd = T.nodes + node;
+  const float4 *f = reinterpret_cast<const float4 *>(nd);
+  TLNode v;
+  v.b0 = __ldg(f + 0);
+  v.b1 = __ldg(f + 1);
+  v.b2 = __ldg(f + 2);
+  v.c = __ldg(reinterpret_cast<const int4 *>(f + 3));
+  s.box = tl_child_box(v, (int)sl);
+  const uint32_t cr = (uint32_t)(sl ? v.c.y : v.c.x);
+  s.cnt = (uint32_t)(sl ? v.c.w : v.c.z);
+  s.bucket = (cr & TL_FLAG) != 0u;
+  s.first = cr & ~TL_FLAG;
+  if (ref & TL_FLAG) s.sref = ref;
+  else s.sref = s.bucket ? (TL_FLAG | (node << 1) | sl) : cr;
+  return s;
+}
+
+__device__ __forceinline__ uint32_t pack_bucket(uint32_t first, uint32_t cnt) {
+  return first | ((cnt - 1u) << 27);
+}
+
+// For a pair (ra, rb) and a combination index 0..3, the child pair it names.
+// Returns false if the combination does not exist for this pair.
+__device__ __forceinline__ bool child_pair(const TLTree &A, const TLTree &B, uint2 pr, int combo,
+                                           Side &sa, Side &sb) {
+  const bool ain = !(pr.x & TL_FLAG), bin = !(pr.y & TL_FLAG);
+  int ia, ib;
+  if (ain && bin) {
+    ia = combo >> 1;
+    ib = combo & 1;
+  } else if (ain) {
+    if (combo >= 2) return false;
+    ia = combo;
+    ib = 0;
+  } else if (bin) {
+    if (combo >= 2) return false;
+    ia = 0;
+    ib = combo;
+  } else {
+    return false;
+  }
+  sa = side_of(A, pr.x, ia);
+  sb = side_of(B, pr.y, ib);
+  return true;
+}
+
+// warp-aggregated append of (x, y) for lanes with pred
+__device__ __forceinline__ void emit(bool pred, uint32_t x, uint32_t y, uint2 *buf,
+                                     unsigned long long cap, unsigned long long *counter,
+                                     unsigned *status, unsigned ovf_bit, int lane) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (!m) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (pred) {
+    const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
+    if (idx < cap) buf[idx] = make_uint2(x, y);
+  }
+  if (lane == 0 && base + __popc(m) > cap) atomicOr(status, ovf_bit);
+}
+
+// ------------------------------------------------------------ init
+
+__global__ void k_step_init(TLCounters *ctr, uint2 *F0, uint32_t superA, uint32_t superB,
+                            int nonempty, const unsigned *build_status) {
+  unsigned *w = reinterpret_cast<unsigned *>(ctr);
+  for (int i = threadIdx.x; i < (int)(sizeof(TLCounters) / 4); i += blockDim.x) w[i] = 0u;
+  if (threadIdx.x == 0) F0[0] = make_uint2(superA, superB);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned bs = *build_status & (unsigned)TL_ST_TIMEOUT;
+    ctr->status = bs;
+    // after a failed build there is nothing valid to traverse
+    ctr->counts[0] = (nonempty && !bs) ? 1u : 0u;
+  }
+}
+
+// ------------------------------------------------------------ frontier
+
+__global__ void __launch_bounds__(256) k_expand(TravArgs a, uint2 *F0, uint2 *F1, unsigned cap,
+                                                unsigned target, int level) {
+  TLCounters *ctr = a.ctr;
+  if (*(volatile unsigned *)&ctr->frozen) return;
+  const unsigned nin = *(volatile unsigned *)&ctr->counts[level];
+  if (nin >= target || nin == 0u) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctr->frozen = 1u;
+      ctr->final_level = (unsigned)level;
+    }
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->final_level = (unsigned)level + 1u;
+  const uint2 *in = (level & 1) ? F1 : F0;
+  uint2 *out = (level & 1) ? F0 : F1;
+  unsigned *ocount = &ctr->counts[level + 1];
+  const int lane = threadIdx.x & 31;
+  unsigned long long tests = 0;
+  const unsigned stride = gridDim.x * blockDim.x;
+  const unsigned nround = (nin + 31u) & ~31u;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
+    const bool valid = i < nin;
+    const uint2 pr = valid ? in[i] : make_uint2(0u, 0u);
+    const bool both_buckets = valid && (pr.x & TL_FLAG) && (pr.y & TL_FLAG);
+    for (int combo = 0; combo < 4; ++combo) {
+      Side sa, sb;
+      bool ok = false;
+      uint2 o = make_uint2(0u, 0u);
+      if (valid && !both_buckets && child_pair(a.A, a.B, pr, combo, sa, sb)) {
+        ++tests;
+        ok = tl_overlap(sa.box, sb.box);
+        o = make_uint2(sa.sref, sb.sref);
+      } else if (both_buckets && combo == 0) {
+        ok = true;  // already tested when it was produced: pass through
+        o = pr;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (m) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(ocount, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) {
+          const unsigned idx = base + __popc(m & ((1u << lane) - 1u));
+          if (idx < cap) out[idx] = o;
+          else atomicOr(&ctr->status, (unsigned)TL_ST_FRONT_OVF);
+        }
+      }
+    }
+  }
+  for (int off = 16; off; off >>= 1) tests += __shfl_xor_sync(0xffffffffu, tests, off);
+  if (lane == 0 && tests) atomicAdd(&ctr->node_tests, tests);
+}
+
+// ------------------------------------------------------------ narrow phase
+
+struct WarpSmem {
+  uint2 leafq[64];
+  int scan[32];
+};
+
+template <bool FP64>
+__device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, int nq, int lane,
+                                             unsigned long long &tests) {
+  const unsigned lt = (1u << lane) - 1u;
+  for (int e0 = 0; e0 < nq; e0 += 32) {
+    const int m = min(32, nq - e0);
+    int sz = 0;
+    if (lane < m) {
+      const uint2 q = ws.leafq[e0 + lane];
+      sz = (int)(((q.x >> 27) + 1u) * ((q.y >> 27) + 1u));
+    }
+    int inc = sz;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    ws.scan[lane] = inc - sz;
+    __syncwarp();
+    tests += (unsigned long long)total;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+      const int t = t0 + lane;
+      int outcome = TL_MISS;
+      uint32_t oi = 0u, oj = 0u;
+      if (t < total) {
+        // largest entry e with scan[e] <= t
+        int lo = 0, hi = m - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (ws.scan[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        const uint2 q = ws.leafq[e0 + lo];
+        const uint32_t fa = q.x & 0x7FFFFFFu, fb = q.y & 0x7FFFFFFu;
+        const uint32_t cb = (q.y >> 27) + 1u;
+        const uint32_t loc = (uint32_t)(t - ws.scan[lo]);
+        const uint32_t ia = loc / cb, jb = loc - ia * cb;
+        const float4 da = __ldg(a.A.dir + fa + ia), db = __ldg(a.B.dir + fb + jb);
+        oi = __float_as_uint(da.w);
+        oj = __float_as_uint(db.w);
+        if (FP64) {
+          outcome = tl_exact_hit(a.mA, oi, a.mB, oj, a.ct, a.dt, a.kappa) ? TL_HIT : TL_MISS;
+        } else {
+          const float4 pa = __ldg(a.A.pos + fa + ia), pb = __ldg(a.B.pos + fb + jb);
+          outcome = tl_narrow32(pa, da, pb, db, a.nk);
+        }
+      }
+      emit(outcome == TL_HIT, oi, oj, a.hits, a.hit_cap, &a.ctr->hits, &a.ctr->status,
+           TL_ST_HIT_OVF, lane);
+      if (!FP64)
+        emit(outcome == TL_BAND, oi, oj, a.band, a.band_cap, &a.ctr->band, &a.ctr->status,
+             TL_ST_BAND_OVF, lane);
+    }
+    __syncwarp();
+  }
+  (void)lt;
+}
+
+// ------------------------------------------------------------ traversal
+
+template <bool FP64>
+__global__ void __launch_bounds__(128) k_traverse(TravArgs a, const uint2 *F0, const uint2 *F1,
+                                                  const uint2 *list, unsigned long long list_n,
+                                                  int from_frontier) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int D = a.stack_depth;
+  uint2 *stack = reinterpret_cast<uint2 *>(smem_raw) + (size_t)warp * D;
+  WarpSmem &ws = reinterpret_cast<WarpSmem *>(
+      smem_raw + sizeof(uint2) * (size_t)D * (blockDim.x >> 5))[warp];
+  TLCounters *ctr = a.ctr;
+  const uint2 *src;
+  unsigned long long nsrc;
+  if (from_frontier) {
+    const unsigned lvl = ctr->final_level;
+    src = (lvl & 1u) ? F1 : F0;
+    nsrc = ctr->counts[lvl];
+  } else {
+    src = list;
+    nsrc = list_n;
+  }
+  const unsigned lt = (1u << lane) - 1u;
+  int sp = 0, nq = 0;
+  unsigned long long node_tests = 0, narrow_tests = 0, leaf_pairs = 0;
+  while (true) {
+    if (sp == 0) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(&ctr->cursor, 1u);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= nsrc) break;
+      if (lane == 0) stack[0] = src[base];
+      __syncwarp();
+      sp = 1;
+    }
+    const int npop = min(sp, 8);
+    sp -= npop;
+    const int p = lane >> 2, combo = lane & 3;
+    const bool active = p < npop;
+    const uint2 pr = active ? stack[sp + p] : make_uint2(0u, 0u);
+    __syncwarp();
+    bool ok = false, leafleaf = false, tested = false;
+    uint2 o = make_uint2(0u, 0u);
+    if (active) {
+      if ((pr.x & TL_FLAG) && (pr.y & TL_FLAG)) {
+        if (combo == 0) {  // a bucket pair taken from the frontier
+          const Side sa = side_of(a.A, pr.x, 0), sb = side_of(a.B, pr.y, 0);
+          ok = leafleaf = true;
+          o = make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt));
+        }
+      } else {
+        Side sa, sb;
+        if (child_pair(a.A, a.B, pr, combo, sa, sb)) {
+          tested = true;
+          ok = tl_overlap(sa.box, sb.box);
+          leafleaf = sa.bucket && sb.bucket;
+          o = leafleaf ? make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt))
+                       : make_uint2(sa.sref, sb.sref);
+        }
+      }
+    }
+    const unsigned mtest = __ballot_sync(0xffffffffu, tested);
+    if (lane == 0) node_tests += (unsigned long long)__popc(mtest);
+    const unsigned mpush = __ballot_sync(0xffffffffu, ok && !leafleaf);
+    const unsigned mleaf = __ballot_sync(0xffffffffu, ok && leafleaf);
+    if (ok && !leafleaf) {
+      const int slot = sp + __popc(mpush & lt);
+      if (slot < D) {
+        stack[slot] = o;
+      } else {
+        const unsigned long long idx = atomicAdd(&ctr->spill, 1ull);
+        if (idx < a.spill_cap) a.spill[idx] = o;
+        else atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+      }
+    }
+    sp = min(sp + __popc(mpush), D);
+    if (ok && leafleaf) ws.leafq[nq + __popc(mleaf & lt)] = o;
+    nq += __popc(mleaf);
+    __syncwarp();
+    if (nq >= 32) {
+      leaf_pairs += nq;
+      flush_leaves<FP64>(a, ws, nq, lane, narrow_tests);
+      nq = 0;
+    }
+  }
+  if (nq) {
+    leaf_pairs += nq;
+    flush_leaves<FP64>(a, ws, nq, lane, narrow_tests);
+  }
+  if (lane == 0) {
+    if (node_tests) atomicAdd(&ctr->node_tests, node_tests);
+    if (narrow_tests) atomicAdd(&ctr->narrow_tests, narrow_tests);
+    if (leaf_pairs) atomicAdd(&ctr->leaf_pairs, leaf_pairs);
+  }
+}
+
+// ------------------------------------------------------------ band re-test
+
+__global__ void __launch_bounds__(256) k_band(TravArgs a) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long n = min(a.ctr->band, a.band_cap);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long nround = (n + 31ull) & ~31ull;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < nround;
+       i += stride) {
+    bool hit = false;
+    uint2 q = make_uint2(0u, 0u);
+    if (i < n) {
+      q = a.band[i];
+      hit = tl_exact_hit(a.mA, q.x, a.mB, q.y, a.ct, a.dt, a.kappa);
+    }
+    emit(hit, q.x, q.y, a.hits, a.hit_cap, &a.ctr->hits, &a.ctr->status, TL_ST_HIT_OVF, lane);
+  }
+}
+
+// ------------------------------------------------------------ yield
+
+// splitmix64 (Steele, Lea & Flood 2014; Vigna's constants)
+__device__ __forceinline__ unsigned long long smix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct Partial {
+  unsigned long long count;
+  double weighted;
+  unsigned long long hsum, hxor;
+};
+
+// Sum over the step's hits of w_i w_j (FP64), the count and the order-free
+// checksums.  Per-block partials are added by the last block in block order.
+__global__ void __launch_bounds__(256) k_yield(TravArgs a, Partial *partials) {
+  __shared__ Partial sp[8];
+  __shared__ bool last;
+  const unsigned long long n = min(a.ctr->hits, a.hit_cap);
+  Partial p = {0ull, 0.0, 0ull, 0ull};
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint2 h = a.hits[i];
+    const double wi = a.mA.w ? a.mA.w[h.x] : 1.0, wj = a.mB.w ? a.mB.w[h.y] : 1.0;
+    p.count += 1ull;
+    p.weighted += wi * wj;
+    const unsigned long long hm = smix64(((unsigned long long)h.x << 32) | h.y);
+    p.hsum += hm;
+    p.hxor ^= hm;
+  }
+  for (int off = 16; off; off >>= 1) {
+    p.count += __shfl_xor_sync(0xffffffffu, p.count, off);
+    p.weighted += __shfl_xor_sync(0xffffffffu, p.weighted, off);
+    p.hsum += __shfl_xor_sync(0xffffffffu, p.hsum, off);
+    p.hxor ^= __shfl_xor_sync(0xffffffffu, p.hxor, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sp[warp] = p;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial b = sp[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      b.count += sp[w].count;
+      b.weighted += sp[w].weighted;
+      b.hsum += sp[w].hsum;
+      b.hxor ^= sp[w].hxor;
+    }
+    partials[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(&a.ctr->reduce_done, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    Partial t = {0ull, 0.0, 0ull, 0ull};
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      const volatile Partial *q = partials + b;
+      t.count += q->count;
+      t.weighted += q->weighted;
+      t.hsum += q->hsum;
+      t.hxor ^= q->hxor;
+    }
+    a.ctr->count = t.count;
+    a.ctr->weighted = t.weighted;
+    a.ctr->hsum = t.hsum;
+    a.ctr->hxor = t.hxor;
+  }
+}
+
+// ------------------------------------------------------------ host launchers
+
+size_t traverse_smem(int warps, int depth) {
+  return sizeof(uint2) * (size_t)depth * warps + sizeof(WarpSmem) * (size_t)warps;
+}
+
+cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t sb, int nonempty,
+                             const unsigned *build_status, cudaStream_t s) {
+  k_step_init<<<1, 128, 0, s>>>(ctr, F0, sa, sb, nonempty, build_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
+                          int level, int blocks, cudaStream_t s) {
+  k_expand<<<blocks, 256, 0, s>>>(a, F0, F1, cap, target, level);
+  return cudaGetLastError();
+}
+
+cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm) {
+  size_t smem = traverse_smem(warps, depth);
+  cudaError_t e;
+  if (fp64) {
+    if ((e = cudaFuncSetAttribute(k_traverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+      return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_traverse<true>,
+                                                         warps * 32, smem);
+  }
+  if ((e = cudaFuncSetAttribute(k_traverse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem)))
+    return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_traverse<false>,
+                                                       warps * 32, smem);
+}
+
+cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
+                            unsigned long long list_n, int from_frontier, int blocks, int warps,
+                            cudaStream_t s) {
+  size_t smem = traverse_smem(warps, a.stack_depth);
+  if (a.fp64)
+    k_traverse<true><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier);
+  else
+    k_traverse<false><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band(const TravArgs &a, int blocks, cudaStream_t s) {
+  k_band<<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_yield(const TravArgs &a, void *partials, int blocks, cudaStream_t s) {
+  k_yield<<<blocks, 256, 0, s>>>(a, reinterpret_cast<Partial *>(partials));
+  return cudaGetLastError();
+}
+
+size_t partial_bytes() { return sizeof(Partial); }
+
+}  // namespace tl

@@ -1,0 +1,73 @@
+"""The C ABI library builds, loads without a GPU and exports every function
+that include/*.h declares; argument checks that happen on the host reject
+bad input without touching a device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1608_01125_gb300 import binding, build_ext
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_ext.build()
+    return binding.lib()
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(trilens_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)  # resolvable through the loader
+
+
+def test_status_strings(lib):
+    for code in range(0, -7, -1):
+        s = binding.status_str(code)
+        assert s and s != "unknown status"
+    assert binding.status_str(-99) == "unknown status"
+    assert b"sm_103a" in lib.trilens_version()
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    h = ctypes.c_void_p()
+    ok = binding.Params(10.0, 1e16, binding.FP64, 0, 0, 0, 0)
+    empty = binding.Beam(0, *([None] * 8))
+    bad_n = binding.Beam(-1, *([None] * 8))
+    missing = binding.Beam(5, *([None] * 8))
+    huge = binding.Beam(1 << 27, *([None] * 8))
+    for A, B, P in ((bad_n, empty, ok), (missing, empty, ok), (huge, empty, ok)):
+        assert lib.trilens_create(ctypes.byref(h), ctypes.byref(A), ctypes.byref(B),
+                                  ctypes.byref(P), None) == binding.ERR_INVALID
+    for P in (binding.Params(0.0, 1e16, 0, 0, 0, 0, 0), binding.Params(10.0, -1.0, 0, 0, 0, 0, 0),
+              binding.Params(10.0, 1e16, 7, 0, 0, 0, 0), binding.Params(10.0, 1e16, 0, 33, 0, 0, 0),
+              binding.Params(10.0, 1e16, 0, 0, 8, 0, 0), binding.Params(10.0, 1e16, 0, 0, 0, 17, 0),
+              binding.Params(10.0, 1e16, 0, 0, 0, 0, -5)):
+        assert lib.trilens_create(ctypes.byref(h), ctypes.byref(empty), ctypes.byref(empty),
+                                  ctypes.byref(P), None) == binding.ERR_INVALID
+    assert lib.trilens_create(None, ctypes.byref(empty), ctypes.byref(empty), ctypes.byref(ok),
+                              None) == binding.ERR_INVALID
+    assert lib.trilens_build(None, 0) == binding.ERR_INVALID
+    assert lib.trilens_collide_step(None, 0, None, 0, None) == binding.ERR_INVALID
+    assert lib.trilens_debug_eval64(None, None, -1, 0, None) == binding.ERR_INVALID
+    lib.trilens_destroy(None)
