@@ -110,11 +110,13 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
 int trilens_build(trilens_ctx *c, int64_t step);
 
 /* Collide the hierarchies built for `step` (trilens_build must have been
- * called with the same step).  Appends the step's counters to the cumulative
+ * called with the same step).  Adds the step's counters to the cumulative
  * yield.  If hits != NULL (device, 2*cap uint32: (i_A, j_B) pairs, order
- * unspecified), up to cap pairs are written; if more exist the call returns
- * CAPACITY and stores the required size in *n_hits.  n_hits (host) may be
- * NULL.  Synchronises the stream (to check device status and regrow internal
+ * unspecified), the step's pairs are written to it; if more than cap exist
+ * the call writes nothing, adds nothing to the yield, returns CAPACITY and
+ * stores the required size in *n_hits -- call it again for the same step
+ * with a larger buffer (no rebuild needed).  n_hits (host) may be NULL.
+ * Synchronises the stream (to check device status and regrow internal
  * buffers). */
 int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t cap,
                          int64_t *n_hits);

@@ -188,7 +188,9 @@ class Collider:
             rc = lib().trilens_collide_step(self.ctx, int(step), ctypes.c_void_p(hits.data_ptr()),
                                             cap, ctypes.byref(n))
         if rc == ERR_CAPACITY:
-            raise TrilensError(rc, f"hit buffer too small, need {n.value}")
+            err = TrilensError(rc, f"hit buffer too small, need {n.value}")
+            err.needed = int(n.value)
+            raise err
         _check(rc, self.ctx)
         return int(n.value)
 
@@ -205,10 +207,7 @@ class Collider:
             except TrilensError as e:
                 if e.code != ERR_CAPACITY:
                     raise
-                self.build(step)
-                cap = int(str(e).rsplit(" ", 1)[-1]) + 16
-                # the failed call already counted this step in the yield
-                self.reset_yield()
+                cap = e.needed + 16
         self.stream.synchronize()
         h = buf[:n].cpu().numpy().view(np.uint32).astype(np.int64)
         return h, self.stats()

@@ -527,6 +527,12 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
     if (!again) break;
     if (++retries > 8) return fail(c, TRILENS_ERR_STACK, "buffers kept overflowing");
   }
+  if (hits && (int64_t)h.count > cap) {
+    // the step is not added to the cumulative yield: the caller repeats it
+    // with a larger buffer (the hierarchies stay built)
+    if (n_hits) *n_hits = (int64_t)h.count;
+    return fail(c, TRILENS_ERR_CAPACITY, "need %llu hit slots", (unsigned long long)h.count);
+  }
   trilens_step_stats &s = c->last;
   s.step = step;
   s.count = (int64_t)h.count;
@@ -546,8 +552,6 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
     if (ncopy)
       CK(cudaMemcpyAsync(hits, c->hits, sizeof(uint2) * ncopy, cudaMemcpyDeviceToDevice, c->stream));
   }
-  if (hits && (int64_t)h.count > cap)
-    return fail(c, TRILENS_ERR_CAPACITY, "need %llu hit slots", (unsigned long long)h.count);
   return TRILENS_OK;
 }
 

@@ -241,7 +241,7 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
 // ------------------------------------------------------------ traversal
 
 template <bool FP64>
-__global__ void __launch_bounds__(128) k_traverse(TravArgs a, const uint2 *F0, const uint2 *F1,
+__global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, const uint2 *F1,
                                                   const uint2 *list, unsigned long long list_n,
                                                   int from_frontier) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -370,8 +370,35 @@ struct Partial {
   unsigned long long hsum, hxor;
 };
 
+__device__ __forceinline__ void padd(Partial &a, const Partial &b) {
+  a.count += b.count;
+  a.weighted += b.weighted;
+  a.hsum += b.hsum;
+  a.hxor ^= b.hxor;
+}
+
+// fixed-order block reduction (warp xor-tree, then warps in order)
+__device__ __forceinline__ Partial block_reduce(Partial p, Partial *sp) {
+  for (int off = 16; off; off >>= 1) {
+    Partial o;
+    o.count = __shfl_xor_sync(0xffffffffu, p.count, off);
+    o.weighted = __shfl_xor_sync(0xffffffffu, p.weighted, off);
+    o.hsum = __shfl_xor_sync(0xffffffffu, p.hsum, off);
+    o.hxor = __shfl_xor_sync(0xffffffffu, p.hxor, off);
+    padd(p, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sp[warp] = p;
+  __syncthreads();
+  Partial b = sp[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) padd(b, sp[w]);
+  __syncthreads();
+  return b;
+}
+
 // Sum over the step's hits of w_i w_j (FP64), the count and the order-free
-// checksums.  Per-block partials are added by the last block in block order.
+// checksums.  Per-block partials are combined by the last block to finish,
+// in a fixed order.
 __global__ void __launch_bounds__(256) k_yield(TravArgs a, Partial *partials) {
   __shared__ Partial sp[8];
   __shared__ bool last;
@@ -387,42 +414,31 @@ __global__ void __launch_bounds__(256) k_yield(TravArgs a, Partial *partials) {
     p.hsum += hm;
     p.hxor ^= hm;
   }
-  for (int off = 16; off; off >>= 1) {
-    p.count += __shfl_xor_sync(0xffffffffu, p.count, off);
-    p.weighted += __shfl_xor_sync(0xffffffffu, p.weighted, off);
-    p.hsum += __shfl_xor_sync(0xffffffffu, p.hsum, off);
-    p.hxor ^= __shfl_xor_sync(0xffffffffu, p.hxor, off);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sp[warp] = p;
-  __syncthreads();
+  const Partial b = block_reduce(p, sp);
   if (threadIdx.x == 0) {
-    Partial b = sp[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      b.count += sp[w].count;
-      b.weighted += sp[w].weighted;
-      b.hsum += sp[w].hsum;
-      b.hxor ^= sp[w].hxor;
-    }
     partials[blockIdx.x] = b;
     __threadfence();
     last = atomicAdd(&a.ctr->reduce_done, 1u) == gridDim.x - 1u;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    Partial t = {0ull, 0.0, 0ull, 0ull};
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-      const volatile Partial *q = partials + b;
-      t.count += q->count;
-      t.weighted += q->weighted;
-      t.hsum += q->hsum;
-      t.hxor ^= q->hxor;
-    }
-    a.ctr->count = t.count;
-    a.ctr->weighted = t.weighted;
-    a.ctr->hsum = t.hsum;
-    a.ctr->hxor = t.hxor;
+  if (!last) return;
+  __threadfence();
+  Partial t = {0ull, 0.0, 0ull, 0ull};
+  for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
+    const volatile Partial *v = partials + q;
+    Partial o;
+    o.count = v->count;
+    o.weighted = v->weighted;
+    o.hsum = v->hsum;
+    o.hxor = v->hxor;
+    padd(t, o);
+  }
+  const Partial tot = block_reduce(t, sp);
+  if (threadIdx.x == 0) {
+    a.ctr->count = tot.count;
+    a.ctr->weighted = tot.weighted;
+    a.ctr->hsum = tot.hsum;
+    a.ctr->hxor = tot.hxor;
   }
 }
 
