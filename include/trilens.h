@@ -145,6 +145,32 @@ const char *trilens_last_error(trilens_ctx *c);
 /* Library version string. */
 const char *trilens_version(void);
 
+/* Largest hit list trilens_yield_reduce_noalloc accepts (2^28 pairs). */
+#define TRILENS_NOALLOC_MAX_HITS (1ll << 28)
+
+/* Yield reduction that allocates no device memory.  The paper has no
+ * counterpart; this is a service for callers that cannot call cudaMalloc
+ * (code that runs inside another framework's memory pool or under a fixed
+ * memory budget, or that must not change the device's allocation state).
+ *
+ * Reduces a hit list -- hits: device, 2 * n_hits uint32 (i_A, j_B) pairs as
+ * written by trilens_collide_step -- with the weights w_a, w_b (device FP64
+ * arrays indexed by i_A and j_B; NULL means weight 1) to the same four values
+ * trilens_collide_step reports for a step: out_result (device, 32 bytes) =
+ * { uint64 count, double sum of w_i w_j, uint64 checksum sum, uint64
+ * checksum xor } (see trilens_step_stats).  Asynchronous on `stream`.
+ *
+ * Scratch lives in a fixed 128 KiB device array inside the library (held on
+ * every GPU that loads it until the process exits), so n_hits is limited to
+ * TRILENS_NOALLOC_MAX_HITS; larger lists, negative n_hits or NULL pointers
+ * give TRILENS_ERR_INVALID without launching anything.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make it before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. */
+int trilens_yield_reduce_noalloc(const uint32_t *hits, int64_t n_hits, const double *w_a,
+                                 const double *w_b, void *out_result, trilens_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

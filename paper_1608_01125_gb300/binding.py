@@ -108,6 +108,8 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_timing.restype = ctypes.c_int
         L.trilens_debug_phase_ms.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.c_int]
         L.trilens_debug_phase_ms.restype = ctypes.c_int
+        L.trilens_yield_reduce_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
+        L.trilens_yield_reduce_noalloc.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -274,4 +276,24 @@ def eval64(x, which: str = "sigma", stream=None):
     _check(lib().trilens_debug_eval64(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       x.numel(), 0 if which == "sigma" else 1,
                                       ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+NOALLOC_MAX_HITS = 1 << 28
+
+
+def yield_reduce_noalloc(hits, n_hits: int, w_a=None, w_b=None, out=None, stream=None):
+    """Reduce a device hit list (int32 tensor of >= 2*n_hits entries) without
+    any device allocation inside the library: returns a 4-element int64 CUDA
+    tensor holding (count, weighted as float64 bits, checksum sum, checksum
+    xor); pass `out` (4 int64 on the device) to avoid torch allocating it."""
+    torch = _torch()
+    if n_hits < 0 or n_hits > NOALLOC_MAX_HITS:
+        raise TrilensError(ERR_INVALID, f"n_hits={n_hits} outside [0, {NOALLOC_MAX_HITS}]")
+    if out is None:
+        out = torch.zeros(4, dtype=torch.int64, device=hits.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    _check(lib().trilens_yield_reduce_noalloc(ptr(hits), int(n_hits), ptr(w_a), ptr(w_b), ptr(out),
+                                             ctypes.c_void_p(st.cuda_stream)))
     return out
