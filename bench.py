@@ -228,9 +228,12 @@ def run_ours(args, wl):
     B = binding.to_device(b_np, dev)
     col = binding.Collider(A, B, wl.dt, wl.kappa, precision=binding.FP32_BAND, stream=stream)
 
+    first, nsteps = args.first_step, (args.time_steps or wl.steps)
+    time_steps = range(first, first + nsteps)
+
     def one_run():
         hits = tests = band = 0
-        for k in range(wl.steps):
+        for k in time_steps:
             col.build(k)
             hits += col.collide(k)
             st = col.stats()
@@ -272,7 +275,7 @@ def run_ours(args, wl):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     K = args.steps
-    units_rank = wl.a.n * wl.b.n * wl.steps * K
+    units_rank = wl.a.n * wl.b.n * nsteps * K
     value = world * units_rank / (ms / 1e3)
 
     # end to end through the public API with host buffers: every step copies
@@ -287,14 +290,14 @@ def run_ours(args, wl):
             for kk, v in D.items():
                 v.copy_(pinned[key][kk], non_blocking=True)
         col.reset_yield()
-        for k in range(wl.steps):
+        for k in time_steps:
             col.build(k)
             col.collide(k)
         cnt, wsum = col.yield_()  # device -> host read of the result
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = world * wl.a.n * wl.b.n * wl.steps / (statistics.mean(e2e_ms) / 1e3)
+    e2e_value = world * wl.a.n * wl.b.n * nsteps / (statistics.mean(e2e_ms) / 1e3)
 
     if rank != 0:
         if world > 1:
@@ -308,13 +311,12 @@ def run_ours(args, wl):
     if dom == "sort":
         units_per_launch = (wl.a.n + wl.b.n) / 2  # one pass of one beam
         algo = per_unit * units_per_launch
-        n_pass = max(launches[dom] - 2 * 2 * wl.steps * (K), 1)  # passes exclude hist + scan
         launch_ms = phase_ms[dom] / n_launch
     elif dom in ("propagate", "gather", "emit", "refit"):
         algo = per_unit * (wl.a.n + wl.b.n) / 2
         launch_ms = phase_ms[dom] / n_launch
     else:
-        algo = per_unit * (wl.a.n + wl.b.n) + 8.0 * (hits + band) / (K * wl.steps)
+        algo = per_unit * (wl.a.n + wl.b.n) + 8.0 * (hits + band) / (K * nsteps)
         launch_ms = phase_ms[dom] / n_launch
     achieved = algo / (launch_ms / 1e3) / 1e9
     cpu = cpu_baseline(wl, a_np, b_np) if (world == 1 and not args.no_cpu_baseline) else None
@@ -322,7 +324,8 @@ def run_ours(args, wl):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": config_of(wl, "flushed (256 MiB write) before every timed step"),
+        "config": dict(config_of(wl, "flushed (256 MiB write) before every timed step"),
+                       time_steps=nsteps, first_step=first),
         "collided_pairs_per_s": world * hits / (ms / 1e3),
         "narrow_tests_per_s": world * tests / (ms / 1e3),
         "hits_per_run": hits / K, "narrow_tests_per_run": tests / K, "band_per_run": band / K,
@@ -350,6 +353,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--photons", type=int, default=1 << 20)
+    ap.add_argument("--first-step", type=int, default=0,
+                    help="first time step of each run (profiling a slice of the run)")
+    ap.add_argument("--time-steps", type=int, default=0,
+                    help="time steps per run (0: the workload's 64)")
     args = ap.parse_args()
     wl = synth.headon_1m(n=args.photons)
     if args.impl == "reference":

@@ -17,7 +17,7 @@ namespace tl {
 cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t sb, int nonempty,
                              const unsigned *build_status, cudaStream_t s);
 cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
-                          int level, int blocks, cudaStream_t s);
+                          int max_levels, cudaStream_t s);
 cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm);
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
                             unsigned long long list_n, int from_frontier, int blocks, int warps,
@@ -184,7 +184,7 @@ static int alloc_beam(trilens_ctx *c, tl::BuildBufs &w, int64_t n) {
   CK(dalloc(&w.parent_leaf, m));
   CK(dalloc(&w.parent_node, m));
   CK(dalloc(&w.visit, m));
-  w.sort_tiles = (int64_t)((m + 4095) / 4096);
+  w.sort_tiles = (int64_t)((m + TL_SORT_TILE - 1) / TL_SORT_TILE);
   CK(dalloc(&w.sort_status, (size_t)w.sort_tiles * 256));
   CK(dalloc(&w.sort_hist, 8 * 256));
   CK(dalloc(&w.sort_tile, 8));
@@ -317,7 +317,8 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
     int64_t n = std::max<int64_t>(c->beam[k].n, 2);
     int lg = 0;
     while ((1ll << lg) < n) ++lg;
-    c->bits[k] = std::min(21, std::max(4, (lg + 2) / 3 + 4));
+    // Morton resolution: a few bits per axis beyond one cell per photon
+    c->bits[k] = std::min(21, std::max(4, (lg + 2) / 3 + 3));
     c->key_bits[k] = 3 * c->bits[k];
     // one-time bounds of p0 and d for the Morton box
     CK(tl::launch_beam_bounds(c->beam[k], c->bounds_dev, c->stream));
@@ -337,7 +338,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   }
   c->trav_blocks = bps * c->n_sm;
   c->expand_blocks = 2 * c->n_sm;
-  c->front_target = (unsigned)std::min<long long>(8ll * c->trav_blocks * c->trav_warps, 1 << 22);
+  c->front_target = (unsigned)std::min<long long>(4ll * c->trav_blocks * c->trav_warps, 1 << 16);
   c->front_cap = 4 * c->front_target + 64;
   CK(dalloc(&c->front[0], c->front_cap));
   CK(dalloc(&c->front[1], c->front_cap));
@@ -448,11 +449,10 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
     tmark(c, PH_EXPAND, 0, 0);
     CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super, nonempty, c->build_status,
                             c->stream));
-    for (int lvl = 0; lvl < kMaxLevels; ++lvl)
-      CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, lvl,
-                           c->expand_blocks, c->stream));
+    CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
+                         c->stream));
     tmark(c, PH_EXPAND, 0, 1);
-    c->phase_launches[PH_EXPAND] += 1 + kMaxLevels;
+    c->phase_launches[PH_EXPAND] += 2;
     tmark(c, PH_TRAV, 0, 0);
     CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->trav_blocks,
                            c->trav_warps, c->stream));

@@ -254,6 +254,15 @@ __device__ __forceinline__ void seg_axis(float p, float dc, float Llo, float Lhi
   hi = __fadd_ru(fmaxf(phi, qhi), half);
 }
 
+// atom.add with acquire-release semantics at device scope: orders this
+// thread's earlier box stores before the increment and the increment before
+// its later loads (PTX memory model), without a full fence
+__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void write_slot(TLNode *nodes, uint32_t node, uint32_t slot,
                                            const TLBox &b) {
   float *f = reinterpret_cast<float *>(&nodes[node]);
@@ -303,9 +312,8 @@ __global__ void __launch_bounds__(256) k_refit(int64_t n, const float4 *__restri
     }
     write_slot(nodes, node, slot, b);
     if (node == super) return;
-    __threadfence();
-    if (atomicAdd(&visit[node], 1u) == 0u) return;  // the sibling finishes this node
-    __threadfence();
+    // release our box, acquire the sibling's: the second arrival finishes the node
+    if (atomic_add_acq_rel(&visit[node], 1u) == 0u) return;
     const TLBox o = read_slot(nodes, node, slot ^ 1u);
     b.lx = fminf(b.lx, o.lx);
     b.ly = fminf(b.ly, o.ly);

@@ -8,6 +8,10 @@
 #define TL_MEC2 0.51099895000       /* electron rest energy [MeV], CODATA 2018 */
 #define TL_PI 3.14159265358979323846
 
+// keys per radix-sort tile (threads 256 x items 8); the look-back status
+// array holds 256 words per tile
+#define TL_SORT_TILE 2048
+
 // Child / stack references.  Bit 31 clear: an inner node index.  Bit 31 set:
 // in a node's child slot, FLAG | first photon of a leaf bucket; on a stack,
 // FLAG | (parent << 1 | slot) naming the bucket through its parent's slot.

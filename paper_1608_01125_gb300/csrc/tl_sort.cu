@@ -1,7 +1,7 @@
 // tl_sort.cu -- stable LSD radix sort of (64-bit key, 32-bit value) pairs.
 //
 // 8-bit digits.  One histogram pass counts every digit of every pass at once;
-// then one kernel per digit pass ranks a 4096-key tile in shared memory
+// then one kernel per digit pass ranks a 2048-key tile in shared memory
 // (warp match-any ranking keeps the order of equal digits), obtains the
 // tile's global offsets by decoupled look-back over the preceding tiles'
 // published digit counts (Merrill & Garland 2016, "Single-pass parallel
@@ -16,8 +16,8 @@
 namespace tl {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
+constexpr int kSortItems = TL_SORT_TILE / kSortThreads;
+constexpr int kSortTile = TL_SORT_TILE;
 constexpr int kRadix = 256;
 constexpr uint32_t kAgg = 1u << 30;     // tile aggregate published
 constexpr uint32_t kPre = 2u << 30;     // inclusive prefix published

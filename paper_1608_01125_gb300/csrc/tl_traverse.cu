@@ -119,57 +119,74 @@ __global__ void k_step_init(TLCounters *ctr, uint2 *F0, uint32_t superA, uint32_
 
 // ------------------------------------------------------------ frontier
 
-__global__ void __launch_bounds__(256) k_expand(TravArgs a, uint2 *F0, uint2 *F1, unsigned cap,
-                                                unsigned target, int level) {
+// One block expands the root pair breadth first, level by level, until the
+// frontier holds at least `target` pairs (or nothing is left to expand).
+// Bucket pairs pass through unchanged; failed overlap tests prune.
+__global__ void __launch_bounds__(1024) k_expand(TravArgs a, uint2 *F0, uint2 *F1, unsigned cap,
+                                                 unsigned target, int max_levels) {
+  __shared__ unsigned s_count[2];
+  __shared__ unsigned long long s_tests;
   TLCounters *ctr = a.ctr;
-  if (*(volatile unsigned *)&ctr->frozen) return;
-  const unsigned nin = *(volatile unsigned *)&ctr->counts[level];
-  if (nin >= target || nin == 0u) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      ctr->frozen = 1u;
-      ctr->final_level = (unsigned)level;
-    }
-    return;
+  if (threadIdx.x == 0) {
+    s_count[0] = ctr->counts[0];
+    s_count[1] = 0u;
+    s_tests = 0ull;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->final_level = (unsigned)level + 1u;
-  const uint2 *in = (level & 1) ? F1 : F0;
-  uint2 *out = (level & 1) ? F0 : F1;
-  unsigned *ocount = &ctr->counts[level + 1];
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   unsigned long long tests = 0;
-  const unsigned stride = gridDim.x * blockDim.x;
-  const unsigned nround = (nin + 31u) & ~31u;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
-    const bool valid = i < nin;
-    const uint2 pr = valid ? in[i] : make_uint2(0u, 0u);
-    const bool both_buckets = valid && (pr.x & TL_FLAG) && (pr.y & TL_FLAG);
-    for (int combo = 0; combo < 4; ++combo) {
-      Side sa, sb;
-      bool ok = false;
-      uint2 o = make_uint2(0u, 0u);
-      if (valid && !both_buckets && child_pair(a.A, a.B, pr, combo, sa, sb)) {
-        ++tests;
-        ok = tl_overlap(sa.box, sb.box);
-        o = make_uint2(sa.sref, sb.sref);
-      } else if (both_buckets && combo == 0) {
-        ok = true;  // already tested when it was produced: pass through
-        o = pr;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, ok);
-      if (m) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(ocount, (unsigned)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (ok) {
-          const unsigned idx = base + __popc(m & ((1u << lane) - 1u));
-          if (idx < cap) out[idx] = o;
-          else atomicOr(&ctr->status, (unsigned)TL_ST_FRONT_OVF);
+  int level = 0;
+  while (true) {
+    const unsigned nin = s_count[level & 1];
+    if (nin >= target || nin == 0u || level >= max_levels) break;
+    const uint2 *in = (level & 1) ? F1 : F0;
+    uint2 *out = (level & 1) ? F0 : F1;
+    unsigned *ocount = &s_count[(level + 1) & 1];
+    const unsigned nround = (nin + 31u) & ~31u;
+    for (unsigned i = threadIdx.x; i < nround; i += blockDim.x) {
+      const bool valid = i < nin;
+      const uint2 pr = valid ? in[i] : make_uint2(0u, 0u);
+      const bool both_buckets = valid && (pr.x & TL_FLAG) && (pr.y & TL_FLAG);
+      for (int combo = 0; combo < 4; ++combo) {
+        Side sa, sb;
+        bool ok = false;
+        uint2 o = make_uint2(0u, 0u);
+        if (valid && !both_buckets && child_pair(a.A, a.B, pr, combo, sa, sb)) {
+          ++tests;
+          ok = tl_overlap(sa.box, sb.box);
+          o = make_uint2(sa.sref, sb.sref);
+        } else if (both_buckets && combo == 0) {
+          ok = true;  // already tested when it was produced: pass through
+          o = pr;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (m) {
+          unsigned base = 0;
+          if (lane == 0) base = atomicAdd(ocount, (unsigned)__popc(m));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (ok) {
+            const unsigned idx = base + __popc(m & ((1u << lane) - 1u));
+            if (idx < cap) out[idx] = o;
+            else atomicOr(&ctr->status, (unsigned)TL_ST_FRONT_OVF);
+          }
         }
       }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) s_count[level & 1] = 0u;  // the next level's output count
+    ++level;
+    __syncthreads();
   }
   for (int off = 16; off; off >>= 1) tests += __shfl_xor_sync(0xffffffffu, tests, off);
-  if (lane == 0 && tests) atomicAdd(&ctr->node_tests, tests);
+  if (lane == 0 && tests) atomicAdd(&s_tests, tests);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned n = s_count[level & 1];
+    ctr->counts[level] = n < cap ? n : cap;
+    ctr->final_level = (unsigned)level;
+    ctr->frozen = 1u;
+    ctr->node_tests += s_tests;
+  }
 }
 
 // ------------------------------------------------------------ narrow phase
@@ -455,8 +472,8 @@ cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t s
 }
 
 cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
-                          int level, int blocks, cudaStream_t s) {
-  k_expand<<<blocks, 256, 0, s>>>(a, F0, F1, cap, target, level);
+                          int max_levels, cudaStream_t s) {
+  k_expand<<<1, 1024, 0, s>>>(a, F0, F1, cap, target, max_levels);
   return cudaGetLastError();
 }
 
