@@ -20,8 +20,8 @@ cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap,
                           int max_levels, cudaStream_t s);
 cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm);
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
-                            unsigned long long list_n, int from_frontier, int blocks, int warps,
-                            cudaStream_t s);
+                            unsigned long long list_n, int from_frontier, int budget, int blocks,
+                            int warps, cudaStream_t s);
 cudaError_t launch_band(const TravArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_yield(const TravArgs &a, void *partials, int blocks, cudaStream_t s);
 size_t partial_bytes();
@@ -46,6 +46,7 @@ struct trilens_ctx {
   int64_t built_step = -1;
   // traversal workspace
   int n_sm = 0, trav_warps = 4, trav_blocks = 0, expand_blocks = 0;
+  int budget = 64;  // traversal iterations per work item before it is split
   unsigned front_target = 0, front_cap = 0;
   uint2 *front[2]{};
   uint2 *spill[2]{};
@@ -338,11 +339,12 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   }
   c->trav_blocks = bps * c->n_sm;
   c->expand_blocks = 2 * c->n_sm;
-  c->front_target = (unsigned)std::min<long long>(4ll * c->trav_blocks * c->trav_warps, 1 << 16);
+  c->front_target = (unsigned)std::min<long long>(2ll * c->trav_blocks * c->trav_warps, 1 << 16);
   c->front_cap = 4 * c->front_target + 64;
   CK(dalloc(&c->front[0], c->front_cap));
   CK(dalloc(&c->front[1], c->front_cap));
-  c->spill_cap = 1 << 20;
+  c->spill_cap = std::max<unsigned long long>(1 << 20, 2ull * c->trav_blocks * c->trav_warps *
+                                                          (unsigned long long)c->p.stack_depth);
   CK(dalloc(&c->spill[0], c->spill_cap));
   CK(dalloc(&c->spill[1], c->spill_cap));
   c->hit_cap = std::max<unsigned long long>(1 << 16, 2ull * (c->beam[0].n + c->beam[1].n));
@@ -454,14 +456,14 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
     tmark(c, PH_EXPAND, 0, 1);
     c->phase_launches[PH_EXPAND] += 2;
     tmark(c, PH_TRAV, 0, 0);
-    CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->trav_blocks,
+    CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->budget, c->trav_blocks,
                            c->trav_warps, c->stream));
     tmark(c, PH_TRAV, 0, 1);
     c->phase_launches[PH_TRAV] += 1;
     CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     int sp = 0, passes = 0;
-    while (h.spill > 0 && !(h.status & TL_ST_SPILL_OVF) && passes < 64) {
+    while (h.spill > 0 && !(h.status & TL_ST_SPILL_OVF) && passes < 256) {
       // descend the pairs that did not fit on a stack, writing new overflow
       // to the other spill list
       const unsigned long long nlist = h.spill;
@@ -470,8 +472,8 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
       CK(cudaMemsetAsync(&c->ctr->spill, 0, sizeof(unsigned long long), c->stream));
       CK(cudaMemsetAsync(&c->ctr->cursor, 0, sizeof(unsigned), c->stream));
       tmark(c, PH_TRAV, 1, 0);
-      CK(tl::launch_traverse(a2, c->front[0], c->front[1], c->spill[sp], nlist, 0, c->trav_blocks,
-                             c->trav_warps, c->stream));
+      CK(tl::launch_traverse(a2, c->front[0], c->front[1], c->spill[sp], nlist, 0, c->budget,
+                             c->trav_blocks, c->trav_warps, c->stream));
       tmark(c, PH_TRAV, 1, 1);
       c->phase_launches[PH_TRAV] += 1;
       CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));

@@ -125,22 +125,32 @@ __global__ void __launch_bounds__(256) k_sort_pass(
       if (!debug_stall) atomicExch(my, kPre | cnt);
     } else {
       atomicExch(my, kAgg | cnt);
+      // walk back over the preceding tiles four at a time (independent loads),
+      // adding published aggregates until an inclusive prefix is found
       int64_t j = (int64_t)tile - 1;
       long long spins = 0;
-      while (j >= 0) {
-        const uint32_t sv = *(volatile uint32_t *)(status + j * kRadix + d);
-        const uint32_t flag = sv & ~kValMask;
-        if (flag == 0u) {
+      bool done = false;
+      while (j >= 0 && !done) {
+        uint32_t sv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          sv[q] = j - q >= 0 ? *(volatile uint32_t *)(status + (j - q) * kRadix + d) : (uint32_t)(2u << 30);
+        int used = 0;
+        for (int q = 0; q < 4 && !done; ++q) {
+          const uint32_t flag = sv[q] & ~kValMask;
+          if (flag == 0u) break;  // not published yet: reload from here
+          if (j - q >= 0) excl += sv[q] & kValMask;
+          ++used;
+          if (flag == kPre) done = true;
+        }
+        j -= used;
+        if (!done && used == 0) {
           if (++spins > spin_limit) {
             atomicOr(st_flags, (unsigned)TL_ST_TIMEOUT);
             break;
           }
           __nanosleep(32);
-          continue;
         }
-        excl += sv & kValMask;
-        if (flag == kPre) break;
-        --j;
       }
       atomicExch(my, kPre | ((excl + cnt) & kValMask));
     }

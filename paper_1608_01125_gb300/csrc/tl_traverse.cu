@@ -260,7 +260,7 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
 template <bool FP64>
 __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, const uint2 *F1,
                                                   const uint2 *list, unsigned long long list_n,
-                                                  int from_frontier) {
+                                                  int from_frontier, int budget) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int D = a.stack_depth;
@@ -279,9 +279,22 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
     nsrc = list_n;
   }
   const unsigned lt = (1u << lane) - 1u;
-  int sp = 0, nq = 0;
+  int sp = 0, nq = 0, iters = 0;
   unsigned long long node_tests = 0, narrow_tests = 0, leaf_pairs = 0;
   while (true) {
+    if (sp > 0 && budget > 0 && iters >= budget) {
+      // this item is large: hand the rest of it (the whole stack) to the next
+      // pass, where its pieces are spread over all warps
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&ctr->spill, (unsigned long long)sp);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      for (int e = lane; e < sp; e += 32) {
+        if (base + e < a.spill_cap) a.spill[base + e] = stack[e];
+        else atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+      }
+      __syncwarp();
+      sp = 0;
+    }
     if (sp == 0) {
       unsigned base = 0;
       if (lane == 0) base = atomicAdd(&ctr->cursor, 1u);
@@ -290,7 +303,9 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
       if (lane == 0) stack[0] = src[base];
       __syncwarp();
       sp = 1;
+      iters = 0;
     }
+    ++iters;
     const int npop = min(sp, 8);
     sp -= npop;
     const int p = lane >> 2, combo = lane & 3;
@@ -495,13 +510,15 @@ cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm) 
 }
 
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
-                            unsigned long long list_n, int from_frontier, int blocks, int warps,
-                            cudaStream_t s) {
+                            unsigned long long list_n, int from_frontier, int budget, int blocks,
+                            int warps, cudaStream_t s) {
   size_t smem = traverse_smem(warps, a.stack_depth);
   if (a.fp64)
-    k_traverse<true><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier);
+    k_traverse<true><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier,
+                                                       budget);
   else
-    k_traverse<false><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier);
+    k_traverse<false><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier,
+                                                        budget);
   return cudaGetLastError();
 }
 
