@@ -145,6 +145,39 @@ const char *trilens_last_error(trilens_ctx *c);
 /* Library version string. */
 const char *trilens_version(void);
 
+/* ---- batches of independent instances ------------------------------------
+ * Many independent beam crossings of uneven size (each one the problem above)
+ * run as one problem: all instances' photons are concatenated per side, the
+ * instance number is placed above the Morton bits of every photon's key so
+ * that one sort and one hierarchy per side hold every instance as its own
+ * subtree, and the traversal starts from each instance's pair of subtree
+ * roots, so no pair of photons from different instances is ever tested.
+ * dt and kappa are shared by all instances. */
+
+/* Create a batch context from n_inst instances: a[q], b[q] are the two beams
+ * of instance q (device arrays as in trilens_beam; copied into library-owned
+ * concatenated arrays, so they need not outlive the call).  Photon indices of
+ * the context (hit lists of trilens_collide_step) are positions in the
+ * concatenation, instance by instance.  INVALID for n_inst outside
+ * [1, 65536], a bad beam, or more than 2^27 photons per side. */
+int trilens_batch_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam *b,
+                         int32_t n_inst, const trilens_params *p, trilens_stream_t stream);
+
+/* Run time steps first_step .. first_step+steps-1 of every instance (build +
+ * collide per step) as one captured CUDA graph, launched on the context's
+ * stream; the graph is captured on the first call and replayed while
+ * (first_step, steps, yields) stay the same.  yields (device, n_inst x 2
+ * doubles) receives, per instance, the number of colliding pairs and the sum
+ * of w_i w_j over the run.  Synchronises the stream at the end to check
+ * device status; on an internal overflow it enlarges the buffer and runs the
+ * graph again (the result is that of a complete run).  INVALID on a context
+ * that trilens_batch_create did not make. */
+int trilens_batch_run(trilens_ctx *c, int64_t first_step, int64_t steps, double *yields);
+
+/* One call: trilens_batch_create, trilens_batch_run(0, steps), destroy. */
+int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const trilens_params *p,
+                          int32_t n_inst, int64_t steps, double *yields, trilens_stream_t stream);
+
 /* Largest hit list trilens_yield_reduce_noalloc accepts (2^28 pairs). */
 #define TRILENS_NOALLOC_MAX_HITS (1ll << 28)
 

@@ -108,6 +108,14 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_timing.restype = ctypes.c_int
         L.trilens_debug_phase_ms.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.c_int]
         L.trilens_debug_phase_ms.restype = ctypes.c_int
+        L.trilens_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Beam),
+                                           ctypes.POINTER(Beam), i32, ctypes.POINTER(Params), vp]
+        L.trilens_batch_create.restype = ctypes.c_int
+        L.trilens_batch_run.argtypes = [vp, i64, i64, vp]
+        L.trilens_batch_run.restype = ctypes.c_int
+        L.trilens_collide_batch.argtypes = [ctypes.POINTER(Beam), ctypes.POINTER(Beam),
+                                            ctypes.POINTER(Params), i32, i64, vp, vp]
+        L.trilens_collide_batch.restype = ctypes.c_int
         L.trilens_yield_reduce_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.trilens_yield_reduce_noalloc.restype = ctypes.c_int
         _lib = L
@@ -297,3 +305,42 @@ def yield_reduce_noalloc(hits, n_hits: int, w_a=None, w_b=None, out=None, stream
     _check(lib().trilens_yield_reduce_noalloc(ptr(hits), int(n_hits), ptr(w_a), ptr(w_b), ptr(out),
                                              ctypes.c_void_p(st.cuda_stream)))
     return out
+
+
+class Batch(Collider):
+    """Many independent instances (pairs of beams) in one context.
+
+    ``run(first, steps)`` executes the steps of every instance as one captured
+    CUDA graph and returns per-instance (count, sum w w) as an (n_inst, 2)
+    numpy array.  ``build``/``collide``/``step_hits`` work on the
+    concatenation (photon indices are positions in it)."""
+
+    def __init__(self, beams_a: list, beams_b: list, dt_fs: float, kappa: float,
+                 precision: int = FP32_BAND, leaf_bucket: int = 0, stack_depth: int = 0,
+                 block_shape: int = 0, spin_limit: int = 0, stream=None):
+        torch = _torch()
+        self._torch = torch
+        assert len(beams_a) == len(beams_b) and len(beams_a) >= 1
+        self.n_inst = len(beams_a)
+        self.inst_a = [x if _is_dev(x) else to_device(x) for x in beams_a]
+        self.inst_b = [x if _is_dev(x) else to_device(x) for x in beams_b]
+        self.a, self.b = self.inst_a[0], self.inst_b[0]
+        self.params = Params(float(dt_fs), float(kappa), int(precision), int(leaf_bucket),
+                             int(stack_depth), int(block_shape), int(spin_limit))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        arr_a = (Beam * self.n_inst)(*[beam_struct(x) for x in self.inst_a])
+        arr_b = (Beam * self.n_inst)(*[beam_struct(x) for x in self.inst_b])
+        h = ctypes.c_void_p()
+        _check(lib().trilens_batch_create(ctypes.byref(h), arr_a, arr_b, self.n_inst,
+                                          ctypes.byref(self.params),
+                                          ctypes.c_void_p(self.stream.cuda_stream)))
+        self.ctx = h
+        self.offsets_a = np.cumsum([0] + [int(x["px"].numel()) for x in self.inst_a])
+        self.offsets_b = np.cumsum([0] + [int(x["px"].numel()) for x in self.inst_b])
+        self.yields = torch.zeros((self.n_inst, 2), dtype=torch.float64,
+                                  device=self.inst_a[0]["px"].device)
+
+    def run(self, first_step: int, steps: int):
+        _check(lib().trilens_batch_run(self.ctx, int(first_step), int(steps),
+                                       ctypes.c_void_p(self.yields.data_ptr())), self.ctx)
+        return self.yields.cpu().numpy().copy()

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "tl_common.cuh"
 #include "trilens.h"
@@ -25,6 +26,12 @@ cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1,
 cudaError_t launch_band(const TravArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_yield(const TravArgs &a, void *partials, int blocks, cudaStream_t s);
 size_t partial_bytes();
+cudaError_t launch_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *rootA,
+                                  const uint32_t *rootB, int n_inst, cudaStream_t s);
+cudaError_t launch_yield_inst(const TravArgs &a, const uint32_t *inst_of_a, double *yields,
+                              int blocks, cudaStream_t s);
+cudaError_t launch_step_finish(const TLCounters *ctr, const unsigned long long *left,
+                               unsigned *run_status, cudaStream_t s);
 }  // namespace tl
 
 static const int kMaxLevels = 24;
@@ -66,6 +73,23 @@ struct trilens_ctx {
   trilens_step_stats last{};
   double tot_count = 0, tot_weighted = 0;
   int debug_stall_sort = 0;
+  // several independent instances (batch contexts)
+  int n_inst = 1;
+  uint32_t *inst_of[2]{};     // device, instance of every photon
+  uint32_t *inst_root[2]{};   // device, subtree root (stack reference) per instance
+  double *inst_bounds[2]{};   // device, 12 doubles per instance
+  float4 *inst_box[2]{};      // device, Morton box of every instance for the current build
+  long long *inst_tmp = nullptr;
+  double *owned[2][8]{};      // concatenated inputs owned by a batch context
+  // graph-captured multi-step runs (batch contexts)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t g_first = -1, g_steps = 0;
+  double *g_yields = nullptr;
+  unsigned long long *spill_n = nullptr;  // device, counts of the two spill lists
+  unsigned *run_status = nullptr;
+  unsigned *run_status_host = nullptr;
+  int graph_passes = 12;
   // per-phase timing (events on the context's stream) and launch counts
   int timing = 0;
   cudaEvent_t ev[9][2][2]{};   // [phase][beam or 0][start, end]
@@ -248,6 +272,19 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFree(c->bounds_dev);
   cudaFreeHost(c->ctr_host);
   cudaFreeHost(c->build_status_host);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(c->inst_of[k]);
+    cudaFree(c->inst_root[k]);
+    cudaFree(c->inst_bounds[k]);
+    cudaFree(c->inst_box[k]);
+    for (int a = 0; a < 8; ++a) cudaFree(c->owned[k][a]);
+  }
+  cudaFree(c->inst_tmp);
+  cudaFree(c->spill_n);
+  cudaFree(c->run_status);
+  cudaFreeHost(c->run_status_host);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (int ph = 0; ph < 9; ++ph)
     for (int k = 0; k < 2; ++k)
       for (int e = 0; e < 2; ++e)
@@ -327,6 +364,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
+  CK(tl::sort_prepare());
   int dev_sm = 0;
   CK(cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, c->device));
   c->n_sm = dev_sm;
@@ -380,7 +418,13 @@ int trilens_build(trilens_ctx *c, int64_t step) {
     }
     tl::BuildBufs &w = c->w[k];
     tmark(c, PH_PROP, k, 0);
-    CK(tl::launch_propagate(c->beam[k], ct, (float)c->L64, lo, scale, c->bits[k], w, c->stream));
+    if (c->n_inst > 1) {
+      CK(tl::launch_inst_box(c->inst_bounds[k], c->n_inst, T, c->bits[k], c->inst_box[k],
+                             c->stream));
+      CK(cudaMemsetAsync(c->inst_root[k], 0xff, sizeof(uint32_t) * c->n_inst, c->stream));
+    }
+    CK(tl::launch_propagate(c->beam[k], ct, (float)c->L64, lo, scale, c->bits[k], w,
+                            c->n_inst > 1 ? c->inst_box[k] : nullptr, c->stream));
     tmark(c, PH_PROP, k, 1);
     CK(cudaMemsetAsync(w.visit, 0, sizeof(uint32_t) * (size_t)n, c->stream));
     tmark(c, PH_SORT, k, 0);
@@ -433,6 +477,8 @@ static tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   a.spill_cap = c->spill_cap;
   a.stack_depth = c->p.stack_depth;
   a.build_status = c->build_status;
+  a.spill_ctr = &c->ctr->spill;
+  a.in_count = nullptr;
   return a;
 }
 
@@ -449,8 +495,11 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
   while (true) {
     tl::TravArgs a = trav_args(c, ct);
     tmark(c, PH_EXPAND, 0, 0);
-    CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super, nonempty, c->build_status,
-                            c->stream));
+    CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super,
+                            c->n_inst > 1 ? 0 : nonempty, c->build_status, c->stream));
+    if (c->n_inst > 1)
+      CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
+                                   c->n_inst, c->stream));
     CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
                          c->stream));
     tmark(c, PH_EXPAND, 0, 1);
@@ -555,6 +604,248 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
       CK(cudaMemcpyAsync(hits, c->hits, sizeof(uint2) * ncopy, cudaMemcpyDeviceToDevice, c->stream));
   }
   return TRILENS_OK;
+}
+
+// ---- batches of independent instances ------------------------------------
+
+static int batch_prepare(trilens_ctx *c, const trilens_beam *const src[2], int32_t n_inst) {
+  // concatenate each side's instances into library-owned arrays
+  std::vector<tl::InstSrc> tab(n_inst);
+  int64_t tot[2] = {0, 0};
+  for (int k = 0; k < 2; ++k)
+    for (int q = 0; q < n_inst; ++q) tot[k] += src[k][q].n;
+  for (int k = 0; k < 2; ++k) {
+    int64_t off = 0;
+    for (int q = 0; q < n_inst; ++q) {
+      const trilens_beam &bq = src[k][q];
+      const double *ps[8] = {bq.px, bq.py, bq.pz, bq.dx, bq.dy, bq.dz, bq.E, bq.w};
+      for (int a = 0; a < 8; ++a) tab[q].p[a] = ps[a];
+      tab[q].n = bq.n;
+      tab[q].off = off;
+      off += bq.n;
+    }
+    for (int a = 0; a < 8; ++a) CK(dalloc(&c->owned[k][a], (size_t)std::max<int64_t>(tot[k], 1)));
+    CK(dalloc(&c->inst_of[k], (size_t)std::max<int64_t>(tot[k], 1)));
+    tl::InstSrc *dtab = nullptr;
+    double **dptr = nullptr;
+    CK(cudaMalloc((void **)&dtab, sizeof(tl::InstSrc) * n_inst));
+    CK(cudaMalloc((void **)&dptr, sizeof(double *) * 8));
+    CK(cudaMemcpyAsync(dtab, tab.data(), sizeof(tl::InstSrc) * n_inst, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(dptr, c->owned[k], sizeof(double *) * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(tl::launch_gather_instances(dtab, n_inst, tot[k], dptr, c->inst_of[k], c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(dtab);
+    cudaFree(dptr);
+  }
+  return TRILENS_OK;
+}
+
+int trilens_batch_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam *b,
+                         int32_t n_inst, const trilens_params *p, trilens_stream_t stream) {
+  if (!out) return TRILENS_ERR_INVALID;
+  *out = nullptr;
+  if (!a || !b || !p || n_inst < 1 || n_inst > 65536) return TRILENS_ERR_INVALID;
+  int64_t tot[2] = {0, 0}, nmax = 1;
+  for (int q = 0; q < n_inst; ++q) {
+    if (!beam_ok(&a[q]) || !beam_ok(&b[q])) return TRILENS_ERR_INVALID;
+    tot[0] += a[q].n;
+    tot[1] += b[q].n;
+    nmax = std::max<int64_t>(nmax, std::max(a[q].n, b[q].n));
+  }
+  if (tot[0] >= (1ll << 27) || tot[1] >= (1ll << 27)) return TRILENS_ERR_INVALID;
+  // a throwaway context holds the owned inputs while they are gathered
+  trilens_ctx tmp;
+  tmp.stream = (cudaStream_t)stream;
+  trilens_ctx *c = &tmp;
+  const trilens_beam *src[2] = {a, b};
+  int rc = batch_prepare(c, src, n_inst);
+  if (rc) return rc;
+  trilens_beam cat[2];
+  for (int k = 0; k < 2; ++k) {
+    cat[k].n = tot[k];
+    cat[k].px = tmp.owned[k][0]; cat[k].py = tmp.owned[k][1]; cat[k].pz = tmp.owned[k][2];
+    cat[k].dx = tmp.owned[k][3]; cat[k].dy = tmp.owned[k][4]; cat[k].dz = tmp.owned[k][5];
+    cat[k].E = tmp.owned[k][6]; cat[k].w = tmp.owned[k][7];
+  }
+  trilens_ctx *ctx = nullptr;
+  rc = trilens_create(&ctx, &cat[0], &cat[1], p, stream);
+  if (rc) {
+    for (int k = 0; k < 2; ++k) {
+      for (int q = 0; q < 8; ++q) cudaFree(tmp.owned[k][q]);
+      cudaFree(tmp.inst_of[k]);
+    }
+    return rc;
+  }
+  c = ctx;
+  for (int k = 0; k < 2; ++k) {
+    for (int q = 0; q < 8; ++q) {
+      c->owned[k][q] = tmp.owned[k][q];
+      tmp.owned[k][q] = nullptr;
+    }
+    c->inst_of[k] = tmp.inst_of[k];
+    tmp.inst_of[k] = nullptr;
+    c->w[k].inst_of = c->inst_of[k];
+  }
+  c->n_inst = n_inst;
+  int ib = 0;
+  while ((1 << ib) < n_inst) ++ib;
+  int lg = 0;
+  while ((1ll << lg) < nmax) ++lg;
+  const int bits = std::min((63 - ib) / 3, std::max(4, (lg + 2) / 3 + 3));
+  CK(cudaMalloc((void **)&c->inst_tmp, sizeof(long long) * 12 * n_inst));
+  for (int k = 0; k < 2; ++k) {
+    c->bits[k] = bits;
+    c->key_bits[k] = 3 * bits + ib;
+    c->w[k].inst_shift = 3 * bits;
+    CK(dalloc(&c->inst_root[k], (size_t)n_inst));
+    c->w[k].inst_root = c->inst_root[k];
+    CK(dalloc(&c->inst_bounds[k], (size_t)12 * n_inst));
+    CK(dalloc(&c->inst_box[k], (size_t)2 * n_inst));
+    CK(tl::launch_inst_bounds(c->beam[k], c->inst_of[k], n_inst, c->inst_tmp, c->inst_bounds[k],
+                              c->stream));
+  }
+  if (c->front_cap < (unsigned)n_inst + 4 * c->front_target + 64) {
+    c->front_cap = (unsigned)n_inst + 4 * c->front_target + 64;
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(c->front[k]);
+      CK(dalloc(&c->front[k], c->front_cap));
+    }
+  }
+  CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  CK(dalloc(&c->spill_n, 2));
+  CK(dalloc(&c->run_status, 1));
+  CK(cudaMallocHost((void **)&c->run_status_host, sizeof(unsigned)));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = c;
+  return TRILENS_OK;
+}
+
+// One step of a captured run: the collide sequence without host checks.  The
+// traversal runs a fixed number of passes with device-side list counts; work
+// left after them, and every overflow, is flagged in run_status.
+static int graph_collide(trilens_ctx *c, int64_t step, double *yields) {
+  const double ct = TL_C * ((double)step * c->p.dt_fs);
+  const int nonempty = c->beam[0].n > 0 && c->beam[1].n > 0;
+  tl::TravArgs a = trav_args(c, ct);
+  CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super,
+                          c->n_inst > 1 ? 0 : nonempty, c->build_status, c->stream));
+  if (c->n_inst > 1)
+    CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
+                                 c->n_inst, c->stream));
+  CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
+                       c->stream));
+  const int P = c->graph_passes;
+  for (int pass = 0; pass < P; ++pass) {
+    const int out = pass & 1, in = out ^ 1;
+    CK(cudaMemsetAsync(&c->spill_n[out], 0, sizeof(unsigned long long), c->stream));
+    CK(cudaMemsetAsync(&c->ctr->cursor, 0, sizeof(unsigned), c->stream));
+    tl::TravArgs ap = a;
+    ap.spill = c->spill[out];
+    ap.spill_ctr = &c->spill_n[out];
+    ap.in_count = pass ? &c->spill_n[in] : nullptr;
+    CK(tl::launch_traverse(ap, c->front[0], c->front[1], pass ? c->spill[in] : nullptr, 0,
+                           pass ? 0 : 1, c->budget, c->trav_blocks, c->trav_warps, c->stream));
+  }
+  if (!a.fp64) CK(tl::launch_band(a, c->n_sm * 4, c->stream));
+  CK(tl::launch_yield(a, c->partials, c->yield_blocks, c->stream));
+  if (yields && c->n_inst > 1)
+    CK(tl::launch_yield_inst(a, c->inst_of[0], yields, c->yield_blocks, c->stream));
+  CK(tl::launch_step_finish(c->ctr, &c->spill_n[(P - 1) & 1], c->run_status, c->stream));
+  return TRILENS_OK;
+}
+
+static int capture_run(trilens_ctx *c, int64_t first, int64_t steps, double *yields) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  const int timing = c->timing;
+  c->timing = 0;
+  cudaStream_t saved = c->stream;
+  c->stream = c->cap_stream;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = TRILENS_OK;
+  cudaError_t e = cudaMemsetAsync(c->run_status, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess && yields && c->n_inst > 1)
+    e = cudaMemsetAsync(yields, 0, sizeof(double) * 2 * c->n_inst, c->stream);
+  if (e != cudaSuccess) rc = fail(c, TRILENS_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+  for (int64_t k = first; rc == TRILENS_OK && k < first + steps; ++k) {
+    rc = trilens_build(c, k);
+    if (rc == TRILENS_OK) rc = graph_collide(c, k, yields);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->cap_stream, &g);
+  c->stream = saved;
+  c->timing = timing;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(c, TRILENS_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, TRILENS_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+  c->g_first = first;
+  c->g_steps = steps;
+  c->g_yields = yields;
+  return TRILENS_OK;
+}
+
+int trilens_batch_run(trilens_ctx *c, int64_t first_step, int64_t steps, double *yields) {
+  if (!c) return TRILENS_ERR_INVALID;
+  if (first_step < 0 || steps < 1 || !c->cap_stream)
+    return fail(c, TRILENS_ERR_INVALID, "batch_run needs a batch context, first_step >= 0, steps >= 1");
+  CK(cudaSetDevice(c->device));
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    if (!c->gexec || c->g_first != first_step || c->g_steps != steps || c->g_yields != yields) {
+      int rc = capture_run(c, first_step, steps, yields);
+      if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(c->gexec, c->stream));
+    CK(cudaMemcpyAsync(c->run_status_host, c->run_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->build_status_host, c->build_status, sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const unsigned st = *c->run_status_host | *c->build_status_host;
+    if (st & TL_ST_TIMEOUT) {
+      CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit");
+    }
+    if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF | TL_ST_PASSES)))
+      return TRILENS_OK;
+    // grow what overflowed and capture again
+    int rc;
+    if (st & TL_ST_HIT_OVF && (rc = grow(c, &c->hits, &c->hit_cap, 2 * c->hit_cap))) return rc;
+    if (st & TL_ST_BAND_OVF && (rc = grow(c, &c->band, &c->band_cap, 2 * c->band_cap))) return rc;
+    if (st & TL_ST_SPILL_OVF) {
+      unsigned long long cap = c->spill_cap;
+      if ((rc = grow(c, &c->spill[0], &cap, 2 * c->spill_cap))) return rc;
+      cudaFree(c->spill[1]);
+      CK(dalloc(&c->spill[1], cap));
+      c->spill_cap = cap;
+    }
+    if (st & TL_ST_PASSES) c->graph_passes *= 2;
+    if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+  }
+  return fail(c, TRILENS_ERR_STACK, "batch run kept overflowing");
+}
+
+int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const trilens_params *p,
+                          int32_t n_inst, int64_t steps, double *yields, trilens_stream_t stream) {
+  if (!yields) return TRILENS_ERR_INVALID;
+  trilens_ctx *c = nullptr;
+  int rc = trilens_batch_create(&c, a, b, n_inst, p, stream);
+  if (rc) return rc;
+  rc = trilens_batch_run(c, 0, steps, yields);
+  trilens_destroy(c);
+  return rc;
 }
 
 int trilens_step_stats_get(trilens_ctx *c, trilens_step_stats *out) {

@@ -81,6 +81,124 @@ cudaError_t launch_beam_bounds(const TLBeam &b, double *out12, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- instances
+
+// Per-instance min and max of p0 and d (12 ordered int64 per instance, laid
+// out like k_beam_bounds).  A warp whose lanes share one instance reduces
+// first and issues one atomic per quantity.
+__global__ void k_inst_bounds(TLBeam b, const uint32_t *inst_of, long long *out) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; i0 < b.n;
+       i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + lane;
+    const bool valid = i < b.n;
+    const uint32_t q = valid ? inst_of[i] : 0xffffffffu;
+    const uint32_t q0 = __shfl_sync(0xffffffffu, q, 0);
+    const bool uniform = __all_sync(0xffffffffu, !valid || q == q0);
+    long long v[12];
+    if (valid) {
+      const double x[6] = {b.px[i], b.py[i], b.pz[i], b.dx[i], b.dy[i], b.dz[i]};
+      for (int c = 0; c < 6; ++c) v[c] = v[6 + c] = ord64(x[c]);
+    } else {
+      for (int c = 0; c < 6; ++c) {
+        v[c] = 0x7fffffffffffffffLL;
+        v[6 + c] = -0x7fffffffffffffffLL - 1;
+      }
+    }
+    if (uniform) {
+      for (int c = 0; c < 6; ++c)
+        for (int off = 16; off; off >>= 1) {
+          v[c] = min(v[c], __shfl_xor_sync(0xffffffffu, v[c], off));
+          v[6 + c] = max(v[6 + c], __shfl_xor_sync(0xffffffffu, v[6 + c], off));
+        }
+      if (lane == 0)
+        for (int c = 0; c < 6; ++c) {
+          atomicMin(&out[12 * (size_t)q0 + c], v[c]);
+          atomicMax(&out[12 * (size_t)q0 + 6 + c], v[6 + c]);
+        }
+    } else if (valid) {
+      for (int c = 0; c < 6; ++c) {
+        atomicMin(&out[12 * (size_t)q + c], v[c]);
+        atomicMax(&out[12 * (size_t)q + 6 + c], v[6 + c]);
+      }
+    }
+  }
+}
+
+__global__ void k_inst_bounds_init(long long *out, int n_inst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 12 * n_inst) out[t] = (t % 12) < 6 ? 0x7fffffffffffffffLL : -0x7fffffffffffffffLL - 1;
+}
+
+__global__ void k_inst_bounds_decode(const long long *in, double *out, int n_inst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 12 * n_inst) {
+    long long i = in[t];
+    i = i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
+    out[t] = __longlong_as_double(i);
+  }
+}
+
+// Morton quantisation box of every instance for the step with travel
+// T = c t_k + L/2 to the swept segment's centre (lo, then scale per axis).
+__global__ void k_inst_box(const double *bounds, int n_inst, double T, unsigned maxq,
+                           float4 *box) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_inst) return;
+  const double *bd = bounds + 12 * (size_t)q;
+  float lo[3], sc[3];
+  for (int a = 0; a < 3; ++a) {
+    const double l = bd[a] + T * bd[3 + a], h = bd[6 + a] + T * bd[9 + a];
+    lo[a] = (float)l;
+    sc[a] = h > l ? (float)((double)maxq / (h - l)) : 0.0f;
+  }
+  box[2 * q] = make_float4(lo[0], lo[1], lo[2], 0.f);
+  box[2 * q + 1] = make_float4(sc[0], sc[1], sc[2], 0.f);
+}
+
+// Concatenate the instances' input arrays into one beam and record the
+// instance of every photon.
+__global__ void k_gather_instances(const InstSrc *src, int n_inst, int64_t n, double *const *dst,
+                                   uint32_t *inst_of) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lo = 0, hi = n_inst - 1;  // last instance whose offset <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (src[mid].off <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const InstSrc &s = src[lo];
+  const int64_t j = i - s.off;
+  for (int k = 0; k < 8; ++k) dst[k][i] = s.p[k] ? s.p[k][j] : 1.0;
+  inst_of[i] = (uint32_t)lo;
+}
+
+cudaError_t launch_inst_bounds(const TLBeam &b, const uint32_t *inst_of, int n_inst,
+                               long long *tmp, double *out, cudaStream_t s) {
+  const int nt = 12 * n_inst;
+  k_inst_bounds_init<<<(nt + 255) / 256, 256, 0, s>>>(tmp, n_inst);
+  if (b.n > 0) {
+    int64_t nb = (b.n + 255) / 256;
+    k_inst_bounds<<<(int)(nb < 4096 ? nb : 4096), 256, 0, s>>>(b, inst_of, tmp);
+  }
+  k_inst_bounds_decode<<<(nt + 255) / 256, 256, 0, s>>>(tmp, out, n_inst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inst_box(const double *bounds, int n_inst, double T, int bits, float4 *box,
+                            cudaStream_t s) {
+  k_inst_box<<<(n_inst + 127) / 128, 128, 0, s>>>(bounds, n_inst, T, (1u << bits) - 1u, box);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_instances(const InstSrc *src, int n_inst, int64_t n, double *const *dst,
+                                    uint32_t *inst_of, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_instances<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n_inst, n, dst, inst_of);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- Morton
 
 // spread the low 21 bits of x to every third bit (bit interleaving by masks)
@@ -103,12 +221,24 @@ __device__ __forceinline__ unsigned quant(float c, float lo, float scale, unsign
 // One thread per photon: P = p0 + (c t_k) d in FP64 (the definition's
 // operation order), rounded to the FP32 SoA; key of the swept segment's
 // centre P + (L/2) d quantised in the beam's box.
+// With several instances (inst_of != NULL) each photon is quantised in its
+// own instance's box and its instance number sits above the Morton bits, so
+// one sort orders the photons by instance, then along the Morton curve.
 __global__ void __launch_bounds__(256) k_propagate(TLBeam b, double ct, float halfL, float3 lo,
                                                    float3 scale, unsigned maxq, float4 *pos_u,
                                                    float4 *dir_u, unsigned long long *key,
-                                                   uint32_t *val) {
+                                                   uint32_t *val, const uint32_t *inst_of,
+                                                   const float4 *inst_box, int inst_shift) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= b.n) return;
+  unsigned long long ikey = 0ull;
+  if (inst_of) {
+    const uint32_t q = inst_of[i];
+    const float4 bl = inst_box[2 * q], bs = inst_box[2 * q + 1];
+    lo = make_float3(bl.x, bl.y, bl.z);
+    scale = make_float3(bs.x, bs.y, bs.z);
+    ikey = (unsigned long long)q << inst_shift;
+  }
   const double dx = b.dx[i], dy = b.dy[i], dz = b.dz[i];
   const double Px = __dadd_rn(b.px[i], __dmul_rn(ct, dx));
   const double Py = __dadd_rn(b.py[i], __dmul_rn(ct, dy));
@@ -122,18 +252,20 @@ __global__ void __launch_bounds__(256) k_propagate(TLBeam b, double ct, float ha
   const float cx = fmaf(halfL, d.x, p.x), cy = fmaf(halfL, d.y, p.y), cz = fmaf(halfL, d.z, p.z);
   const unsigned qx = quant(cx, lo.x, scale.x, maxq), qy = quant(cy, lo.y, scale.y, maxq),
                  qz = quant(cz, lo.z, scale.z, maxq);
-  key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+  key[i] = ikey | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
   val[i] = (uint32_t)i;
 }
 
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
-                             const float box_scale[3], int bits, BuildBufs &w, cudaStream_t s) {
+                             const float box_scale[3], int bits, BuildBufs &w,
+                             const float4 *inst_box, cudaStream_t s) {
   if (b.n <= 0) return cudaSuccess;
   unsigned maxq = (1u << bits) - 1u;
   int blocks = (int)((b.n + 255) / 256);
   k_propagate<<<blocks, 256, 0, s>>>(b, ct, 0.5f * L, make_float3(box_lo[0], box_lo[1], box_lo[2]),
                                      make_float3(box_scale[0], box_scale[1], box_scale[2]), maxq,
-                                     w.pos_u, w.dir_u, w.key[0], w.val[0]);
+                                     w.pos_u, w.dir_u, w.key[0], w.val[0], w.inst_of, inst_box,
+                                     3 * bits);
   return cudaGetLastError();
 }
 
@@ -178,25 +310,35 @@ __device__ __forceinline__ void empty_box(float4 &b1, float4 &b2) {
   b2 = make_float4(inf, -inf, -inf, -inf);
 }
 
+// With several instances (inst_root != NULL) a subtree never mixes instances
+// below its instance's root: a node spanning two instances is never a leaf
+// bucket, and the root of each instance's subtree (the first node on the path
+// down that lies inside one instance) is recorded as a stack reference.
 __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__restrict__ key,
                                                 int64_t n, int bucket, TLNode *nodes,
                                                 uint32_t *parent_leaf, uint32_t *parent_node,
-                                                const unsigned *build_status) {
+                                                const unsigned *build_status, uint32_t *inst_root,
+                                                int inst_shift) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (*build_status & TL_ST_TIMEOUT) return;  // keys unsorted: the build is abandoned
   const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
+  const bool multi = inst_root != nullptr;
   if (i == 0) {
     // the super root: one child (the whole beam) in slot 0, slot 1 empty
     TLNode sr;
     sr.b0 = make_float4(0.f, 0.f, 0.f, 0.f);
     sr.b1 = make_float4(0.f, 0.f, 0.f, 0.f);
     empty_box(sr.b1, sr.b2);
-    int ref0 = (n <= bucket) ? (int)(TL_FLAG | 0u) : 0;
+    const bool one_inst = !multi || (key[0] >> inst_shift) == (key[n - 1] >> inst_shift);
+    const bool root_bucket = n <= bucket && one_inst;
+    int ref0 = root_bucket ? (int)(TL_FLAG | 0u) : 0;
     sr.c = make_int4(ref0, (int)TL_NONE, (int)n, 0);
     // boxes are written by the refit; write refs and the empty slot now
     nodes[super] = sr;
     if (n > 1) parent_node[0] = (super << 1) | 0u;
     else parent_leaf[0] = (super << 1) | 0u;
+    if (multi && one_inst)
+      inst_root[key[0] >> inst_shift] = root_bucket ? (TL_FLAG | (super << 1)) : 0u;
   }
   if (i >= n - 1) return;
   int dl = kdelta(key, n, i, i - 1), dr = kdelta(key, n, i, i + 1);
@@ -217,8 +359,20 @@ __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__rest
   int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
   int64_t first = i < j ? i : j, last = i < j ? j : i;
   int64_t cl = gamma - first + 1, cr = last - gamma;
-  int refl = cl <= bucket ? (int)(TL_FLAG | (uint32_t)first) : (int)gamma;
-  int refr = cr <= bucket ? (int)(TL_FLAG | (uint32_t)(gamma + 1)) : (int)(gamma + 1);
+  bool lone = true, rone = true;  // child inside one instance
+  if (multi) {
+    const unsigned long long kf = key[first] >> inst_shift, kg = key[gamma] >> inst_shift,
+                             kh = key[gamma + 1] >> inst_shift, kl = key[last] >> inst_shift;
+    lone = kf == kg;
+    rone = kh == kl;
+    if (kf != kl) {  // this node spans instances: a one-instance child roots its instance
+      if (lone) inst_root[kf] = cl <= bucket ? (TL_FLAG | ((uint32_t)i << 1)) : (uint32_t)gamma;
+      if (rone)
+        inst_root[kl] = cr <= bucket ? (TL_FLAG | ((uint32_t)i << 1) | 1u) : (uint32_t)(gamma + 1);
+    }
+  }
+  int refl = (cl <= bucket && lone) ? (int)(TL_FLAG | (uint32_t)first) : (int)gamma;
+  int refr = (cr <= bucket && rone) ? (int)(TL_FLAG | (uint32_t)(gamma + 1)) : (int)(gamma + 1);
   nodes[i].c = make_int4(refl, refr, (int)cl, (int)cr);
   if (first == gamma) parent_leaf[gamma] = ((uint32_t)i << 1) | 0u;
   else parent_node[gamma] = ((uint32_t)i << 1) | 0u;
@@ -231,7 +385,8 @@ cudaError_t launch_karras(BuildBufs &w, int64_t n, int sel, int bucket, cudaStre
   int64_t threads = n > 1 ? n - 1 : 1;
   k_karras<<<(int)((threads + 255) / 256), 256, 0, s>>>(w.key[sel], n, bucket, w.nodes,
                                                         w.parent_leaf, w.parent_node,
-                                                        w.build_status);
+                                                        w.build_status, w.inst_root,
+                                                        w.inst_shift);
   return cudaGetLastError();
 }
 

@@ -55,7 +55,8 @@ enum {
   TL_ST_SPILL_OVF = 4,
   TL_ST_FRONT_OVF = 8,
   TL_ST_TIMEOUT = 16,
-  TL_ST_LEAFQ = 32
+  TL_ST_LEAFQ = 32,
+  TL_ST_PASSES = 64  // graph mode: traversal work left after the fixed passes
 };
 
 // Per-step device counters; zeroed by the step's init kernel.
@@ -115,6 +116,18 @@ struct TLNarrowConst {
 
 // Build-time launch helpers (defined in the .cu files).
 namespace tl {
+// one instance's input arrays (px py pz dx dy dz E w; w may be NULL) and
+// its first photon in the concatenated beam
+struct InstSrc {
+  const double *p[8];
+  long long n, off;
+};
+cudaError_t launch_inst_bounds(const TLBeam &b, const uint32_t *inst_of, int n_inst,
+                               long long *tmp, double *out, cudaStream_t s);
+cudaError_t launch_inst_box(const double *bounds, int n_inst, double T, int bits, float4 *box,
+                            cudaStream_t s);
+cudaError_t launch_gather_instances(const InstSrc *src, int n_inst, int64_t n, double *const *dst,
+                                    uint32_t *inst_of, cudaStream_t s);
 struct BuildBufs {
   float4 *pos_u, *dir_u;      // unsorted SoA32
   float4 *pos, *dir;          // sorted SoA32
@@ -129,6 +142,10 @@ struct BuildBufs {
   uint32_t *sort_tile;    // 8 tile counters
   int64_t sort_tiles;
   unsigned *build_status;  // shared status word of the context's builds
+  // several independent instances in one beam (NULL / 0 for a single one)
+  const uint32_t *inst_of;  // instance of each input photon
+  uint32_t *inst_root;      // per instance: stack reference of its subtree root
+  int inst_shift;           // bit position of the instance number in the key
 };
 
 // Arguments of the traversal kernels (tl_traverse.cu).
@@ -147,10 +164,14 @@ struct TravArgs {
   unsigned long long spill_cap;
   int stack_depth;
   const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal
+  unsigned long long *spill_ctr;        // where pairs handed to the next pass are counted
+  const unsigned long long *in_count;   // device count of the input list (NULL: argument)
 };
 
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
-                             const float box_scale[3], int bits, BuildBufs &w, cudaStream_t s);
+                             const float box_scale[3], int bits, BuildBufs &w,
+                             const float4 *inst_box, cudaStream_t s);
+cudaError_t sort_prepare();
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
                         int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s);
 cudaError_t launch_gather(BuildBufs &w, int64_t n, int sel, cudaStream_t s);

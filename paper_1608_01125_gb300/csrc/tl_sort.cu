@@ -189,6 +189,12 @@ __global__ void __launch_bounds__(256) k_sort_pass(
   }
 }
 
+// Kernel attributes of the sort (before any launch or stream capture).
+cudaError_t sort_prepare() {
+  return cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(SortSmem));
+}
+
 // Sort w.key[0]/w.val[0] by the low key_bits bits.  *out_sel receives the
 // buffer index holding the result.
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
@@ -205,13 +211,6 @@ cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_li
     int blocks = (int)(nb < 2048 ? nb : 2048);
     k_sort_hist<<<blocks, 256, 0, s>>>(w.key[0], n, passes, w.sort_hist);
     k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_hist, passes);
-  }
-  static bool attr_done = false;
-  if (!attr_done) {
-    if ((e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sizeof(SortSmem))))
-      return e;
-    attr_done = true;
   }
   int sel = 0;
   for (int p = 0; p < passes; ++p) {

@@ -117,6 +117,18 @@ __global__ void k_step_init(TLCounters *ctr, uint2 *F0, uint32_t superA, uint32_
   }
 }
 
+// Several instances: the frontier starts from each instance's pair of
+// subtree roots, so no pair of photons from different instances is tested.
+__global__ void k_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *rootA,
+                                 const uint32_t *rootB, int n_inst) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_inst || (ctr->status & TL_ST_TIMEOUT)) return;
+  const uint32_t ra = rootA[q], rb = rootB[q];
+  if (ra == TL_NONE || rb == TL_NONE) return;
+  const unsigned idx = atomicAdd(&ctr->counts[0], 1u);
+  F0[idx] = make_uint2(ra, rb);
+}
+
 // ------------------------------------------------------------ frontier
 
 // One block expands the root pair breadth first, level by level, until the
@@ -276,7 +288,10 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
     nsrc = ctr->counts[lvl];
   } else {
     src = list;
-    nsrc = list_n;
+    nsrc = a.in_count ? *a.in_count : list_n;
+    // an input list that overflowed holds only spill_cap entries (the
+    // overflow is already flagged by its producer)
+    if (nsrc > a.spill_cap) nsrc = a.spill_cap;
   }
   const unsigned lt = (1u << lane) - 1u;
   int sp = 0, nq = 0, iters = 0;
@@ -286,7 +301,7 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
       // this item is large: hand the rest of it (the whole stack) to the next
       // pass, where its pieces are spread over all warps
       unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(&ctr->spill, (unsigned long long)sp);
+      if (lane == 0) base = atomicAdd(a.spill_ctr, (unsigned long long)sp);
       base = __shfl_sync(0xffffffffu, base, 0);
       for (int e = lane; e < sp; e += 32) {
         if (base + e < a.spill_cap) a.spill[base + e] = stack[e];
@@ -341,7 +356,7 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
       if (slot < D) {
         stack[slot] = o;
       } else {
-        const unsigned long long idx = atomicAdd(&ctr->spill, 1ull);
+        const unsigned long long idx = atomicAdd(a.spill_ctr, 1ull);
         if (idx < a.spill_cap) a.spill[idx] = o;
         else atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
       }
@@ -474,6 +489,30 @@ __global__ void __launch_bounds__(256) k_yield(TravArgs a, Partial *partials) {
   }
 }
 
+// Per-instance yield: count and sum of w_i w_j of each instance's hits,
+// accumulated into yields[2 * inst], yields[2 * inst + 1].
+__global__ void __launch_bounds__(256) k_yield_inst(TravArgs a, const uint32_t *inst_of_a,
+                                                    double *yields) {
+  const unsigned long long n = min(a.ctr->hits, a.hit_cap);
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint2 h = a.hits[i];
+    const double wi = a.mA.w ? a.mA.w[h.x] : 1.0, wj = a.mB.w ? a.mB.w[h.y] : 1.0;
+    const uint32_t q = inst_of_a[h.x];
+    atomicAdd(&yields[2 * q], 1.0);
+    atomicAdd(&yields[2 * q + 1], wi * wj);
+  }
+}
+
+// End of a step in graph mode: keep the step's status bits, and flag work
+// that the fixed number of traversal passes did not finish.
+__global__ void k_step_finish(const TLCounters *ctr, const unsigned long long *left,
+                              unsigned *run_status) {
+  unsigned st = ctr->status;
+  if (*left) st |= TL_ST_PASSES;
+  if (st) atomicOr(run_status, st);
+}
+
 // ------------------------------------------------------------ host launchers
 
 size_t traverse_smem(int warps, int depth) {
@@ -533,5 +572,23 @@ cudaError_t launch_yield(const TravArgs &a, void *partials, int blocks, cudaStre
 }
 
 size_t partial_bytes() { return sizeof(Partial); }
+
+cudaError_t launch_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *rootA,
+                                  const uint32_t *rootB, int n_inst, cudaStream_t s) {
+  k_seed_instances<<<(n_inst + 255) / 256, 256, 0, s>>>(ctr, F0, rootA, rootB, n_inst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_yield_inst(const TravArgs &a, const uint32_t *inst_of_a, double *yields,
+                              int blocks, cudaStream_t s) {
+  k_yield_inst<<<blocks, 256, 0, s>>>(a, inst_of_a, yields);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_finish(const TLCounters *ctr, const unsigned long long *left,
+                               unsigned *run_status, cudaStream_t s) {
+  k_step_finish<<<1, 1, 0, s>>>(ctr, left, run_status);
+  return cudaGetLastError();
+}
 
 }  // namespace tl
