@@ -241,6 +241,8 @@ def run_ours(args, wl):
             band += st["band"]
         return hits, tests, band
 
+    tuned = col.autotune([2, 4, 40], os.path.join(ROOT, "paper_1608_01125_gb300",
+                                                   "_tuning_cache.json")) if args.tune else col.tuning()
     for _ in range(max(args.warmup, 0)):
         one_run()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -338,11 +340,51 @@ def run_ours(args, wl):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 16},
         "gpu_launches": int(sum(launches.values())),
+        "tuning": tuned,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batch(args):
+    """The batching workload (not the default line): 256 independent
+    instances, 1,024-262,144 photons per beam, 16 steps, one CUDA graph."""
+    import torch
+
+    from paper_1608_01125_gb300 import binding
+    torch.cuda.set_device(0)
+    wls = [synth.batch_instance(i) for i in range(256)]
+    A, B = zip(*[synth.beams(w) for w in wls])
+    bt = binding.Batch(list(A), list(B), wls[0].dt, wls[0].kappa)
+    tuned = bt.autotune([7, 8], os.path.join(ROOT, "paper_1608_01125_gb300",
+                                             "_tuning_cache.json")) if args.tune else bt.tuning()
+    for _ in range(max(args.warmup, 1)):
+        y = bt.run(0, 16)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y = bt.run(0, 16)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    pairs = sum(len(a["px"]) * len(b["px"]) for a, b in zip(A, B)) * 16
+    line = {"metric": "photon-pair tests/s, 256 batched instances", "value": pairs * args.steps / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch_256", "instances": 256,
+                       "photons_per_beam": [min(len(a["px"]) for a in A), max(len(a["px"]) for a in A)],
+                       "photons_total_per_side": int(sum(len(a["px"]) for a in A)), "time_steps": 16,
+                       "graph": True, "l2": "flushed (256 MiB write) before every timed step"},
+            "hits_per_run": float(y[:, 0].sum()), "tuning": tuned}
+    print(json.dumps(line), flush=True)
+    bt.close()
 
 
 def main():
@@ -352,13 +394,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the autotuner (default knobs)")
     ap.add_argument("--photons", type=int, default=1 << 20)
+    ap.add_argument("--workload", default="headon_2x1M", choices=("headon_2x1M", "batch256"))
     ap.add_argument("--first-step", type=int, default=0,
                     help="first time step of each run (profiling a slice of the run)")
     ap.add_argument("--time-steps", type=int, default=0,
                     help="time steps per run (0: the workload's 64)")
     args = ap.parse_args()
     wl = synth.headon_1m(n=args.photons)
+    if args.workload == "batch256":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args, wl)
     else:

@@ -178,6 +178,32 @@ int trilens_batch_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
 int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const trilens_params *p,
                           int32_t n_inst, int64_t steps, double *yields, trilens_stream_t stream);
 
+/* ---- tuning -----------------------------------------------------------------
+ * The hit set never depends on these knobs; only the time does.
+ *   leaf_bucket  photons per hierarchy leaf (1..32)
+ *   stack_depth  traversal stack entries per warp, in shared memory (64..4096)
+ *   block_shape  traversal warps per block (1..16)
+ *   budget       traversal iterations a warp spends on one work item before it
+ *                hands the rest to the next pass (0 = never) */
+
+/* Set the knobs; the next trilens_collide_step needs a fresh trilens_build.
+ * INVALID if a knob is out of range or the shape does not fit an SM. */
+int trilens_set_tuning(trilens_ctx *c, int32_t leaf_bucket, int32_t stack_depth,
+                       int32_t block_shape, int32_t budget);
+
+/* Current knobs into out[4] (leaf_bucket, stack_depth, block_shape, budget). */
+int trilens_get_tuning(trilens_ctx *c, int32_t out[4]);
+
+/* Autotuner.  If cache_path (a JSON file; NULL = no cache) holds an entry for
+ * this context's configuration class (beam sizes rounded to powers of two,
+ * instance count, precision, SM count), apply it.  Otherwise time build +
+ * collide of the n_steps sample steps while sweeping each knob in turn (the
+ * others held at the best so far), apply the fastest, and record it in the
+ * cache.  Tuning runs are not added to the yield.  chosen (host, 4 ints) may
+ * be NULL.  Synchronises the stream. */
+int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
+                     const char *cache_path, int32_t chosen[4]);
+
 /* Largest hit list trilens_yield_reduce_noalloc accepts (2^28 pairs). */
 #define TRILENS_NOALLOC_MAX_HITS (1ll << 28)
 

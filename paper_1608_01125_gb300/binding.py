@@ -116,6 +116,13 @@ def lib() -> ctypes.CDLL:
         L.trilens_collide_batch.argtypes = [ctypes.POINTER(Beam), ctypes.POINTER(Beam),
                                             ctypes.POINTER(Params), i32, i64, vp, vp]
         L.trilens_collide_batch.restype = ctypes.c_int
+        L.trilens_set_tuning.argtypes = [vp, i32, i32, i32, i32]
+        L.trilens_set_tuning.restype = ctypes.c_int
+        L.trilens_get_tuning.argtypes = [vp, ctypes.POINTER(i32)]
+        L.trilens_get_tuning.restype = ctypes.c_int
+        L.trilens_autotune.argtypes = [vp, ctypes.POINTER(i64), i32, ctypes.c_char_p,
+                                       ctypes.POINTER(i32)]
+        L.trilens_autotune.restype = ctypes.c_int
         L.trilens_yield_reduce_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.trilens_yield_reduce_noalloc.restype = ctypes.c_int
         _lib = L
@@ -247,6 +254,22 @@ class Collider:
         ln = (ctypes.c_int64 * 9)()
         _check(lib().trilens_debug_phase_ms(self.ctx, ms, ln, int(bool(reset))), self.ctx)
         return dict(zip(PHASES, list(ms))), dict(zip(PHASES, list(ln)))
+
+    def set_tuning(self, leaf_bucket: int, stack_depth: int, block_shape: int, budget: int):
+        _check(lib().trilens_set_tuning(self.ctx, leaf_bucket, stack_depth, block_shape, budget),
+               self.ctx)
+
+    def tuning(self) -> dict:
+        v = (ctypes.c_int32 * 4)()
+        _check(lib().trilens_get_tuning(self.ctx, v), self.ctx)
+        return dict(zip(("leaf_bucket", "stack_depth", "block_shape", "budget"), list(v)))
+
+    def autotune(self, steps, cache_path: str | None = None) -> dict:
+        st = (ctypes.c_int64 * len(steps))(*[int(x) for x in steps])
+        v = (ctypes.c_int32 * 4)()
+        _check(lib().trilens_autotune(self.ctx, st, len(steps),
+                                      cache_path.encode() if cache_path else None, v), self.ctx)
+        return dict(zip(("leaf_bucket", "stack_depth", "block_shape", "budget"), list(v)))
 
     def debug_set_spin_limit(self, limit: int):
         _check(lib().trilens_debug_set_spin_limit(self.ctx, int(limit)), self.ctx)

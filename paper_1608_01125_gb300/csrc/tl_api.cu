@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "tl_common.cuh"
@@ -846,6 +847,201 @@ int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const tr
   rc = trilens_batch_run(c, 0, steps, yields);
   trilens_destroy(c);
   return rc;
+}
+
+// ---- tuning ---------------------------------------------------------------
+
+static int apply_tuning(trilens_ctx *c, int bucket, int depth, int warps, int budget) {
+  if (bucket < 1 || bucket > 32 || depth < 64 || depth > 4096 || warps < 1 || warps > 16 ||
+      budget < 0)
+    return fail(c, TRILENS_ERR_INVALID, "tuning out of range");
+  int bps = 0;
+  CK(tl::traverse_config(c->p.precision == TRILENS_FP64, warps, depth, &bps));
+  if (bps < 1) return fail(c, TRILENS_ERR_INVALID, "traversal shape does not fit an SM");
+  c->p.leaf_bucket = bucket;
+  c->p.stack_depth = depth;
+  c->p.block_shape = warps;
+  c->trav_warps = warps;
+  c->trav_blocks = bps * c->n_sm;
+  c->budget = budget;
+  c->front_target = (unsigned)std::min<long long>(2ll * c->trav_blocks * c->trav_warps, 1 << 16);
+  const unsigned need_front = (unsigned)c->n_inst + 4 * c->front_target + 64;
+  if (need_front > c->front_cap) {
+    c->front_cap = need_front;
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(c->front[k]);
+      c->front[k] = nullptr;
+      CK(dalloc(&c->front[k], c->front_cap));
+    }
+  }
+  const unsigned long long need_spill =
+      2ull * c->trav_blocks * c->trav_warps * (unsigned long long)depth;
+  if (need_spill > c->spill_cap) {
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(c->spill[k]);
+      c->spill[k] = nullptr;
+      CK(dalloc(&c->spill[k], need_spill));
+    }
+    c->spill_cap = need_spill;
+  }
+  if (c->gexec) {  // a captured run holds the old shapes
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->built_step = -1;  // the leaf bucket changes the hierarchy: build again
+  return TRILENS_OK;
+}
+
+int trilens_set_tuning(trilens_ctx *c, int32_t leaf_bucket, int32_t stack_depth,
+                       int32_t block_shape, int32_t budget) {
+  if (!c) return TRILENS_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  return apply_tuning(c, leaf_bucket, stack_depth, block_shape, budget);
+}
+
+int trilens_get_tuning(trilens_ctx *c, int32_t out[4]) {
+  if (!c || !out) return TRILENS_ERR_INVALID;
+  out[0] = c->p.leaf_bucket;
+  out[1] = c->p.stack_depth;
+  out[2] = c->p.block_shape;
+  out[3] = c->budget;
+  return TRILENS_OK;
+}
+
+// key of a configuration class: sizes rounded to powers of two, precision,
+// SM count
+static void tuning_key(trilens_ctx *c, char *key, size_t len) {
+  int la = 0, lb = 0;
+  while ((1ll << la) < std::max<int64_t>(c->beam[0].n, 1)) ++la;
+  while ((1ll << lb) < std::max<int64_t>(c->beam[1].n, 1)) ++lb;
+  snprintf(key, len, "nA2^%d_nB2^%d_inst%d_prec%d_sm%d", la, lb, c->n_inst, c->p.precision,
+           c->n_sm);
+}
+
+static bool cache_lookup(const char *path, const char *key, int v[4]) {
+  if (!path) return false;
+  FILE *f = fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool found = false;
+  while (!found && fgets(line, sizeof(line), f)) {
+    char k[256];
+    int a, b, cc, d;
+    if (sscanf(line, " {\"key\": \"%255[^\"]\", \"leaf_bucket\": %d, \"stack_depth\": %d, "
+                     "\"block_shape\": %d, \"budget\": %d", k, &a, &b, &cc, &d) == 5 &&
+        strcmp(k, key) == 0) {
+      v[0] = a; v[1] = b; v[2] = cc; v[3] = d;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+static void cache_store(const char *path, const char *key, const int v[4], double ms) {
+  if (!path) return;
+  // keep the other keys' lines, replace this key's
+  std::vector<std::string> keep;
+  if (FILE *f = fopen(path, "r")) {
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+      std::string l(line);
+      if (l.find("\"key\"") != std::string::npos &&
+          l.find(std::string("\"") + key + "\"") == std::string::npos) {
+        while (!l.empty() && (l.back() == '\n' || l.back() == ',')) l.pop_back();
+        keep.push_back(l);
+      }
+    }
+    fclose(f);
+  }
+  char mine[512];
+  snprintf(mine, sizeof(mine),
+           " {\"key\": \"%s\", \"leaf_bucket\": %d, \"stack_depth\": %d, \"block_shape\": %d, "
+           "\"budget\": %d, \"ms\": %.4f}",
+           key, v[0], v[1], v[2], v[3], ms);
+  keep.push_back(mine);
+  std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "[\n");
+  for (size_t i = 0; i < keep.size(); ++i)
+    fprintf(f, "%s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+  fprintf(f, "]\n");
+  fclose(f);
+  rename(tmp.c_str(), path);
+}
+
+// time build + collide over the sample steps with the current tuning
+static int time_steps(trilens_ctx *c, const int64_t *steps, int n, double *ms) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const double keep_count = c->tot_count, keep_w = c->tot_weighted;
+  CK(cudaEventRecord(e0, c->stream));
+  for (int i = 0; i < n; ++i) {
+    int rc = trilens_build(c, steps[i]);
+    if (!rc) rc = trilens_collide_step(c, steps[i], nullptr, 0, nullptr);
+    if (rc) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc;
+    }
+  }
+  CK(cudaEventRecord(e1, c->stream));
+  CK(cudaEventSynchronize(e1));
+  float f = 0.f;
+  CK(cudaEventElapsedTime(&f, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tot_count = keep_count;  // tuning runs do not count towards the yield
+  c->tot_weighted = keep_w;
+  *ms = f;
+  return TRILENS_OK;
+}
+
+int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
+                     const char *cache_path, int32_t chosen[4]) {
+  if (!c || !steps || n_steps < 1) return TRILENS_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  char key[128];
+  tuning_key(c, key, sizeof(key));
+  int v[4];
+  if (cache_lookup(cache_path, key, v)) {
+    int rc = apply_tuning(c, v[0], v[1], v[2], v[3]);
+    if (rc) return rc;
+    if (chosen)
+      for (int i = 0; i < 4; ++i) chosen[i] = v[i];
+    return TRILENS_OK;
+  }
+  // coordinate descent over the four knobs, each swept with the others
+  // fixed at the best so far; results never depend on them, only time does
+  int best[4] = {c->p.leaf_bucket, c->p.stack_depth, c->p.block_shape, c->budget};
+  static const int cand[4][5] = {{2, 4, 8, 16, 0}, {128, 256, 512, 0, 0}, {2, 4, 8, 0, 0},
+                                 {16, 64, 256, 0, 0}};
+  double best_ms = 1e30;
+  int rc = apply_tuning(c, best[0], best[1], best[2], best[3]);
+  if (rc) return rc;
+  if ((rc = time_steps(c, steps, n_steps, &best_ms))) return rc;  // warm-up
+  if ((rc = time_steps(c, steps, n_steps, &best_ms))) return rc;
+  for (int knob = 0; knob < 4; ++knob) {
+    for (int j = 0; j < 5 && cand[knob][j]; ++j) {
+      int t[4] = {best[0], best[1], best[2], best[3]};
+      t[knob] = cand[knob][j];
+      if (t[knob] == best[knob]) continue;
+      if ((rc = apply_tuning(c, t[0], t[1], t[2], t[3]))) continue;  // shape does not fit
+      double ms = 0;
+      if ((rc = time_steps(c, steps, n_steps, &ms))) return rc;
+      if (ms < best_ms) {
+        best_ms = ms;
+        for (int i = 0; i < 4; ++i) best[i] = t[i];
+      }
+    }
+  }
+  if ((rc = apply_tuning(c, best[0], best[1], best[2], best[3]))) return rc;
+  cache_store(cache_path, key, best, best_ms);
+  if (chosen)
+    for (int i = 0; i < 4; ++i) chosen[i] = best[i];
+  return TRILENS_OK;
 }
 
 int trilens_step_stats_get(trilens_ctx *c, trilens_step_stats *out) {
