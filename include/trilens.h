@@ -204,6 +204,30 @@ int trilens_get_tuning(trilens_ctx *c, int32_t out[4]);
 int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
                      const char *cache_path, int32_t chosen[4]);
 
+/* ---- surrogate network ------------------------------------------------------
+ * The learned part of the statistical regime (the paper's ST regime estimates
+ * collision rates of whole clouds, Sec. 2.2; here a network estimates the
+ * pair yield of whole node pairs): 24 -> 128 -> 128 -> 128 -> 2 with exact
+ * GELU, BF16 weights and activations, FP32 accumulation on the tensor cores.
+ * Parameters are a flat FP32 device vector of TRILENS_MLP_PARAMS floats:
+ * W1 (128x24), b1 (128), W2 (128x128), b2, W3 (128x128), b3, W4 (2x128), b4 (2),
+ * each W row-major [out][in], layer z = W h + b.  norm (device, 48 floats) holds
+ * the feature mean[24] and 1/std[24] applied to the raw features first.
+ * Output per row: (mu, s), a Gaussian over y = log1p(pair yield) with log
+ * variance s; loss 0.5 (s + (y - mu)^2 e^-s), s clamped to +-12. */
+#define TRILENS_MLP_PARAMS 36482
+
+/* out (device, m x 2 FP32) = network(x) for x (device, m x 24 FP32 raw
+ * features).  Synchronises the stream.  TIMEOUT if a tensor-core wait ran out. */
+int trilens_mlp_forward(const float *params, const float *norm, const float *x, int64_t m,
+                        float *out, trilens_stream_t stream);
+
+/* grad (device, TRILENS_MLP_PARAMS FP32) = gradient of the MEAN loss over the
+ * m rows of (x, y) (y: device, m FP32 targets); loss (device, 1 FP32) = the
+ * SUM of the per-row losses.  Synchronises the stream. */
+int trilens_mlp_grad(const float *params, const float *norm, const float *x, const float *y,
+                     int64_t m, float *grad, float *loss, trilens_stream_t stream);
+
 /* Largest hit list trilens_yield_reduce_noalloc accepts (2^28 pairs). */
 #define TRILENS_NOALLOC_MAX_HITS (1ll << 28)
 

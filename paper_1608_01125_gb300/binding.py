@@ -123,6 +123,10 @@ def lib() -> ctypes.CDLL:
         L.trilens_autotune.argtypes = [vp, ctypes.POINTER(i64), i32, ctypes.c_char_p,
                                        ctypes.POINTER(i32)]
         L.trilens_autotune.restype = ctypes.c_int
+        L.trilens_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.trilens_mlp_forward.restype = ctypes.c_int
+        L.trilens_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+        L.trilens_mlp_grad.restype = ctypes.c_int
         L.trilens_yield_reduce_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.trilens_yield_reduce_noalloc.restype = ctypes.c_int
         _lib = L
@@ -367,3 +371,47 @@ class Batch(Collider):
         _check(lib().trilens_batch_run(self.ctx, int(first_step), int(steps),
                                        ctypes.c_void_p(self.yields.data_ptr())), self.ctx)
         return self.yields.cpu().numpy().copy()
+
+
+MLP_PARAMS = 36482
+MLP_ORDER = (("W1", (128, 24)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+             ("W3", (128, 128)), ("b3", (128,)), ("W4", (2, 128)), ("b4", (2,)))
+
+
+def mlp_flatten(p: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).reshape(-1) for k, _ in MLP_ORDER])
+
+
+def mlp_unflatten(v) -> dict:
+    v = np.asarray(v)
+    out, off = {}, 0
+    for k, shp in MLP_ORDER:
+        n = int(np.prod(shp))
+        out[k] = v[off:off + n].reshape(shp)
+        off += n
+    return out
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_forward(params, norm, x, stream=None):
+    """Network outputs (m, 2) for device FP32 tensors params, norm (48), x (m, 24)."""
+    torch = _torch()
+    out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().trilens_mlp_forward(_ptr(params), _ptr(norm), _ptr(x), x.shape[0], _ptr(out),
+                                     ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def mlp_grad(params, norm, x, y, stream=None):
+    """(gradient of the mean loss, summed loss) for device FP32 tensors."""
+    torch = _torch()
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().trilens_mlp_grad(_ptr(params), _ptr(norm), _ptr(x), _ptr(y), x.shape[0], _ptr(g),
+                                  _ptr(loss), ctypes.c_void_p(st.cuda_stream)))
+    return g, loss

@@ -1,0 +1,64 @@
+"""The tensor-core surrogate network against the FP64 CPU reference
+(oracle/mlp.py): forward outputs, the loss and every parameter gradient,
+within BF16 tolerances."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_1608_01125_gb300 import binding
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(m, seed):
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    rng = np.random.default_rng(seed)
+    p = mlp.init_params(seed)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.standard_normal(p[k].shape) * 0.1
+    x = rng.standard_normal((m, 24))
+    y = rng.standard_normal(m) * 1.5 + 0.5
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    norm = np.concatenate([np.zeros(24), np.ones(24)])
+    return p, x, y, dev(binding.mlp_flatten(p)), dev(norm), dev(x), dev(y)
+
+
+@pytest.mark.parametrize("m", [1, 127, 128, 1000, 70001])
+def test_forward_matches_fp64_reference(m):
+    p, x, y, P, N, X, Y = _setup(m, 3)
+    out = binding.mlp_forward(P, N, X).cpu().numpy()
+    ref, _ = mlp.forward(p, x)
+    # BF16 operands (8 significant bits) through 4 layers
+    err = np.abs(out - ref)
+    scale = np.abs(ref).mean() + 1e-3
+    assert err.max() <= 0.08 * scale + 0.05 * np.abs(ref).max(), (err.max(), scale)
+    assert np.median(err) <= 0.02 * scale
+
+
+def test_normalisation_is_applied():
+    import torch
+    p, x, y, P, N, X, Y = _setup(500, 4)
+    mean = np.linspace(-1, 1, 24)
+    inv = np.linspace(0.5, 2, 24)
+    raw = x / inv + mean
+    N2 = torch.from_numpy(np.concatenate([mean, inv]).astype(np.float32)).cuda()
+    a = binding.mlp_forward(P, N2, torch.from_numpy(raw.astype(np.float32)).cuda()).cpu().numpy()
+    b = binding.mlp_forward(P, N, X).cpu().numpy()
+    assert np.allclose(a, b, atol=0.05 * np.abs(b).max())
+
+
+def test_gradients_match_fp64_reference():
+    m = 4096
+    p, x, y, P, N, X, Y = _setup(m, 5)
+    g, loss = binding.mlp_grad(P, N, X, Y)
+    L, gref = mlp.loss_and_grads(p, x, y)
+    assert abs(float(loss.item()) / m - L) <= 0.03 * abs(L) + 1e-3
+    gv = binding.mlp_unflatten(g.cpu().numpy().astype(np.float64))
+    for k, _ in binding.MLP_ORDER:
+        a, r = gv[k].reshape(-1), gref[k].reshape(-1)
+        rel = np.linalg.norm(a - r) / (np.linalg.norm(r) + 1e-12)
+        cos = float(a @ r) / (np.linalg.norm(a) * np.linalg.norm(r) + 1e-30)
+        assert rel < 0.08 and cos > 0.995, (k, rel, cos)
