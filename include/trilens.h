@@ -126,7 +126,9 @@ int trilens_step_stats_get(trilens_ctx *c, trilens_step_stats *out);
 
 /* Cumulative yield since creation or the last reset: number of colliding
  * pairs and sum of w_i w_j (host doubles).  mode EXACT returns the exact
- * totals; level_L is ignored for EXACT. */
+ * totals (level_L ignored); mode SURROGATE returns, in *weighted, the sum of
+ * trilens_surrogate_step estimates (level_L must be the model's) and sets
+ * *count to -1 (the network estimates the weighted yield only). */
 int trilens_yield(trilens_ctx *c, int32_t mode, int32_t level_L, double *count,
                   double *weighted);
 
@@ -213,8 +215,9 @@ int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
  * W1 (128x24), b1 (128), W2 (128x128), b2, W3 (128x128), b3, W4 (2x128), b4 (2),
  * each W row-major [out][in], layer z = W h + b.  norm (device, 48 floats) holds
  * the feature mean[24] and 1/std[24] applied to the raw features first.
- * Output per row: (mu, s), a Gaussian over y = log1p(pair yield) with log
- * variance s; loss 0.5 (s + (y - mu)^2 e^-s), s clamped to +-12. */
+ * Output per row: (mu, s), a Gaussian over the target y (for the surrogate,
+ * the residual of log1p(pair yield) over log1p of the ST-form estimate) with
+ * log variance s; loss 0.5 (s + (y - mu)^2 e^-s), s clamped to +-12. */
 #define TRILENS_MLP_PARAMS 36482
 
 /* out (device, m x 2 FP32) = network(x) for x (device, m x 24 FP32 raw
@@ -227,6 +230,74 @@ int trilens_mlp_forward(const float *params, const float *norm, const float *x, 
  * SUM of the per-row losses.  Synchronises the stream. */
 int trilens_mlp_grad(const float *params, const float *norm, const float *x, const float *y,
                      int64_t m, float *grad, float *loss, trilens_stream_t stream);
+
+/* ---- learned statistical regime ----------------------------------------------
+ * The dual traversal stops at hierarchy level L: the first node on every path
+ * whose Morton prefix is at least L bits long (or a leaf bucket), so every
+ * photon lies in exactly one level-L node of its beam.  Overlapping level-L
+ * node pairs get 24 features -- centre offset (3), half-extents of both boxes
+ * (6), log counts (2), log weight sums (2), mean and std of ln E (4), mean
+ * directions (6), 1 - dA.dB of the means (1) -- from FP64 prefix sums of the
+ * weights and their energy and direction moments over the Morton-ordered
+ * photons.  Training labels are the exact yields of the pairs (an exact
+ * traversal seeded with the pairs; every hit is attributed to the pair that
+ * holds its two photons).  Next to the features the kernels compute an
+ * estimate of the paper's ST form (rate ~ n_I n_II sigma: weight sums times
+ * sigma(s) at the mean energies and directions times the boxes' overlap over
+ * their volumes, scaled by a constant fitted on the training pairs).  The
+ * network learns the residual of log1p(yield) over log1p(ST estimate); a
+ * pair's yield is exp(mu + log1p(ST) + var/2) - 1 (the mean of the
+ * predicted log-normal, var = e^s capped at 2), times a calibration scale
+ * fitted on the training pairs; pairs whose predicted standard deviation of y
+ * exceeds tau are evaluated exactly instead (the fallback). */
+
+/* Build each listed step, collect its level-L pairs with features and exact
+ * labels into the context's training set (steps are not added to the
+ * yield).  INVALID for level_L outside [1, 63], n < 1, a batch context, or a
+ * level different from samples already collected. */
+int trilens_surrogate_collect(trilens_ctx *c, const int64_t *steps, int32_t n, int32_t level_L);
+
+/* Train the network on the collected samples (feature normalisation from
+ * the samples, He-initialised weights from `seed`, AdamW with cosine decay,
+ * minibatches of 8192, `epochs` passes), then fit the calibration scales of
+ * the network's and of the ST-form estimates on the samples. */
+int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed);
+
+/* collect + fit. */
+int trilens_surrogate_train(trilens_ctx *c, const int64_t *train_steps, int32_t n, int32_t level_L,
+                            int32_t epochs, uint64_t seed);
+
+/* Surrogate yield of the built step (trilens_build(step) first) with a model
+ * trained or loaded for the same level_L.  out (host, 8 doubles): [0] the
+ * estimated weighted yield (network part plus exact fallback), [1] the
+ * ST-form estimate of the same pairs (no network, calibrated), [2] level-L
+ * pairs, [3] pairs sent to the fallback, [4] their exact yield, [5] device
+ * milliseconds of the whole surrogate path, [6] of network + estimate, [7]
+ * of the cut traversal + features.  Adds [0] to the cumulative surrogate
+ * yield (trilens_yield with TRILENS_YIELD_SURROGATE). */
+int trilens_surrogate_step(trilens_ctx *c, int64_t step, int32_t level_L, float tau,
+                           double out[8]);
+
+/* [0] samples collected, [1] last training loss, [2] network calibration,
+ * [3] ST-form calibration, [4] level L, [5] cumulative surrogate yield. */
+int trilens_surrogate_info(trilens_ctx *c, double out[6]);
+
+/* Copy the training set to host arrays of capacity cap: x (cap x 24 FP32
+ * features), label (cap FP64 exact pair yields), st (cap FP32 uncalibrated
+ * ST-form estimates); any may be NULL.  *n receives the number of samples. */
+int trilens_surrogate_dataset(trilens_ctx *c, float *x, double *label, float *st, int64_t cap,
+                              int64_t *n);
+
+/* Append samples (host arrays as trilens_surrogate_dataset returns them)
+ * to the context's training set, e.g. pairs collected in other contexts
+ * (other seeds).  INVALID on a level mismatch. */
+int trilens_surrogate_add_samples(trilens_ctx *c, const float *x, const double *label,
+                                  const float *st, int64_t n, int32_t level_L);
+
+/* Save / load the model (level, calibrations, feature normalisation and
+ * parameters) as a little-endian binary file. */
+int trilens_surrogate_save(trilens_ctx *c, const char *path);
+int trilens_surrogate_load(trilens_ctx *c, const char *path);
 
 /* Largest hit list trilens_yield_reduce_noalloc accepts (2^28 pairs). */
 #define TRILENS_NOALLOC_MAX_HITS (1ll << 28)

@@ -127,6 +127,18 @@ def lib() -> ctypes.CDLL:
         L.trilens_mlp_forward.restype = ctypes.c_int
         L.trilens_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
         L.trilens_mlp_grad.restype = ctypes.c_int
+        L.trilens_surrogate_collect.argtypes = [vp, ctypes.POINTER(i64), i32, i32]
+        L.trilens_surrogate_fit.argtypes = [vp, i32, ctypes.c_uint64]
+        L.trilens_surrogate_train.argtypes = [vp, ctypes.POINTER(i64), i32, i32, i32, ctypes.c_uint64]
+        L.trilens_surrogate_step.argtypes = [vp, i64, i32, ctypes.c_float, ctypes.POINTER(dbl)]
+        L.trilens_surrogate_info.argtypes = [vp, ctypes.POINTER(dbl)]
+        L.trilens_surrogate_dataset.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(i64)]
+        L.trilens_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+        L.trilens_surrogate_load.argtypes = [vp, ctypes.c_char_p]
+        L.trilens_surrogate_add_samples.argtypes = [vp, vp, vp, vp, i64, i32]
+        for f in ("collect", "fit", "train", "step", "info", "dataset", "save", "load",
+                  "add_samples"):
+            getattr(L, "trilens_surrogate_" + f).restype = ctypes.c_int
         L.trilens_yield_reduce_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.trilens_yield_reduce_noalloc.restype = ctypes.c_int
         _lib = L
@@ -274,6 +286,58 @@ class Collider:
         _check(lib().trilens_autotune(self.ctx, st, len(steps),
                                       cache_path.encode() if cache_path else None, v), self.ctx)
         return dict(zip(("leaf_bucket", "stack_depth", "block_shape", "budget"), list(v)))
+
+    # ---- learned statistical regime
+    def surrogate_collect(self, steps, level_L: int):
+        st = (ctypes.c_int64 * len(steps))(*[int(x) for x in steps])
+        _check(lib().trilens_surrogate_collect(self.ctx, st, len(steps), int(level_L)), self.ctx)
+
+    def surrogate_fit(self, epochs: int, seed: int = 0):
+        _check(lib().trilens_surrogate_fit(self.ctx, int(epochs), int(seed)), self.ctx)
+
+    def surrogate_train(self, steps, level_L: int, epochs: int, seed: int = 0):
+        self.surrogate_collect(steps, level_L)
+        self.surrogate_fit(epochs, seed)
+
+    def surrogate_step(self, step: int, level_L: int, tau: float = 1e30) -> dict:
+        """Build `step` and return the surrogate estimate and its timings."""
+        self.build(step)
+        v = (ctypes.c_double * 8)()
+        _check(lib().trilens_surrogate_step(self.ctx, int(step), int(level_L), float(tau), v),
+               self.ctx)
+        return dict(zip(("yield", "st_yield", "pairs", "fallback_pairs", "fallback_yield",
+                         "ms", "ms_network", "ms_cut"), list(v)))
+
+    def surrogate_info(self) -> dict:
+        v = (ctypes.c_double * 6)()
+        _check(lib().trilens_surrogate_info(self.ctx, v), self.ctx)
+        return dict(zip(("samples", "loss", "calib", "st_calib", "level", "total"), list(v)))
+
+    def surrogate_dataset(self):
+        n = ctypes.c_int64(0)
+        _check(lib().trilens_surrogate_dataset(self.ctx, None, None, None, 0, ctypes.byref(n)),
+               self.ctx)
+        x = np.zeros((n.value, 24), np.float32)
+        lab = np.zeros(n.value, np.float64)
+        st = np.zeros(n.value, np.float32)
+        _check(lib().trilens_surrogate_dataset(
+            self.ctx, x.ctypes.data_as(ctypes.c_void_p), lab.ctypes.data_as(ctypes.c_void_p),
+            st.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)), self.ctx)
+        return x, lab, st
+
+    def surrogate_add_samples(self, x, label, st, level_L: int):
+        x = np.ascontiguousarray(x, np.float32)
+        label = np.ascontiguousarray(label, np.float64)
+        st = np.ascontiguousarray(st, np.float32)
+        _check(lib().trilens_surrogate_add_samples(
+            self.ctx, x.ctypes.data_as(ctypes.c_void_p), label.ctypes.data_as(ctypes.c_void_p),
+            st.ctypes.data_as(ctypes.c_void_p), len(label), int(level_L)), self.ctx)
+
+    def surrogate_save(self, path: str):
+        _check(lib().trilens_surrogate_save(self.ctx, path.encode()), self.ctx)
+
+    def surrogate_load(self, path: str):
+        _check(lib().trilens_surrogate_load(self.ctx, path.encode()), self.ctx)
 
     def debug_set_spin_limit(self, limit: int):
         _check(lib().trilens_debug_set_spin_limit(self.ctx, int(limit)), self.ctx)

@@ -11,8 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "tl_common.cuh"
-#include "trilens.h"
+#include "tl_ctx.h"
 #include "trilens_debug.h"
 
 namespace tl {
@@ -35,71 +34,6 @@ cudaError_t launch_step_finish(const TLCounters *ctr, const unsigned long long *
                                unsigned *run_status, cudaStream_t s);
 }  // namespace tl
 
-static const int kMaxLevels = 24;
-
-struct trilens_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  trilens_params p{};
-  TLBeam beam[2]{};
-  // derived constants
-  double L64 = 0, rmax = 0, sigma_max = 0;
-  float L_lo = 0, L_hi = 0, half = 0;
-  TLNarrowConst nk{};
-  int bits[2]{}, key_bits[2]{};
-  double bounds[2][12]{};
-  // build workspace
-  tl::BuildBufs w[2]{};
-  int sel[2]{};
-  int64_t built_step = -1;
-  // traversal workspace
-  int n_sm = 0, trav_warps = 4, trav_blocks = 0, expand_blocks = 0;
-  int budget = 64;  // traversal iterations per work item before it is split
-  unsigned front_target = 0, front_cap = 0;
-  uint2 *front[2]{};
-  uint2 *spill[2]{};
-  unsigned long long spill_cap = 0;
-  uint2 *hits = nullptr;
-  unsigned long long hit_cap = 0;
-  uint2 *band = nullptr;
-  unsigned long long band_cap = 0;
-  TLCounters *ctr = nullptr;
-  TLCounters *ctr_host = nullptr;  // pinned
-  void *partials = nullptr;
-  int yield_blocks = 0;
-  unsigned *build_status = nullptr;  // device status of the builds (sort waits)
-  unsigned *build_status_host = nullptr;
-  double *bounds_dev = nullptr;
-  // results
-  trilens_step_stats last{};
-  double tot_count = 0, tot_weighted = 0;
-  int debug_stall_sort = 0;
-  // several independent instances (batch contexts)
-  int n_inst = 1;
-  uint32_t *inst_of[2]{};     // device, instance of every photon
-  uint32_t *inst_root[2]{};   // device, subtree root (stack reference) per instance
-  double *inst_bounds[2]{};   // device, 12 doubles per instance
-  float4 *inst_box[2]{};      // device, Morton box of every instance for the current build
-  long long *inst_tmp = nullptr;
-  double *owned[2][8]{};      // concatenated inputs owned by a batch context
-  // graph-captured multi-step runs (batch contexts)
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  int64_t g_first = -1, g_steps = 0;
-  double *g_yields = nullptr;
-  unsigned long long *spill_n = nullptr;  // device, counts of the two spill lists
-  unsigned *run_status = nullptr;
-  unsigned *run_status_host = nullptr;
-  int graph_passes = 12;
-  // per-phase timing (events on the context's stream) and launch counts
-  int timing = 0;
-  cudaEvent_t ev[9][2][2]{};   // [phase][beam or 0][start, end]
-  bool ev_pending[9][2]{};
-  double phase_ms[9]{};
-  int64_t phase_launches[9]{};
-  char msg[512] = {0};
-};
-
 enum { PH_PROP = 0, PH_SORT, PH_GATHER, PH_EMIT, PH_REFIT, PH_EXPAND, PH_TRAV, PH_BAND, PH_YIELD };
 
 static void tmark(trilens_ctx *c, int ph, int k, int end) {
@@ -119,24 +53,6 @@ static void tcollect(trilens_ctx *c) {
         c->ev_pending[ph][k] = false;
       }
 }
-
-static int fail(trilens_ctx *c, int code, const char *fmt, ...) {
-  if (c) {
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
-    va_end(ap);
-  }
-  return code;
-}
-
-#define CK(call)                                                                          \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      return fail(c, e_ == cudaErrorMemoryAllocation ? TRILENS_ERR_NOMEM : TRILENS_ERR_CUDA, \
-                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
-  } while (0)
 
 // ---- host-side constants (plain double; used only for conservative bounds)
 
@@ -168,15 +84,6 @@ static float round_down(double x) {
   return f;
 }
 
-// ---- allocation helpers
-
-template <class T>
-static cudaError_t dalloc(T **p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  return cudaMalloc((void **)p, sizeof(T) * count);
-}
-
 static void free_beam(tl::BuildBufs &w) {
   cudaFree(w.pos_u);
   cudaFree(w.dir_u);
@@ -190,6 +97,8 @@ static void free_beam(tl::BuildBufs &w) {
   cudaFree(w.parent_leaf);
   cudaFree(w.parent_node);
   cudaFree(w.visit);
+  cudaFree(w.nfirst);
+  cudaFree(w.nlev);
   cudaFree(w.sort_status);
   cudaFree(w.sort_hist);
   cudaFree(w.sort_tile);
@@ -210,20 +119,12 @@ static int alloc_beam(trilens_ctx *c, tl::BuildBufs &w, int64_t n) {
   CK(dalloc(&w.parent_leaf, m));
   CK(dalloc(&w.parent_node, m));
   CK(dalloc(&w.visit, m));
+  CK(dalloc(&w.nfirst, m));
+  CK(dalloc(&w.nlev, m));
   w.sort_tiles = (int64_t)((m + TL_SORT_TILE - 1) / TL_SORT_TILE);
   CK(dalloc(&w.sort_status, (size_t)w.sort_tiles * 256));
   CK(dalloc(&w.sort_hist, 8 * 256));
   CK(dalloc(&w.sort_tile, 8));
-  return TRILENS_OK;
-}
-
-static int grow(trilens_ctx *c, uint2 **buf, unsigned long long *cap, unsigned long long need) {
-  unsigned long long nc = std::max<unsigned long long>(need + need / 4 + 1024, *cap * 2);
-  cudaFree(*buf);
-  *buf = nullptr;
-  *cap = 0;
-  CK(dalloc(buf, (size_t)nc));
-  *cap = nc;
   return TRILENS_OK;
 }
 
@@ -271,6 +172,7 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFree(c->partials);
   cudaFree(c->build_status);
   cudaFree(c->bounds_dev);
+  surrogate_free(c);
   cudaFreeHost(c->ctr_host);
   cudaFreeHost(c->build_status_host);
   for (int k = 0; k < 2; ++k) {
@@ -359,6 +261,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
     // Morton resolution: a few bits per axis beyond one cell per photon
     c->bits[k] = std::min(21, std::max(4, (lg + 2) / 3 + 3));
     c->key_bits[k] = 3 * c->bits[k];
+    c->w[k].key_bits = c->key_bits[k];
     // one-time bounds of p0 and d for the Morton box
     CK(tl::launch_beam_bounds(c->beam[k], c->bounds_dev, c->stream));
     CK(cudaMemcpyAsync(c->bounds[k], c->bounds_dev, sizeof(double) * 12, cudaMemcpyDeviceToHost,
@@ -451,7 +354,9 @@ int trilens_build(trilens_ctx *c, int64_t step) {
   return TRILENS_OK;
 }
 
-static tl::TravArgs trav_args(trilens_ctx *c, double ct) {
+}  // extern "C"
+
+tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   tl::TravArgs a;
   memset(&a, 0, sizeof(a));
   for (int k = 0; k < 2; ++k) {
@@ -483,13 +388,7 @@ static tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   return a;
 }
 
-int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t cap,
-                         int64_t *n_hits) {
-  if (!c) return TRILENS_ERR_INVALID;
-  if (step != c->built_step) return fail(c, TRILENS_ERR_INVALID, "step %lld not built", (long long)step);
-  if (cap < 0 || (hits == nullptr && cap > 0)) return fail(c, TRILENS_ERR_INVALID, "bad hit buffer");
-  CK(cudaSetDevice(c->device));
-  const double ct = TL_C * ((double)step * c->p.dt_fs);
+int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, int *retries_out) {
   const int nonempty = c->beam[0].n > 0 && c->beam[1].n > 0;
   int retries = 0;
   TLCounters &h = *c->ctr_host;
@@ -497,17 +396,23 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
     tl::TravArgs a = trav_args(c, ct);
     tmark(c, PH_EXPAND, 0, 0);
     CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super,
-                            c->n_inst > 1 ? 0 : nonempty, c->build_status, c->stream));
-    if (c->n_inst > 1)
-      CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
-                                   c->n_inst, c->stream));
-    CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
-                         c->stream));
+                            (c->n_inst > 1 || seeds) ? 0 : nonempty, c->build_status, c->stream));
+    if (!seeds) {
+      if (c->n_inst > 1)
+        CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
+                                     c->n_inst, c->stream));
+      CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
+                           c->stream));
+    }
     tmark(c, PH_EXPAND, 0, 1);
-    c->phase_launches[PH_EXPAND] += 2;
+    c->phase_launches[PH_EXPAND] += seeds ? 1 : 2;
     tmark(c, PH_TRAV, 0, 0);
-    CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->budget, c->trav_blocks,
-                           c->trav_warps, c->stream));
+    if (seeds)
+      CK(tl::launch_traverse(a, c->front[0], c->front[1], seeds, n_seeds, 0, c->budget,
+                             c->trav_blocks, c->trav_warps, c->stream));
+    else
+      CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->budget, c->trav_blocks,
+                             c->trav_warps, c->stream));
     tmark(c, PH_TRAV, 0, 1);
     c->phase_launches[PH_TRAV] += 1;
     CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));
@@ -579,6 +484,23 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
     if (!again) break;
     if (++retries > 8) return fail(c, TRILENS_ERR_STACK, "buffers kept overflowing");
   }
+  if (retries_out) *retries_out = retries;
+  return TRILENS_OK;
+}
+
+extern "C" {
+
+int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t cap,
+                         int64_t *n_hits) {
+  if (!c) return TRILENS_ERR_INVALID;
+  if (step != c->built_step) return fail(c, TRILENS_ERR_INVALID, "step %lld not built", (long long)step);
+  if (cap < 0 || (hits == nullptr && cap > 0)) return fail(c, TRILENS_ERR_INVALID, "bad hit buffer");
+  CK(cudaSetDevice(c->device));
+  const double ct = TL_C * ((double)step * c->p.dt_fs);
+  int retries = 0;
+  const int rc = run_exact(c, ct, nullptr, 0, &retries);
+  if (rc) return rc;
+  TLCounters &h = *c->ctr_host;
   if (hits && (int64_t)h.count > cap) {
     // the step is not added to the cumulative yield: the caller repeats it
     // with a larger buffer (the hierarchies stay built)
@@ -698,6 +620,7 @@ int trilens_batch_create(trilens_ctx **out, const trilens_beam *a, const trilens
   for (int k = 0; k < 2; ++k) {
     c->bits[k] = bits;
     c->key_bits[k] = 3 * bits + ib;
+    c->w[k].key_bits = c->key_bits[k];
     c->w[k].inst_shift = 3 * bits;
     CK(dalloc(&c->inst_root[k], (size_t)n_inst));
     c->w[k].inst_root = c->inst_root[k];
@@ -1052,8 +975,11 @@ int trilens_step_stats_get(trilens_ctx *c, trilens_step_stats *out) {
 
 int trilens_yield(trilens_ctx *c, int32_t mode, int32_t level_L, double *count,
                   double *weighted) {
-  (void)level_L;
   if (!c || !count || !weighted) return TRILENS_ERR_INVALID;
+  if (mode == TRILENS_YIELD_SURROGATE) {
+    *count = -1.0;
+    return surrogate_total(c, level_L, weighted);
+  }
   if (mode != TRILENS_YIELD_EXACT) return fail(c, TRILENS_ERR_INVALID, "yield mode %d", mode);
   *count = c->tot_count;
   *weighted = c->tot_weighted;

@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__rest
                                                 int64_t n, int bucket, TLNode *nodes,
                                                 uint32_t *parent_leaf, uint32_t *parent_node,
                                                 const unsigned *build_status, uint32_t *inst_root,
-                                                int inst_shift) {
+                                                int inst_shift, uint32_t *nfirst, uint8_t *nlev,
+                                                int key_bits) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (*build_status & TL_ST_TIMEOUT) return;  // keys unsorted: the build is abandoned
   const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
@@ -339,6 +340,8 @@ __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__rest
     else parent_leaf[0] = (super << 1) | 0u;
     if (multi && one_inst)
       inst_root[key[0] >> inst_shift] = root_bucket ? (TL_FLAG | (super << 1)) : 0u;
+    nfirst[super] = 0u;
+    nlev[super] = 0;
   }
   if (i >= n - 1) return;
   int dl = kdelta(key, n, i, i - 1), dr = kdelta(key, n, i, i + 1);
@@ -371,6 +374,11 @@ __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__rest
         inst_root[kl] = cr <= bucket ? (TL_FLAG | ((uint32_t)i << 1) | 1u) : (uint32_t)(gamma + 1);
     }
   }
+  nfirst[i] = (uint32_t)first;
+  {
+    const int lev = dnode - (64 - key_bits);  // equal keys: beyond key_bits
+    nlev[i] = (uint8_t)(lev < 0 ? 0 : (lev > 255 ? 255 : lev));
+  }
   int refl = (cl <= bucket && lone) ? (int)(TL_FLAG | (uint32_t)first) : (int)gamma;
   int refr = (cr <= bucket && rone) ? (int)(TL_FLAG | (uint32_t)(gamma + 1)) : (int)(gamma + 1);
   nodes[i].c = make_int4(refl, refr, (int)cl, (int)cr);
@@ -386,7 +394,8 @@ cudaError_t launch_karras(BuildBufs &w, int64_t n, int sel, int bucket, cudaStre
   k_karras<<<(int)((threads + 255) / 256), 256, 0, s>>>(w.key[sel], n, bucket, w.nodes,
                                                         w.parent_leaf, w.parent_node,
                                                         w.build_status, w.inst_root,
-                                                        w.inst_shift);
+                                                        w.inst_shift, w.nfirst, w.nlev,
+                                                        w.key_bits);
   return cudaGetLastError();
 }
 

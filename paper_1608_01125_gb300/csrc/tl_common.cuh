@@ -146,6 +146,11 @@ struct BuildBufs {
   const uint32_t *inst_of;  // instance of each input photon
   uint32_t *inst_root;      // per instance: stack reference of its subtree root
   int inst_shift;           // bit position of the instance number in the key
+  // per inner node: first photon of its range and its level (Morton prefix
+  // length in bits below the key's top bit), for the level-L cut
+  uint32_t *nfirst;
+  uint8_t *nlev;
+  int key_bits;
 };
 
 // Arguments of the traversal kernels (tl_traverse.cu).

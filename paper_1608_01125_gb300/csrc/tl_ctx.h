@@ -1,0 +1,126 @@
+// tl_ctx.h -- the library context shared by the host translation units
+// (private; the public interface is include/trilens.h).
+#pragma once
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "tl_common.cuh"
+#include "trilens.h"
+
+struct SurrogateState;
+
+constexpr int kMaxLevels = 24;
+
+struct trilens_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  trilens_params p{};
+  TLBeam beam[2]{};
+  // derived constants
+  double L64 = 0, rmax = 0, sigma_max = 0;
+  float L_lo = 0, L_hi = 0, half = 0;
+  TLNarrowConst nk{};
+  int bits[2]{}, key_bits[2]{};
+  double bounds[2][12]{};
+  // build workspace
+  tl::BuildBufs w[2]{};
+  int sel[2]{};
+  int64_t built_step = -1;
+  // traversal workspace
+  int n_sm = 0, trav_warps = 4, trav_blocks = 0, expand_blocks = 0;
+  int budget = 64;  // traversal iterations per work item before it is split
+  unsigned front_target = 0, front_cap = 0;
+  uint2 *front[2]{};
+  uint2 *spill[2]{};
+  unsigned long long spill_cap = 0;
+  uint2 *hits = nullptr;
+  unsigned long long hit_cap = 0;
+  uint2 *band = nullptr;
+  unsigned long long band_cap = 0;
+  TLCounters *ctr = nullptr;
+  TLCounters *ctr_host = nullptr;  // pinned
+  void *partials = nullptr;
+  int yield_blocks = 0;
+  unsigned *build_status = nullptr;  // device status of the builds (sort waits)
+  unsigned *build_status_host = nullptr;
+  double *bounds_dev = nullptr;
+  // results
+  trilens_step_stats last{};
+  double tot_count = 0, tot_weighted = 0;
+  int debug_stall_sort = 0;
+  // several independent instances (batch contexts)
+  int n_inst = 1;
+  uint32_t *inst_of[2]{};     // device, instance of every photon
+  uint32_t *inst_root[2]{};   // device, subtree root (stack reference) per instance
+  double *inst_bounds[2]{};   // device, 12 doubles per instance
+  float4 *inst_box[2]{};      // device, Morton box of every instance for the current build
+  long long *inst_tmp = nullptr;
+  double *owned[2][8]{};      // concatenated inputs owned by a batch context
+  // graph-captured multi-step runs (batch contexts)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t g_first = -1, g_steps = 0;
+  double *g_yields = nullptr;
+  unsigned long long *spill_n = nullptr;  // device, counts of the two spill lists
+  unsigned *run_status = nullptr;
+  unsigned *run_status_host = nullptr;
+  int graph_passes = 12;
+  // per-phase timing (events on the context's stream) and launch counts
+  int timing = 0;
+  cudaEvent_t ev[9][2][2]{};   // [phase][beam or 0][start, end]
+  bool ev_pending[9][2]{};
+  double phase_ms[9]{};
+  int64_t phase_launches[9]{};
+  SurrogateState *sur = nullptr;  // learned statistical regime (tl_surrogate_host.cu)
+  char msg[512] = {0};
+};
+
+
+static inline int fail(trilens_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? TRILENS_ERR_NOMEM : TRILENS_ERR_CUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+  } while (0)
+
+// ---- allocation helpers
+
+template <class T>
+static inline cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+static inline int grow(trilens_ctx *c, uint2 **buf, unsigned long long *cap, unsigned long long need) {
+  unsigned long long nc = std::max<unsigned long long>(need + need / 4 + 1024, *cap * 2);
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  CK(dalloc(buf, (size_t)nc));
+  *cap = nc;
+  return TRILENS_OK;
+}
+
+
+// traversal arguments for the current build at time c t_k = ct
+tl::TravArgs trav_args(trilens_ctx *c, double ct);
+// exact collision of seed pairs (or, with seeds == NULL, of the whole
+// hierarchies from the roots) for the built step; fills c->ctr_host
+int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, int *retries);
+void surrogate_free(trilens_ctx *c);
+extern "C" int surrogate_total(trilens_ctx *c, int level, double *out);

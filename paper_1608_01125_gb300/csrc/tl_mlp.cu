@@ -13,7 +13,7 @@
 // s clamped to +-12, mean over the batch.
 #include <cuda_bf16.h>
 
-#include "tl_common.cuh"
+#include "tl_sur.h"
 #include "tl_tc.cuh"
 #include "trilens.h"
 
@@ -439,17 +439,6 @@ cudaError_t mlp_prepare() {
   return cudaFuncSetAttribute(k_mlp_dgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)mlp_bwd_smem());
 }
-
-// device workspace of the network (weights in BF16, training buffers)
-struct MLPWork {
-  __nv_bfloat16 *W1, *W2, *W3, *W4;
-  __nv_bfloat16 *Z[3], *dZ[3];
-  float *dout;
-  float *grad;
-  float *loss;
-  int *err;
-  int64_t cap;  // rows the training buffers hold
-};
 
 cudaError_t mlp_pack(const float *prm, MLPWork &w, cudaStream_t s) {
   k_mlp_pack<<<(kH * kH + 255) / 256, 256, 0, s>>>(prm, w.W1, w.W2, w.W3, w.W4);

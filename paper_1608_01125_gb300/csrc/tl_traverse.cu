@@ -288,10 +288,13 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
     nsrc = ctr->counts[lvl];
   } else {
     src = list;
-    nsrc = a.in_count ? *a.in_count : list_n;
-    // an input list that overflowed holds only spill_cap entries (the
-    // overflow is already flagged by its producer)
-    if (nsrc > a.spill_cap) nsrc = a.spill_cap;
+    nsrc = list_n;
+    if (a.in_count) {
+      // a spill list counted on the device; one that overflowed holds only
+      // spill_cap entries (the overflow is already flagged by its producer)
+      nsrc = *a.in_count;
+      if (nsrc > a.spill_cap) nsrc = a.spill_cap;
+    }
   }
   const unsigned lt = (1u << lane) - 1u;
   int sp = 0, nq = 0, iters = 0;

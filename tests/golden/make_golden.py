@@ -39,5 +39,35 @@ def main():
     print(path)
 
 
+def crossing90(out_path=None):
+    """Stored oracle values of the 90-degree crossing workload (2 x 5e7
+    photons, 256 steps): three steps drawn with PCG64(0) from the window
+    80..176 in which the bunches overlap.  Slow: run by hand
+    (python tests/golden/make_golden.py crossing90)."""
+    import numpy as np
+    wl = synth.crossing90_5e7()
+    a, b = synth.beams(wl)
+    steps = sorted(int(s) for s in np.random.default_rng(0).choice(np.arange(80, 177), 3,
+                                                                    replace=False))
+    out = {"_about": "FP64 oracle (k-d tree) results; written by tests/golden/make_golden.py",
+           "cases": []}
+    for step in steps:
+        _, r = oracle.tree(a, b, step, wl.dt, wl.kappa, nthreads=os.cpu_count() or 1,
+                           cap=1 << 24)
+        out["cases"].append({"workload": wl.name, "n": wl.a.n, "seed": wl.seed, "step": step,
+                             "method": "tree", "count": r["count"], "weighted": r["weighted"],
+                             "hsum": str(r["hsum"]), "hxor": str(r["hxor"])})
+        print(out["cases"][-1], flush=True)
+    path = out_path or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                    "oracle_values_crossing90.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path)
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1 and sys.argv[1] == "crossing90":
+        crossing90()
+    else:
+        main()
+
