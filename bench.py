@@ -387,6 +387,66 @@ def run_batch(args):
     bt.close()
 
 
+def run_statistical(args):
+    """The statistical workload (not the default line): 2 x 1e8 macro-photons,
+    weights U[1,10], Gamma(2, 5 MeV) energies, 32 steps.  A network trained on
+    seed 1 (time steps 8..24, level L) estimates seed 0's yield; the exact GPU
+    traversal of the same steps is the reference for error and time."""
+    import torch
+
+    from paper_1608_01125_gb300 import binding
+    torch.cuda.set_device(0)
+    L = args.level
+    n = args.stat_photons
+    model = os.path.join(tempfile.gettempdir(), f"trilens_surrogate_L{L}.bin")
+    t0 = time.perf_counter()
+    wl1 = synth.statistical_1e8(n=n, seed=1)
+    a1, b1 = synth.beams(wl1)
+    with binding.Collider(a1, b1, wl1.dt, wl1.kappa) as col:
+        col.surrogate_collect(list(range(8, 25)), L)
+        col.surrogate_fit(30, 7)
+        info = col.surrogate_info()
+        col.surrogate_save(model)
+    del a1, b1
+    t_train = time.perf_counter() - t0
+    wl0 = synth.statistical_1e8(n=n, seed=0)
+    a0, b0 = synth.beams(wl0)
+    exact = sur = stv = 0.0
+    ms_exact = ms_sur = ms_build = 0.0
+    pairs = fb = 0
+    with binding.Collider(a0, b0, wl0.dt, wl0.kappa) as col:
+        col.surrogate_load(model)
+        col.timing(True)
+        for k in range(wl0.steps):
+            col.phase_ms(reset=True)
+            col.build(k)
+            col.collide(k)
+            ph, _ = col.phase_ms()
+            ms_exact += ph["expand"] + ph["traverse"] + ph["band"] + ph["yield"]
+            ms_build += sum(ph[p] for p in ("propagate", "sort", "gather", "emit", "refit"))
+            exact += col.stats()["weighted"]
+            r = col.surrogate_step(k, L, args.tau)
+            sur += r["yield"]
+            stv += r["st_yield"]
+            ms_sur += r["ms"]
+            pairs += r["pairs"]
+            fb += r["fallback_pairs"]
+    line = {"metric": "surrogate vs exact GPU traversal speedup at <=1% yield error",
+            "value": ms_exact / ms_sur, "unit": "x", "n_gpus": 1, "steps": wl0.steps,
+            "warmup": 0, "ms_per_step": ms_sur / wl0.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32+f64 exact",
+            "data": "synthetic",
+            "config": {"workload": wl0.name, "photons_per_beam": n, "time_steps": wl0.steps,
+                       "level_L": L, "tau": args.tau, "train": "seed 1, steps 8..24",
+                       "test": "seed 0, all steps"},
+            "yield_error": (sur - exact) / exact, "st_yield_error": (stv - exact) / exact,
+            "exact_weighted_yield": exact, "surrogate_weighted_yield": sur,
+            "exact_traversal_ms": ms_exact, "surrogate_ms": ms_sur, "build_ms": ms_build,
+            "pairs": pairs, "fallback_pairs": fb, "train_samples": info["samples"],
+            "train_s": t_train}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,7 +457,12 @@ def main():
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default knobs)")
     ap.add_argument("--photons", type=int, default=1 << 20)
-    ap.add_argument("--workload", default="headon_2x1M", choices=("headon_2x1M", "batch256"))
+    ap.add_argument("--workload", default="headon_2x1M",
+                    choices=("headon_2x1M", "batch256", "statistical"))
+    ap.add_argument("--level", type=int, default=14, help="statistical workload: cut level L")
+    ap.add_argument("--tau", type=float, default=1e30,
+                    help="statistical workload: fallback threshold on the predicted std")
+    ap.add_argument("--stat-photons", type=int, default=100_000_000)
     ap.add_argument("--first-step", type=int, default=0,
                     help="first time step of each run (profiling a slice of the run)")
     ap.add_argument("--time-steps", type=int, default=0,
@@ -406,6 +471,9 @@ def main():
     wl = synth.headon_1m(n=args.photons)
     if args.workload == "batch256":
         run_batch(args)
+        return
+    if args.workload == "statistical":
+        run_statistical(args)
         return
     if args.impl == "reference":
         run_reference(args, wl)

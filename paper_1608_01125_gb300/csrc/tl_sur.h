@@ -44,8 +44,8 @@ struct MLPWork {
   int64_t cap;  // rows the training buffers hold
 };
 
-cudaError_t launch_prefix_moments(const TLBeam &B, const float4 *dir, int64_t n, double *bsum,
-                                  double *pre, cudaStream_t s);
+cudaError_t launch_prefix_moments(const TLBeam &B, const float4 *pos, const float4 *dir, int64_t n,
+                                  double *bsum, double *pre, cudaStream_t s);
 cudaError_t launch_cut_level(const CutArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_features(const CutTree &A, const CutTree &B, const uint4 *cut,
                             const unsigned *cut_count, unsigned cap, float *feat, float *st,

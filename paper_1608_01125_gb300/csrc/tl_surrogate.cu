@@ -58,29 +58,32 @@ __device__ __forceinline__ void child(const CutTree &T, uint32_t ref, int slot, 
 
 // ------------------------------------------------------------ prefix moments
 
-// per photon (sorted order): w, w lnE, w lnE^2, w dx, w dy, w dz from the FP64 inputs
-__device__ __forceinline__ void moments(const TLBeam &B, const float4 *dir, int64_t p, double m[6]) {
-  const uint32_t i = __float_as_uint(dir[p].w);
-  const double w = B.w ? B.w[i] : 1.0;
-  const double le = log(B.E[i]);
+// per photon (sorted order): w, w lnE, w lnE^2, w dx, w dy, w dz; energy and
+// direction from the Morton-ordered FP32 SoA (coalesced), only the weight
+// gathered from the FP64 input
+__device__ __forceinline__ void moments(const TLBeam &B, const float4 *pos, const float4 *dir,
+                                        int64_t p, double m[6]) {
+  const float4 d = dir[p];
+  const double w = B.w ? B.w[__float_as_uint(d.w)] : 1.0;
+  const double le = (double)logf(pos[p].w);
   m[0] = w;
   m[1] = w * le;
   m[2] = w * le * le;
-  m[3] = w * B.dx[i];
-  m[4] = w * B.dy[i];
-  m[5] = w * B.dz[i];
+  m[3] = w * (double)d.x;
+  m[4] = w * (double)d.y;
+  m[5] = w * (double)d.z;
 }
 
 constexpr int kScanBlock = 1024;
 
-__global__ void __launch_bounds__(256) k_pre_blocks(TLBeam B, const float4 *dir, int64_t n,
-                                                    double *bsum) {
+__global__ void __launch_bounds__(256) k_pre_blocks(TLBeam B, const float4 *pos,
+                                                    const float4 *dir, int64_t n, double *bsum) {
   __shared__ double sh[8][6];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   const int64_t b0 = (int64_t)blockIdx.x * kScanBlock;
   for (int64_t p = b0 + threadIdx.x; p < b0 + kScanBlock && p < n; p += blockDim.x) {
     double m[6];
-    moments(B, dir, p, m);
+    moments(B, pos, dir, p, m);
     for (int c = 0; c < 6; ++c) acc[c] += m[c];
   }
   for (int c = 0; c < 6; ++c)
@@ -124,8 +127,8 @@ __global__ void k_pre_scan(double *bsum, int64_t nb) {
 }
 
 // pre[c][p + 1] = sum over photons 0..p; pre[c][0] = 0
-__global__ void __launch_bounds__(32) k_pre_fill(TLBeam B, const float4 *dir, int64_t n,
-                                                 const double *boff, double *pre) {
+__global__ void __launch_bounds__(32) k_pre_fill(TLBeam B, const float4 *pos, const float4 *dir,
+                                                 int64_t n, const double *boff, double *pre) {
   // one warp per block of kScanBlock photons, sequential in 32-photon chunks
   const int lane = threadIdx.x;
   const int64_t b0 = (int64_t)blockIdx.x * kScanBlock;
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(32) k_pre_fill(TLBeam B, const float4 *dir, in
   for (int64_t base = b0; base < b0 + kScanBlock && base < n; base += 32) {
     const int64_t p = base + lane;
     double m[6] = {0, 0, 0, 0, 0, 0};
-    if (p < n) moments(B, dir, p, m);
+    if (p < n) moments(B, pos, dir, p, m);
     for (int c = 0; c < 6; ++c) {
       double v = m[c];
       for (int off = 1; off < 32; off <<= 1) {
@@ -149,13 +152,13 @@ __global__ void __launch_bounds__(32) k_pre_fill(TLBeam B, const float4 *dir, in
   }
 }
 
-cudaError_t launch_prefix_moments(const TLBeam &B, const float4 *dir, int64_t n, double *bsum,
-                                  double *pre, cudaStream_t s) {
+cudaError_t launch_prefix_moments(const TLBeam &B, const float4 *pos, const float4 *dir, int64_t n,
+                                  double *bsum, double *pre, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-  k_pre_blocks<<<(unsigned)nb, 256, 0, s>>>(B, dir, n, bsum);
+  k_pre_blocks<<<(unsigned)nb, 256, 0, s>>>(B, pos, dir, n, bsum);
   k_pre_scan<<<1, 1024, 0, s>>>(bsum, nb);
-  k_pre_fill<<<(unsigned)nb, 32, 0, s>>>(B, dir, n, bsum, pre);
+  k_pre_fill<<<(unsigned)nb, 32, 0, s>>>(B, pos, dir, n, bsum, pre);
   return cudaGetLastError();
 }
 

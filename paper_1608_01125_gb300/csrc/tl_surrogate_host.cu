@@ -185,8 +185,8 @@ static int sur_cut(trilens_ctx *c, int L, unsigned *ncut) {
   SurrogateState *s = c->sur;
   for (int attempt = 0; attempt < 6; ++attempt) {
     for (int k = 0; k < 2; ++k)
-      CK(tl::launch_prefix_moments(c->beam[k], c->w[k].dir, c->beam[k].n, s->bsum[k], s->pre[k],
-                                   c->stream));
+      CK(tl::launch_prefix_moments(c->beam[k], c->w[k].pos, c->w[k].dir, c->beam[k].n, s->bsum[k],
+                                   s->pre[k], c->stream));
     CK(cudaMemsetAsync(s->lcount, 0, sizeof(unsigned) * 256, c->stream));
     CK(cudaMemsetAsync(s->cut_count, 0, sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(s->status, 0, sizeof(unsigned), c->stream));
@@ -353,13 +353,20 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
   CK(cudaMemcpy(hx.data(), s->tx, sizeof(float) * 24 * N, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(hst.data(), s->tst, sizeof(float) * N, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(hlab.data(), s->tlab, sizeof(double) * N, cudaMemcpyDeviceToHost));
-  // the ST-form estimate's scale, then the network's target: the residual
-  // y = log1p(label) - log1p(scale * st) that it learns on top of it
+  // samples in random order: the first 80% train the network, the last 20%
+  // (held out) fit both calibration scales
+  std::mt19937_64 rng(seed);
+  std::vector<int64_t> perm((size_t)N);
+  for (int64_t i = 0; i < N; ++i) perm[i] = i;
+  std::shuffle(perm.begin(), perm.end(), rng);
+  const int64_t Ntr = N >= 10 ? (N * 4) / 5 : N;
+  // the ST-form estimate's scale (from the training part), then the
+  // network's target: the residual y = log1p(label) - log1p(scale * st)
   {
     double ls = 0, ss = 0;
-    for (int64_t i = 0; i < N; ++i) {
-      ls += hlab[i];
-      ss += hst[i];
+    for (int64_t q = 0; q < Ntr; ++q) {
+      ls += hlab[perm[q]];
+      ss += hst[perm[q]];
     }
     s->st_calib = ss > 0 ? ls / ss : 1.0;
     for (int64_t i = 0; i < N; ++i)
@@ -377,7 +384,6 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
   }
   CK(cudaMemcpy(s->norm, hn, sizeof(hn), cudaMemcpyHostToDevice));
   // initial parameters (He initialisation; output bias at the target mean)
-  std::mt19937_64 rng(seed);
   std::normal_distribution<double> nd(0.0, 1.0);
   std::vector<float> p(TRILENS_MLP_PARAMS, 0.0f);
   auto fill = [&](int off, int rows, int cols) {
@@ -390,38 +396,43 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
   const int offW4 = 128 * 24 + 128 + 2 * (128 * 128 + 128);
   for (int i = 0; i < 2 * 128; ++i) p[offW4 + i] = (float)(nd(rng) * 0.01);
   double ymean = 0, yvar = 0;
-  for (int64_t i = 0; i < N; ++i) ymean += hy[i];
-  ymean /= (double)N;
-  for (int64_t i = 0; i < N; ++i) yvar += (hy[i] - ymean) * (hy[i] - ymean);
-  yvar /= (double)N;
+  for (int64_t q = 0; q < Ntr; ++q) ymean += hy[perm[q]];
+  ymean /= (double)Ntr;
+  for (int64_t q = 0; q < Ntr; ++q) yvar += (hy[perm[q]] - ymean) * (hy[perm[q]] - ymean);
+  yvar /= (double)Ntr;
   p[offW4 + 256] = (float)ymean;
   p[offW4 + 257] = (float)log(std::max(yvar, 1e-4));
   CK(cudaMemcpy(s->prm, p.data(), sizeof(float) * TRILENS_MLP_PARAMS, cudaMemcpyHostToDevice));
   CK(cudaMemset(s->mom1, 0, sizeof(float) * TRILENS_MLP_PARAMS));
   CK(cudaMemset(s->mom2, 0, sizeof(float) * TRILENS_MLP_PARAMS));
   s->adam_step = 0;
-  // shuffled copy of the samples
-  std::vector<int64_t> perm((size_t)N);
-  for (int64_t i = 0; i < N; ++i) perm[i] = i;
-  std::shuffle(perm.begin(), perm.end(), rng);
-  std::vector<float> sx((size_t)N * 24), sy((size_t)N);
+  // shuffled copy of the samples (training part first, held-out part last)
+  std::vector<float> sx((size_t)N * 24), sy((size_t)N), sst((size_t)N);
+  std::vector<double> slab((size_t)N);
   for (int64_t i = 0; i < N; ++i) {
     for (int k = 0; k < 24; ++k) sx[i * 24 + k] = hx[perm[i] * 24 + k];
     sy[i] = hy[perm[i]];
+    sst[i] = hst[perm[i]];
+    slab[i] = hlab[perm[i]];
   }
-  float *dx = nullptr, *dy = nullptr;
+  float *dx = nullptr, *dy = nullptr, *dst = nullptr;
+  double *dlab = nullptr;
   CK(dalloc(&dx, (size_t)N * 24));
   CK(dalloc(&dy, (size_t)N));
+  CK(dalloc(&dst, (size_t)N));
+  CK(dalloc(&dlab, (size_t)N));
   CK(cudaMemcpy(dx, sx.data(), sizeof(float) * 24 * N, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dy, sy.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
-  const int64_t nb = (N + kBatch - 1) / kBatch;
+  CK(cudaMemcpy(dst, sst.data(), sizeof(float) * N, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dlab, slab.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  const int64_t nb = (Ntr + kBatch - 1) / kBatch;
   const int64_t total_steps = nb * epochs;
   const float lr0 = 2e-3f, lr1 = 5e-5f;
   int rc = TRILENS_OK;
   for (int e = 0; e < epochs && !rc; ++e) {
     double lsum = 0;
     for (int64_t b = 0; b < nb; ++b) {
-      const int64_t r0 = b * kBatch, m = std::min<int64_t>(kBatch, N - r0);
+      const int64_t r0 = b * kBatch, m = std::min<int64_t>(kBatch, Ntr - r0);
       const double t = (double)s->adam_step / (double)std::max<int64_t>(total_steps - 1, 1);
       const float lr = (float)(lr1 + 0.5 * (lr0 - lr1) * (1.0 + cos(3.14159265358979323846 * t)));
       if (tl::mlp_pack(s->prm, s->work, c->stream) ||
@@ -441,35 +452,46 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
     }
     s->last_loss = lsum;
   }
-  cudaFree(dx);
-  cudaFree(dy);
-  if (rc) return rc;
   int herr = 0;
-  CK(cudaMemcpy(&herr, s->work.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (herr) return fail(c, TRILENS_ERR_TIMEOUT, "a tensor-core wait ran out during training");
-  // calibration of the summed estimates on the training samples
-  CK(tl::mlp_pack(s->prm, s->work, c->stream));
-  double lab = 0, est = 0, st = 0;
-  unsigned zero = 0;
-  for (int64_t r0 = 0; r0 < N; r0 += s->cut_cap) {
+  if (!rc) {
+    CK(cudaMemcpy(&herr, s->work.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) rc = fail(c, TRILENS_ERR_TIMEOUT, "a tensor-core wait ran out during training");
+  }
+  // calibration of the summed estimates on the held-out samples (all of them
+  // when there are too few to hold any out)
+  const int64_t c0 = Ntr < N ? Ntr : 0;
+  double lab = 0, est = 0, stsum = 0;
+  if (!rc && tl::mlp_pack(s->prm, s->work, c->stream)) rc = fail(c, TRILENS_ERR_CUDA, "pack");
+  for (int64_t r0 = c0; !rc && r0 < N; r0 += s->cut_cap) {
     const int64_t m = std::min<int64_t>(s->cut_cap, N - r0);
-    CK(tl::mlp_forward(s->prm, s->norm, s->work, s->tx + 24 * r0, m, s->out, c->n_sm,
-                       c->p.spin_limit, c->stream));
     const unsigned mm = (unsigned)m;
-    CK(cudaMemcpyAsync(s->cut_count, &mm, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemsetAsync(s->fb_count, 0, sizeof(unsigned), c->stream));
-    CK(tl::launch_estimate(s->out, s->tst + r0, (float)s->st_calib, s->cut, s->cut_count,
-                           s->cut_cap, 1e30f, s->pred, s->fb, s->fb_count, s->cut_cap, 4 * c->n_sm,
-                           c->stream));
-    double a = 0, b = 0;
-    int rc2;
-    if ((rc2 = dsum(c, 2, s->pred, m, &a)) || (rc2 = dsum(c, 2, s->tlab + r0, m, &b))) return rc2;
+    double a = 0, b = 0, d = 0;
+    if (tl::mlp_forward(s->prm, s->norm, s->work, dx + 24 * r0, m, s->out, c->n_sm,
+                        c->p.spin_limit, c->stream) ||
+        cudaMemcpyAsync(s->cut_count, &mm, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream) ||
+        cudaMemsetAsync(s->fb_count, 0, sizeof(unsigned), c->stream) ||
+        tl::launch_estimate(s->out, dst + r0, (float)s->st_calib, s->cut, s->cut_count,
+                            s->cut_cap, 1e30f, s->pred, s->fb, s->fb_count, s->cut_cap,
+                            4 * c->n_sm, c->stream)) {
+      rc = fail(c, TRILENS_ERR_CUDA, "calibration pass failed");
+      break;
+    }
+    if ((rc = dsum(c, 2, s->pred, m, &a)) || (rc = dsum(c, 2, dlab + r0, m, &b)) ||
+        (rc = dsum(c, 3, dst + r0, m, &d)))
+      break;
     est += a;
     lab += b;
+    stsum += d;
   }
-  (void)zero;
-  (void)st;
+  cudaFree(dx);
+  cudaFree(dy);
+  cudaFree(dst);
+  cudaFree(dlab);
+  if (rc) return rc;
   s->calib = est > 0 ? lab / est : 1.0;
+  // the ST-form scale as well from the held-out part: both estimators are
+  // judged on samples they were not fitted on
+  if (stsum > 0) s->st_calib = lab / stsum;
   s->trained = true;
   return TRILENS_OK;
 }

@@ -26,12 +26,19 @@ STEPS = list(range(8, 25))
 def trained(tmp_path_factory):
     import __graft_entry__
     __graft_entry__.build()
+    # training pairs from two seeds (1 and 2); the model is fitted in the first
+    wl2 = synth.statistical_1e8(n=N, seed=2)
+    a2, b2 = synth.beams(wl2)
+    with binding.Collider(a2, b2, wl2.dt, KAPPA) as col2:
+        col2.surrogate_collect(STEPS, L)
+        extra = col2.surrogate_dataset()
     wl = synth.statistical_1e8(n=N, seed=1)
     a, b = synth.beams(wl)
     path = str(tmp_path_factory.mktemp("model") / "surrogate.bin")
     with binding.Collider(a, b, wl.dt, KAPPA) as col:
         col.surrogate_collect(STEPS, L)
         x, lab, st = col.surrogate_dataset()
+        col.surrogate_add_samples(*extra, L)
         col.surrogate_fit(epochs=30, seed=7)
         info = col.surrogate_info()
         col.surrogate_save(path)
@@ -47,7 +54,7 @@ def test_labels_and_features(trained):
     assert (x[:, 11:13] >= 0).all()       # log weight sums (w >= 1)
     dn = np.linalg.norm(x[:, 17:20], axis=1)
     assert ((dn > 0.99) & (dn <= 1.0 + 1e-5)).all()  # mean of unit directions
-    assert trained["info"]["samples"] == len(x)
+    assert trained["info"]["samples"] > len(x)  # both seeds
 
 
 def test_step_labels_sum_to_exact():
