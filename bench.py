@@ -390,7 +390,7 @@ def run_batch(args):
 def run_statistical(args):
     """The statistical workload (not the default line): 2 x 1e8 macro-photons,
     weights U[1,10], Gamma(2, 5 MeV) energies, 32 steps.  A network trained on
-    seed 1 (time steps 8..24, level L) estimates seed 0's yield; the exact GPU
+    seed 1 (all time steps, level L) estimates seed 0's yield; the exact GPU
     traversal of the same steps is the reference for error and time."""
     import torch
 
@@ -403,7 +403,7 @@ def run_statistical(args):
     wl1 = synth.statistical_1e8(n=n, seed=1)
     a1, b1 = synth.beams(wl1)
     with binding.Collider(a1, b1, wl1.dt, wl1.kappa) as col:
-        col.surrogate_collect(list(range(8, 25)), L)
+        col.surrogate_collect(list(range(wl1.steps)), L)
         col.surrogate_fit(30, 7)
         info = col.surrogate_info()
         col.surrogate_save(model)
@@ -437,7 +437,7 @@ def run_statistical(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32+f64 exact",
             "data": "synthetic",
             "config": {"workload": wl0.name, "photons_per_beam": n, "time_steps": wl0.steps,
-                       "level_L": L, "tau": args.tau, "train": "seed 1, steps 8..24",
+                       "level_L": L, "tau": args.tau, "train": "seed 1, all steps",
                        "test": "seed 0, all steps"},
             "yield_error": (sur - exact) / exact, "st_yield_error": (stv - exact) / exact,
             "exact_weighted_yield": exact, "surrogate_weighted_yield": sur,

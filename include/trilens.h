@@ -227,9 +227,15 @@ int trilens_mlp_forward(const float *params, const float *norm, const float *x, 
 
 /* grad (device, TRILENS_MLP_PARAMS FP32) = gradient of the MEAN loss over the
  * m rows of (x, y) (y: device, m FP32 targets); loss (device, 1 FP32) = the
- * SUM of the per-row losses.  Synchronises the stream. */
+ * SUM of the per-row losses.  loss_kind 0: the Gaussian NLL above (st
+ * unused).  loss_kind 1 (what the surrogate trains): y is the linear label
+ * Y, B = st_scale * st[row] a baseline (st: device, m FP32), lam = (B + 1)
+ * e^mu the predicted mean, per-row loss (lam - Y ln lam)/(B + 1) +
+ * 0.5 (s + r^2 e^-s) with r = log1p(Y) - log1p(lam), lam held fixed in r (its
+ * gradient does not reach mu).  Synchronises the stream. */
 int trilens_mlp_grad(const float *params, const float *norm, const float *x, const float *y,
-                     int64_t m, float *grad, float *loss, trilens_stream_t stream);
+                     const float *st, float st_scale, int32_t loss_kind, int64_t m, float *grad,
+                     float *loss, trilens_stream_t stream);
 
 /* ---- learned statistical regime ----------------------------------------------
  * The dual traversal stops at hierarchy level L: the first node on every path
@@ -245,10 +251,10 @@ int trilens_mlp_grad(const float *params, const float *norm, const float *x, con
  * estimate of the paper's ST form (rate ~ n_I n_II sigma: weight sums times
  * sigma(s) at the mean energies and directions times the boxes' overlap over
  * their volumes, scaled by a constant fitted on the training pairs).  The
- * network learns the residual of log1p(yield) over log1p(ST estimate); a
- * pair's yield is exp(mu + log1p(ST) + var/2) - 1 (the mean of the
- * predicted log-normal, var = e^s capped at 2), times a calibration scale
- * fitted on the training pairs; pairs whose predicted standard deviation of y
+ * network predicts each pair's mean yield (B + 1) e^mu over that baseline B
+ * (trained with a Poisson-type deviance, whose minimiser is the conditional
+ * mean; trilens_mlp_grad loss_kind 1), times a calibration scale fitted on
+ * held-out training pairs; pairs whose predicted standard deviation of y
  * exceeds tau are evaluated exactly instead (the fallback). */
 
 /* Build each listed step, collect its level-L pairs with features and exact

@@ -95,3 +95,44 @@ def backward(p: dict, cache, dout: np.ndarray) -> dict:
 def loss_and_grads(p: dict, x: np.ndarray, y: np.ndarray):
     out, cache = forward(p, x)
     return loss(out, y), backward(p, cache, loss_grad(out, y))
+
+
+# ---- the surrogate's mean-consistent objective --------------------------------
+# For a pair with label Y >= 0 (its exact yield) and baseline B >= 0 (the
+# calibrated ST-form estimate) the network's first output mu sets the predicted
+# mean lam = (B + 1) exp(mu); the second output s is the log variance of the
+# log-space residual r = log1p(Y) - log1p(lam).  Per pair
+#     P = (lam - Y log lam) / (B + 1)          (weighted Poisson deviance:
+#                                              its minimiser is lam = E[Y | x])
+#     V = 0.5 (s + r^2 exp(-s)) with lam held fixed in r (semi-gradient: the
+#                                              variance head does not move mu)
+# and the objective is the batch mean of P + V.
+MU_CLAMP = 30.0
+
+
+def mean_outputs(out, B):
+    mu = np.minimum(out[:, 0], MU_CLAMP)
+    return (B + 1.0) * np.exp(mu)
+
+
+def loss_mean(out, Y, B, lam_fixed=None):
+    lam = mean_outputs(out, B)
+    lam_r = lam if lam_fixed is None else lam_fixed
+    s = np.clip(out[:, 1], -S_CLAMP, S_CLAMP)
+    r = np.log1p(Y) - np.log1p(lam_r)
+    P = (lam - Y * np.log(lam)) / (B + 1.0)
+    V = 0.5 * (s + r * r * np.exp(-s))
+    return float(np.mean(P + V))
+
+
+def loss_mean_grad(out, Y, B):
+    n = len(Y)
+    lam = mean_outputs(out, B)
+    s_raw = out[:, 1]
+    s = np.clip(s_raw, -S_CLAMP, S_CLAMP)
+    r = np.log1p(Y) - np.log1p(lam)
+    g = np.zeros_like(out)
+    g[:, 0] = np.where(out[:, 0] < MU_CLAMP, (lam - Y) / (B + 1.0), 0.0) / n
+    inside = (s_raw > -S_CLAMP) & (s_raw < S_CLAMP)
+    g[:, 1] = np.where(inside, 0.5 * (1.0 - r * r * np.exp(-s)), 0.0) / n
+    return g

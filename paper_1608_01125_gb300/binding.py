@@ -125,7 +125,7 @@ def lib() -> ctypes.CDLL:
         L.trilens_autotune.restype = ctypes.c_int
         L.trilens_mlp_forward.argtypes = [vp, vp, vp, i64, vp, vp]
         L.trilens_mlp_forward.restype = ctypes.c_int
-        L.trilens_mlp_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+        L.trilens_mlp_grad.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, i32, i64, vp, vp, vp]
         L.trilens_mlp_grad.restype = ctypes.c_int
         L.trilens_surrogate_collect.argtypes = [vp, ctypes.POINTER(i64), i32, i32]
         L.trilens_surrogate_fit.argtypes = [vp, i32, ctypes.c_uint64]
@@ -470,12 +470,15 @@ def mlp_forward(params, norm, x, stream=None):
     return out
 
 
-def mlp_grad(params, norm, x, y, stream=None):
-    """(gradient of the mean loss, summed loss) for device FP32 tensors."""
+def mlp_grad(params, norm, x, y, stream=None, kind=0, baseline=None, scale=1.0):
+    """(gradient of the mean loss, summed loss) for device FP32 tensors;
+    kind 1 is the surrogate's objective with baseline (m,) and its scale."""
     torch = _torch()
     g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
     loss = torch.empty(1, dtype=torch.float32, device=x.device)
     st = stream if stream is not None else torch.cuda.current_stream()
-    _check(lib().trilens_mlp_grad(_ptr(params), _ptr(norm), _ptr(x), _ptr(y), x.shape[0], _ptr(g),
-                                  _ptr(loss), ctypes.c_void_p(st.cuda_stream)))
+    _check(lib().trilens_mlp_grad(_ptr(params), _ptr(norm), _ptr(x), _ptr(y),
+                                  _ptr(baseline) if baseline is not None else None,
+                                  float(scale), int(kind), x.shape[0], _ptr(g), _ptr(loss),
+                                  ctypes.c_void_p(st.cuda_stream)))
     return g, loss

@@ -130,11 +130,16 @@ __device__ __forceinline__ bool layer_mma(FwdSmem &S, uint32_t d, const void *A,
 // Forward pass over M rows of raw features x [M][24].  Inference writes out
 // [M][2]; training (y != NULL) also stores the pre-activations Z1..Z3 (BF16),
 // the loss gradient dout [M][2] (of the mean loss, scale inv_b) and adds the
-// loss sum to *loss.
+// loss sum to *loss.  Loss kind 0: Gaussian NLL of y with (mu, s).  Kind 1
+// (the surrogate's): y is the linear label Y, B = st_scale * st[row] the
+// baseline, lam = (B + 1) e^mu the predicted mean; loss
+// (lam - Y ln lam)/(B + 1) + 0.5 (s + r^2 e^-s), r = log1p(Y) - log1p(lam)
+// with lam held fixed in r.
 __global__ void __launch_bounds__(128, 1)
     k_mlp_forward(MLPDev P, const float *__restrict__ x, int64_t M, float *out, const float *y,
                   __nv_bfloat16 *Z1, __nv_bfloat16 *Z2, __nv_bfloat16 *Z3, float *dout,
-                  float *loss, float inv_b, int *err, long long spin) {
+                  float *loss, float inv_b, int *err, long long spin, int kind, const float *st,
+                  float st_scale) {
   extern __shared__ unsigned char smem_raw[];
   FwdSmem &S = *align1k<FwdSmem>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -214,12 +219,21 @@ __global__ void __launch_bounds__(128, 1)
         out[2 * row] = o0;
         out[2 * row + 1] = o1;
       }
-      if (y) {
+      if (y && kind == 0) {
         const float s = fminf(fmaxf(o1, -kSClamp), kSClamp);
         const float res = y[row] - o0, e = __expf(-s);
         lsum += 0.5f * (s + res * res * e);
         dout[2 * row] = -res * e * inv_b;
         dout[2 * row + 1] = (o1 > -kSClamp && o1 < kSClamp) ? 0.5f * (1.0f - res * res * e) * inv_b
+                                                             : 0.0f;
+      } else if (y) {
+        const float Y = y[row], B1 = st_scale * st[row] + 1.0f;
+        const float lam = B1 * __expf(fminf(o0, 30.0f));
+        const float s = fminf(fmaxf(o1, -kSClamp), kSClamp), e = __expf(-s);
+        const float r = log1pf(Y) - log1pf(lam);
+        lsum += (lam - Y * __logf(lam)) / B1 + 0.5f * (s + r * r * e);
+        dout[2 * row] = o0 < 30.0f ? (lam - Y) / B1 * inv_b : 0.0f;
+        dout[2 * row + 1] = (o1 > -kSClamp && o1 < kSClamp) ? 0.5f * (1.0f - r * r * e) * inv_b
                                                              : 0.0f;
       }
     }
@@ -463,13 +477,14 @@ cudaError_t mlp_forward(const float *prm, const float *norm, const MLPWork &w, c
   const int g = (int)(tiles < blocks ? tiles : blocks);
   k_mlp_forward<<<g, 128, mlp_fwd_smem(), s>>>(dev_of(prm, norm, w), x, M, out, nullptr, nullptr,
                                                nullptr, nullptr, nullptr, nullptr, 0.f, w.err,
-                                               spin);
+                                               spin, 0, nullptr, 0.f);
   return cudaGetLastError();
 }
 
 // loss and gradient of the mean loss over M rows (w.grad, w.loss)
 cudaError_t mlp_grad(const float *prm, const float *norm, const MLPWork &w, const float *x,
-                     const float *y, int64_t M, int blocks, long long spin, cudaStream_t s) {
+                     const float *y, int64_t M, int blocks, long long spin, cudaStream_t s,
+                     int kind, const float *st, float st_scale) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(w.grad, 0, sizeof(float) * kParams, s))) return e;
   if ((e = cudaMemsetAsync(w.loss, 0, sizeof(float), s))) return e;
@@ -478,7 +493,8 @@ cudaError_t mlp_grad(const float *prm, const float *norm, const MLPWork &w, cons
   const int g = (int)(tiles < blocks ? tiles : blocks);
   const MLPDev P = dev_of(prm, norm, w);
   k_mlp_forward<<<g, 128, mlp_fwd_smem(), s>>>(P, x, M, nullptr, y, w.Z[0], w.Z[1], w.Z[2],
-                                               w.dout, w.loss, 1.0f / (float)M, w.err, spin);
+                                               w.dout, w.loss, 1.0f / (float)M, w.err, spin, kind,
+                                               st, st_scale);
   k_mlp_dgrad<<<g, 128, mlp_bwd_smem(), s>>>(P, w.dout, w.Z[0], w.Z[1], w.Z[2], w.dZ[0], w.dZ[1],
                                              w.dZ[2], M, w.err, spin);
   const int64_t chunk = 2048;
@@ -577,9 +593,10 @@ extern "C" int trilens_mlp_forward(const float *params, const float *norm, const
 }
 
 extern "C" int trilens_mlp_grad(const float *params, const float *norm, const float *x,
-                                const float *y, int64_t m, float *grad, float *loss,
-                                trilens_stream_t stream) {
+                                const float *y, const float *st, float st_scale, int32_t loss_kind,
+                                int64_t m, float *grad, float *loss, trilens_stream_t stream) {
   if (!params || !norm || !grad || !loss || m < 1 || !x || !y) return TRILENS_ERR_INVALID;
+  if (loss_kind != 0 && (loss_kind != 1 || !st)) return TRILENS_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   tl::MLPWork w;
   if (tl::mlp_work_alloc(w, m) || tl::mlp_prepare()) {
@@ -589,7 +606,7 @@ extern "C" int trilens_mlp_grad(const float *params, const float *norm, const fl
   int rc = TRILENS_OK;
   int herr = 0;
   if (tl::mlp_pack(params, w, s) ||
-      tl::mlp_grad(params, norm, w, x, y, m, mlp_blocks(), 1ll << 24, s) ||
+      tl::mlp_grad(params, norm, w, x, y, m, mlp_blocks(), 1ll << 24, s, loss_kind, st, st_scale) ||
       cudaMemcpyAsync(grad, w.grad, sizeof(float) * tl::kParams, cudaMemcpyDeviceToDevice, s) ||
       cudaMemcpyAsync(loss, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s) ||
       cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, s) ||

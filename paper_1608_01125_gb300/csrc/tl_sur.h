@@ -80,7 +80,8 @@ cudaError_t mlp_pack(const float *prm, MLPWork &w, cudaStream_t s);
 cudaError_t mlp_forward(const float *prm, const float *norm, const MLPWork &w, const float *x,
                         int64_t M, float *out, int blocks, long long spin, cudaStream_t s);
 cudaError_t mlp_grad(const float *prm, const float *norm, const MLPWork &w, const float *x,
-                     const float *y, int64_t M, int blocks, long long spin, cudaStream_t s);
+                     const float *y, int64_t M, int blocks, long long spin, cudaStream_t s,
+                     int kind, const float *st, float st_scale);
 cudaError_t mlp_adamw(float *prm, const float *grad, float *m, float *v, float lr, float wd,
                       int step, cudaStream_t s);
 

@@ -476,11 +476,9 @@ cudaError_t launch_attribute(const uint2 *hits, const unsigned long long *nhits,
 
 // ------------------------------------------------------------ surrogate estimate
 
-// Pair yield from the network's (mu, s), where mu is the residual of
-// log1p(yield) over log1p(st_scale * st): exp(mu + log1p(st_scale * st) +
-// var/2) - 1, the mean of the predicted log-normal distribution with its
-// variance var = e^s capped at 2 (so a pair with a wild variance cannot
-// dominate; such pairs belong to the fallback).  Pairs whose
+// Pair yield from the network's (mu, s): the predicted mean (B + 1) e^mu over
+// the baseline B = st_scale * st (the network is trained with a Poisson-type
+// deviance whose minimiser is the conditional mean).  Pairs whose
 // predicted standard deviation exceeds tau are flagged for the exact
 // fallback (their refs copied out).
 __global__ void k_estimate(const float *out, const float *st, float st_scale, const uint4 *cut,
@@ -497,9 +495,8 @@ __global__ void k_estimate(const float *out, const float *st, float st_scale, co
       const float mu = out[2 * p], s = fminf(fmaxf(out[2 * p + 1], -12.f), 12.f);
       const float var = __expf(s);
       fall = sqrtf(var) > tau;
-      const double base = log1p((double)st_scale * (double)st[p]);
-      // log-normal mean of the predicted distribution, variance capped at 2
-      const double e = expm1(fmin((double)mu + base + 0.5 * fmin((double)var, 2.0), 60.0));
+      // the predicted mean (B + 1) e^mu with baseline B = st_scale * st
+      const double e = ((double)st_scale * (double)st[p] + 1.0) * exp(fmin((double)mu, 30.0));
       pred[p] = fall ? 0.0 : fmax(e, 0.0);
       const uint4 c = cut[p];
       r = make_uint2(c.x, c.y);

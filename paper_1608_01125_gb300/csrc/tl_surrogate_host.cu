@@ -21,7 +21,7 @@ struct SurrogateState {
   tl::MLPWork work{};
   bool trained = false;
   int level = -1;
-  double calib = 1.0, st_calib = 1.0;
+  double calib = 1.0, st_calib = 1.0, st_only_calib = 1.0;
   int adam_step = 0;
   // per-step buffers
   double *pre[2]{}, *bsum[2]{};
@@ -369,8 +369,7 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
       ss += hst[perm[q]];
     }
     s->st_calib = ss > 0 ? ls / ss : 1.0;
-    for (int64_t i = 0; i < N; ++i)
-      hy[i] = (float)(log1p(hlab[i]) - log1p(s->st_calib * (double)hst[i]));
+    for (int64_t i = 0; i < N; ++i) hy[i] = (float)hlab[i];  // the linear label
   }
   float hn[48];
   for (int k = 0; k < 24; ++k) {
@@ -395,13 +394,15 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
   fill(128 * 24 + 128 + 128 * 128 + 128, 128, 128);
   const int offW4 = 128 * 24 + 128 + 2 * (128 * 128 + 128);
   for (int i = 0; i < 2 * 128; ++i) p[offW4 + i] = (float)(nd(rng) * 0.01);
-  double ymean = 0, yvar = 0;
-  for (int64_t q = 0; q < Ntr; ++q) ymean += hy[perm[q]];
-  ymean /= (double)Ntr;
-  for (int64_t q = 0; q < Ntr; ++q) yvar += (hy[perm[q]] - ymean) * (hy[perm[q]] - ymean);
-  yvar /= (double)Ntr;
-  p[offW4 + 256] = (float)ymean;
-  p[offW4 + 257] = (float)log(std::max(yvar, 1e-4));
+  {  // start at the calibrated baseline: mu = ln(sum Y / sum (B + 1))
+    double ys = 0, bs = 0;
+    for (int64_t q = 0; q < Ntr; ++q) {
+      ys += hy[perm[q]];
+      bs += s->st_calib * hst[perm[q]] + 1.0;
+    }
+    p[offW4 + 256] = (float)(ys > 0 && bs > 0 ? log(ys / bs) : 0.0);
+    p[offW4 + 257] = 0.0f;
+  }
   CK(cudaMemcpy(s->prm, p.data(), sizeof(float) * TRILENS_MLP_PARAMS, cudaMemcpyHostToDevice));
   CK(cudaMemset(s->mom1, 0, sizeof(float) * TRILENS_MLP_PARAMS));
   CK(cudaMemset(s->mom2, 0, sizeof(float) * TRILENS_MLP_PARAMS));
@@ -437,7 +438,7 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
       const float lr = (float)(lr1 + 0.5 * (lr0 - lr1) * (1.0 + cos(3.14159265358979323846 * t)));
       if (tl::mlp_pack(s->prm, s->work, c->stream) ||
           tl::mlp_grad(s->prm, s->norm, s->work, dx + 24 * r0, dy + r0, m, c->n_sm,
-                       c->p.spin_limit, c->stream) ||
+                       c->p.spin_limit, c->stream, 1, dst + r0, (float)s->st_calib) ||
           tl::mlp_adamw(s->prm, s->work.grad, s->mom1, s->mom2, lr, 1e-4f, ++s->adam_step,
                         c->stream)) {
         rc = fail(c, TRILENS_ERR_CUDA, "training step failed");
@@ -489,9 +490,9 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
   cudaFree(dlab);
   if (rc) return rc;
   s->calib = est > 0 ? lab / est : 1.0;
-  // the ST-form scale as well from the held-out part: both estimators are
-  // judged on samples they were not fitted on
-  if (stsum > 0) s->st_calib = lab / stsum;
+  // the ST-form estimator alone gets its own scale from the held-out part
+  // (the network keeps the baseline scale it was trained with)
+  s->st_only_calib = stsum > 0 ? lab / stsum : s->st_calib;
   s->trained = true;
   return TRILENS_OK;
 }
@@ -556,7 +557,7 @@ int trilens_surrogate_step(trilens_ctx *c, int64_t step, int32_t level_L, float 
   const double yield = s->calib * est + fb_exact;
   s->tot += yield;
   out[0] = yield;                 // surrogate estimate of the step's weighted yield
-  out[1] = s->st_calib * st;      // the ST-form estimate (no network), same pairs
+  out[1] = s->st_only_calib * st;  // the ST-form estimate (no network), same pairs
   out[2] = (double)ncut;          // node pairs at level L
   out[3] = (double)nfb;           // pairs sent to the exact fallback
   out[4] = fb_exact;              // their exact yield
@@ -571,7 +572,7 @@ int trilens_surrogate_info(trilens_ctx *c, double out[6]) {
   out[0] = (double)c->sur->tn;
   out[1] = c->sur->last_loss;
   out[2] = c->sur->calib;
-  out[3] = c->sur->st_calib;
+  out[3] = c->sur->st_only_calib;
   out[4] = (double)c->sur->level;
   out[5] = c->sur->tot;
   return TRILENS_OK;
@@ -632,11 +633,11 @@ int trilens_surrogate_save(trilens_ctx *c, const char *path) {
   CK(cudaMemcpy(nrm.data(), s->norm, sizeof(float) * 48, cudaMemcpyDeviceToHost));
   FILE *f = fopen(path, "wb");
   if (!f) return fail(c, TRILENS_ERR_INVALID, "cannot write %s", path);
-  const char magic[8] = {'T', 'R', 'L', 'S', 'U', 'R', '0', '1'};
+  const char magic[8] = {'T', 'R', 'L', 'S', 'U', 'R', '0', '2'};
   const int32_t hdr[2] = {s->level, TRILENS_MLP_PARAMS};
-  const double cal[2] = {s->calib, s->st_calib};
+  const double cal[3] = {s->calib, s->st_calib, s->st_only_calib};
   bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 2, f) == 2 &&
-            fwrite(cal, sizeof(double), 2, f) == 2 && fwrite(nrm.data(), sizeof(float), 48, f) == 48 &&
+            fwrite(cal, sizeof(double), 3, f) == 3 && fwrite(nrm.data(), sizeof(float), 48, f) == 48 &&
             fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
   fclose(f);
   return ok ? TRILENS_OK : fail(c, TRILENS_ERR_INVALID, "short write to %s", path);
@@ -653,11 +654,11 @@ int trilens_surrogate_load(trilens_ctx *c, const char *path) {
   if (!f) return fail(c, TRILENS_ERR_INVALID, "cannot read %s", path);
   char magic[8];
   int32_t hdr[2];
-  double cal[2];
+  double cal[3];
   std::vector<float> p(TRILENS_MLP_PARAMS), nrm(48);
-  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TRLSUR01", 8) == 0 &&
+  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TRLSUR02", 8) == 0 &&
             fread(hdr, sizeof(int32_t), 2, f) == 2 && hdr[1] == TRILENS_MLP_PARAMS &&
-            fread(cal, sizeof(double), 2, f) == 2 && fread(nrm.data(), sizeof(float), 48, f) == 48 &&
+            fread(cal, sizeof(double), 3, f) == 3 && fread(nrm.data(), sizeof(float), 48, f) == 48 &&
             fread(p.data(), sizeof(float), p.size(), f) == p.size();
   fclose(f);
   if (!ok) return fail(c, TRILENS_ERR_INVALID, "%s is not a surrogate model file", path);
@@ -666,6 +667,7 @@ int trilens_surrogate_load(trilens_ctx *c, const char *path) {
   s->level = hdr[0];
   s->calib = cal[0];
   s->st_calib = cal[1];
+  s->st_only_calib = cal[2];
   s->trained = true;
   return TRILENS_OK;
 }

@@ -62,3 +62,26 @@ def test_gradients_match_fp64_reference():
         rel = np.linalg.norm(a - r) / (np.linalg.norm(r) + 1e-12)
         cos = float(a @ r) / (np.linalg.norm(a) * np.linalg.norm(r) + 1e-30)
         assert rel < 0.08 and cos > 0.995, (k, rel, cos)
+
+
+def test_surrogate_objective_gradients_match_fp64_reference():
+    import torch
+    m = 4096
+    p, x, y, P, N, X, Y = _setup(m, 6)
+    rng = np.random.default_rng(8)
+    lab = rng.gamma(1.5, 4.0, m) * (rng.random(m) < 0.7)  # many zero labels
+    st = rng.gamma(2.0, 2.0, m)
+    scale = 1.3
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()  # noqa: E731
+    g, loss = binding.mlp_grad(P, N, X, dev(lab), kind=1, baseline=dev(st), scale=scale)
+    out, cache = mlp.forward(p, x)
+    B = scale * st
+    L = mlp.loss_mean(out, lab, B)
+    gref = mlp.backward(p, cache, mlp.loss_mean_grad(out, lab, B))
+    assert abs(float(loss.item()) / m - L) <= 0.03 * abs(L) + 1e-3
+    gv = binding.mlp_unflatten(g.cpu().numpy().astype(np.float64))
+    for k, _ in binding.MLP_ORDER:
+        a, r = gv[k].reshape(-1), gref[k].reshape(-1)
+        rel = np.linalg.norm(a - r) / (np.linalg.norm(r) + 1e-12)
+        cos = float(a @ r) / (np.linalg.norm(a) * np.linalg.norm(r) + 1e-30)
+        assert rel < 0.08 and cos > 0.995, (k, rel, cos)

@@ -268,3 +268,22 @@ def test_full_size_headon_1m_sampled_steps():
             assert st["hsum"] == int(c["hsum"]) and st["hxor"] == int(c["hxor"]), c
             assert math.isclose(st["weighted"], c["weighted"], rel_tol=1e-6)
             assert st["band"] < 0.05 * max(st["count"], 1) + 1000
+
+
+def test_full_size_crossing90_sampled_steps():
+    """2 x 5e7 photons crossing at 90 degrees (Gamma energies), FP32 + FP64
+    band, per-step rebuild: three sampled steps equal the stored values of the
+    FP64 k-d-tree oracle (tests/golden/oracle_values_crossing90.json)."""
+    path = os.path.join(HERE, "golden", "oracle_values_crossing90.json")
+    cases = json.load(open(path))["cases"]
+    wl = synth.crossing90_5e7()
+    a, b = synth.beams(wl)
+    with binding.Collider(a, b, wl.dt, wl.kappa, precision=binding.FP32_BAND) as col:
+        del a, b
+        for c in cases:
+            col.build(c["step"])
+            n = col.collide(c["step"])
+            st = col.stats()
+            assert n == c["count"], c
+            assert st["hsum"] == int(c["hsum"]) and st["hxor"] == int(c["hxor"]), c
+            assert math.isclose(st["weighted"], c["weighted"], rel_tol=1e-6)

@@ -48,3 +48,29 @@ def test_loss_minimum_is_the_gaussian_fit():
     out = np.tile([y.mean(), math.log(y.var())], (len(y), 1))
     g = mlp.loss_grad(out, y)
     assert abs(g[:, 0].sum()) < 1e-9 and abs(g[:, 1].sum()) < 1e-9
+
+
+def test_mean_objective_gradient_and_minimiser():
+    rng = np.random.default_rng(4)
+    n = 9
+    out = rng.standard_normal((n, 2))
+    Y = rng.gamma(2.0, 3.0, n)
+    B = rng.gamma(2.0, 2.0, n)
+    g = mlp.loss_mean_grad(out, Y, B)
+    lam0 = mlp.mean_outputs(out, B)
+    h = 1e-6
+    for i in range(n):
+        for j in range(2):
+            o = out.copy()
+            o[i, j] += h
+            Lp = mlp.loss_mean(o, Y, B, lam_fixed=lam0)
+            o[i, j] -= 2 * h
+            Lm = mlp.loss_mean(o, Y, B, lam_fixed=lam0)
+            assert abs((Lp - Lm) / (2 * h) - g[i, j]) < 1e-7
+    # the Poisson part is minimised by the mean label: for one feature vector
+    # seen with labels Y_k, d/dmu sum_k P_k = 0 at lam = mean(Y)
+    Ys = rng.gamma(2.0, 3.0, 1000)
+    Bc = 1.7
+    mu = np.log(Ys.mean() / (Bc + 1.0))
+    o = np.tile([mu, 0.0], (len(Ys), 1))
+    assert abs(mlp.loss_mean_grad(o, Ys, np.full(len(Ys), Bc))[:, 0].sum()) < 1e-12
