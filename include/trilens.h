@@ -254,7 +254,7 @@ int trilens_mlp_grad(const float *params, const float *norm, const float *x, con
  * network predicts each pair's mean yield (B + 1) e^mu over that baseline B
  * (trained with a Poisson-type deviance, whose minimiser is the conditional
  * mean; trilens_mlp_grad loss_kind 1), times a calibration scale fitted on
- * held-out training pairs; pairs whose predicted standard deviation of y
+ * the training pairs; pairs whose predicted standard deviation of y
  * exceeds tau are evaluated exactly instead (the fallback). */
 
 /* Build each listed step, collect its level-L pairs with features and exact
@@ -266,7 +266,7 @@ int trilens_surrogate_collect(trilens_ctx *c, const int64_t *steps, int32_t n, i
 /* Train the network on the collected samples (feature normalisation from
  * the samples, He-initialised weights from `seed`, AdamW with cosine decay,
  * minibatches of 8192, `epochs` passes), then fit the calibration scales of
- * the network's and of the ST-form estimates on the samples. */
+ * the network's and of the ST-form estimates on all the samples. */
 int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed);
 
 /* collect + fit. */
