@@ -390,8 +390,9 @@ def run_batch(args):
 def run_statistical(args):
     """The statistical workload (not the default line): 2 x 1e8 macro-photons,
     weights U[1,10], Gamma(2, 5 MeV) energies, 32 steps.  A network trained on
-    seed 1 (all time steps, level L) estimates seed 0's yield; the exact GPU
-    traversal of the same steps is the reference for error and time."""
+    the draws --train-seeds (all time steps, level L) estimates seed 0's yield;
+    the exact GPU traversal of the same steps is the reference for error and
+    time.  The in-sample error on the first training draw is reported too."""
     import torch
 
     from paper_1608_01125_gb300 import binding
@@ -399,16 +400,29 @@ def run_statistical(args):
     L = args.level
     n = args.stat_photons
     model = os.path.join(tempfile.gettempdir(), f"trilens_surrogate_L{L}.bin")
+    seeds = [int(x) for x in str(args.train_seeds).split(",")]
     t0 = time.perf_counter()
-    wl1 = synth.statistical_1e8(n=n, seed=1)
+    wl1 = synth.statistical_1e8(n=n, seed=seeds[0])
     a1, b1 = synth.beams(wl1)
+    train_exact = 0.0
     with binding.Collider(a1, b1, wl1.dt, wl1.kappa) as col:
         col.surrogate_collect(list(range(wl1.steps)), L)
+        train_exact = float(col.surrogate_dataset()[1].sum())
+        for sd in seeds[1:]:  # further draws: their labelled pairs join the training set
+            wlx = synth.statistical_1e8(n=n, seed=sd)
+            ax, bx = synth.beams(wlx)
+            with binding.Collider(ax, bx, wlx.dt, wlx.kappa) as cx:
+                cx.surrogate_collect(list(range(wlx.steps)), L)
+                x, lab, st = cx.surrogate_dataset()
+            del ax, bx
+            col.surrogate_add_samples(x, lab, st, L)
         col.surrogate_fit(30, 7)
         info = col.surrogate_info()
         col.surrogate_save(model)
+        t_train = time.perf_counter() - t0
+        # in-sample: the first training draw, estimated by the fitted network
+        train_sur = sum(col.surrogate_step(k, L)["yield"] for k in range(wl1.steps))
     del a1, b1
-    t_train = time.perf_counter() - t0
     wl0 = synth.statistical_1e8(n=n, seed=0)
     a0, b0 = synth.beams(wl0)
     taus = [float(t) for t in str(args.tau).split(",")]
@@ -441,10 +455,12 @@ def run_statistical(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32+f64 exact",
                 "data": "synthetic",
                 "config": {"workload": wl0.name, "photons_per_beam": n, "time_steps": wl0.steps,
-                           "level_L": L, "tau": t, "train": "seed 1, all steps",
+                           "level_L": L, "tau": t,
+                           "train": f"seeds {args.train_seeds}, all steps",
                            "test": "seed 0, all steps"},
                 "yield_error": (a["sur"] - exact) / exact,
                 "st_yield_error": (a["st"] - exact) / exact,
+                "train_draw_yield_error": (train_sur - train_exact) / train_exact,
                 "exact_weighted_yield": exact, "surrogate_weighted_yield": a["sur"],
                 "exact_traversal_ms": ms_exact, "surrogate_ms": a["ms"], "build_ms": ms_build,
                 "pairs": a["pairs"], "fallback_pairs": a["fb"], "train_samples": info["samples"],
@@ -469,6 +485,8 @@ def main():
                     help="statistical workload: fallback threshold(s) on the predicted std, "
                          "comma-separated")
     ap.add_argument("--stat-photons", type=int, default=100_000_000)
+    ap.add_argument("--train-seeds", default="1",
+                    help="statistical workload: seeds of the training draws, comma-separated")
     ap.add_argument("--first-step", type=int, default=0,
                     help="first time step of each run (profiling a slice of the run)")
     ap.add_argument("--time-steps", type=int, default=0,

@@ -96,8 +96,13 @@ static void free_beam(tl::BuildBufs &w) {
   cudaFree(w.nodes);
   cudaFree(w.parent_leaf);
   cudaFree(w.parent_node);
-  cudaFree(w.visit);
+  cudaFree(w.rpre);
+  cudaFree(w.rsuf);
+  cudaFree(w.rtile);
+  cudaFree(w.rsuper);
   cudaFree(w.nfirst);
+  cudaFree(w.tbox);
+  cudaFree(w.tpart);
   cudaFree(w.nlev);
   cudaFree(w.sort_status);
   cudaFree(w.sort_hist);
@@ -118,10 +123,16 @@ static int alloc_beam(trilens_ctx *c, tl::BuildBufs &w, int64_t n) {
   CK(dalloc(&w.nodes, m));
   CK(dalloc(&w.parent_leaf, m));
   CK(dalloc(&w.parent_node, m));
-  CK(dalloc(&w.visit, m));
+  CK(dalloc(&w.rpre, 6 * m));
+  CK(dalloc(&w.rsuf, 6 * m));
+  CK(dalloc(&w.rtile, 6 * (size_t)tl::refit_tiles((int64_t)m)));
+  CK(dalloc(&w.rsuper, tl::refit_super_floats((int64_t)m)));
   CK(dalloc(&w.nfirst, m));
+  CK(dalloc(&w.tbox, 8));
+  CK(dalloc(&w.tpart, (size_t)((m + 255) / 256) * 6));
   CK(dalloc(&w.nlev, m));
   w.sort_tiles = (int64_t)((m + TL_SORT_TILE - 1) / TL_SORT_TILE);
+  w.sort_epoch = 0;
   CK(dalloc(&w.sort_status, (size_t)w.sort_tiles * 256));
   CK(dalloc(&w.sort_hist, 8 * 256));
   CK(dalloc(&w.sort_tile, 8));
@@ -269,6 +280,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
     CK(cudaStreamSynchronize(c->stream));
   }
   CK(tl::sort_prepare());
+  CK(tl::refit_prepare());
   int dev_sm = 0;
   CK(cudaDeviceGetAttribute(&dev_sm, cudaDevAttrMultiProcessorCount, c->device));
   c->n_sm = dev_sm;
@@ -330,10 +342,9 @@ int trilens_build(trilens_ctx *c, int64_t step) {
     CK(tl::launch_propagate(c->beam[k], ct, (float)c->L64, lo, scale, c->bits[k], w,
                             c->n_inst > 1 ? c->inst_box[k] : nullptr, c->stream));
     tmark(c, PH_PROP, k, 1);
-    CK(cudaMemsetAsync(w.visit, 0, sizeof(uint32_t) * (size_t)n, c->stream));
     tmark(c, PH_SORT, k, 0);
     CK(tl::launch_sort(w, n, c->key_bits[k], c->p.spin_limit, c->debug_stall_sort,
-                       c->build_status, &c->sel[k], c->stream));
+                       c->build_status, &c->sel[k], c->n_inst <= 1, c->stream));
     tmark(c, PH_SORT, k, 1);
     tmark(c, PH_GATHER, k, 0);
     CK(tl::launch_gather(w, n, c->sel[k], c->stream));
@@ -342,13 +353,13 @@ int trilens_build(trilens_ctx *c, int64_t step) {
     CK(tl::launch_karras(w, n, c->sel[k], c->p.leaf_bucket, c->stream));
     tmark(c, PH_EMIT, k, 1);
     tmark(c, PH_REFIT, k, 0);
-    CK(tl::launch_refit(w, n, c->L_lo, c->L_hi, c->half, c->stream));
+    CK(tl::launch_refit(w, n, c->L_lo, c->L_hi, c->half, c->n_sm, c->stream));
     tmark(c, PH_REFIT, k, 1);
-    c->phase_launches[PH_PROP] += 1;
-    c->phase_launches[PH_SORT] += n > 1 ? 2 + (c->key_bits[k] + 7) / 8 : 0;
+    c->phase_launches[PH_PROP] += c->n_inst > 1 ? 1 : 3;
+    c->phase_launches[PH_SORT] += n > 1 ? (c->n_inst <= 1 ? 1 : 2) + (c->key_bits[k] + 7) / 8 : 0;
     c->phase_launches[PH_GATHER] += 1;
     c->phase_launches[PH_EMIT] += 1;
-    c->phase_launches[PH_REFIT] += 1;
+    c->phase_launches[PH_REFIT] += tl::refit_tiles(n) > 1 ? 3 : 1;
   }
   c->built_step = step;
   return TRILENS_OK;
@@ -456,6 +467,7 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
     tcollect(c);
     const unsigned st = h.status | *c->build_status_host;
     if (st & TL_ST_TIMEOUT) {
+      c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
       CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
       CK(cudaStreamSynchronize(c->stream));
       return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit=%lld",
@@ -734,6 +746,7 @@ int trilens_batch_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
     CK(cudaStreamSynchronize(c->stream));
     const unsigned st = *c->run_status_host | *c->build_status_host;
     if (st & TL_ST_TIMEOUT) {
+      c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
       CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
       CK(cudaStreamSynchronize(c->stream));
       return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit");

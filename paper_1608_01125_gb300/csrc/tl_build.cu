@@ -228,8 +228,43 @@ __global__ void __launch_bounds__(256) k_propagate(TLBeam b, double ct, float ha
                                                    float3 scale, unsigned maxq, float4 *pos_u,
                                                    float4 *dir_u, unsigned long long *key,
                                                    uint32_t *val, const uint32_t *inst_of,
-                                                   const float4 *inst_box, int inst_shift) {
+                                                   const float4 *inst_box, int inst_shift,
+                                                   float *tpart) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tpart) {  // one beam: moments of this step's swept-box centres; keys come after
+    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sum c, sum c^2 per axis
+    if (i < b.n) {
+      const double dx = b.dx[i], dy = b.dy[i], dz = b.dz[i];
+      const double Px = __dadd_rn(b.px[i], __dmul_rn(ct, dx));
+      const double Py = __dadd_rn(b.py[i], __dmul_rn(ct, dy));
+      const double Pz = __dadd_rn(b.pz[i], __dmul_rn(ct, dz));
+      const float4 p = make_float4(__double2float_rn(Px), __double2float_rn(Py),
+                                   __double2float_rn(Pz), __double2float_rn(b.E[i]));
+      const float4 d = make_float4(__double2float_rn(dx), __double2float_rn(dy),
+                                   __double2float_rn(dz), __int_as_float((int)i));
+      pos_u[i] = p;
+      dir_u[i] = d;
+      const float c3[3] = {fmaf(halfL, d.x, p.x), fmaf(halfL, d.y, p.y), fmaf(halfL, d.z, p.z)};
+      for (int a = 0; a < 3; ++a) {
+        m[a] = c3[a];
+        m[3 + a] = c3[a] * c3[a];
+      }
+    }
+    // fixed-order block reduction: the box does not depend on scheduling
+    __shared__ float sm[8][6];
+    for (int q = 0; q < 6; ++q)
+      for (int off = 16; off; off >>= 1) m[q] += __shfl_xor_sync(0xffffffffu, m[q], off);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+      for (int q = 0; q < 6; ++q) sm[wid][q] = m[q];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      float t = 0.f;
+      for (int w8 = 0; w8 < 8; ++w8) t += sm[w8][threadIdx.x];
+      tpart[(int64_t)blockIdx.x * 6 + threadIdx.x] = t;
+    }
+    return;
+  }
   if (i >= b.n) return;
   unsigned long long ikey = 0ull;
   if (inst_of) {
@@ -256,16 +291,92 @@ __global__ void __launch_bounds__(256) k_propagate(TLBeam b, double ct, float ha
   val[i] = (uint32_t)i;
 }
 
+// Quantisation box of one beam's step from the block moments: per axis the
+// mean of the swept-box centres +- 5 standard deviations (centres outside are
+// clamped to the edge cells).  Unlike the extreme centres, the moments of a
+// large beam barely change from one draw to the next, so the cells a level of
+// the tree stands for do not either.  Summed in FP64 in a fixed order.
+__global__ void __launch_bounds__(1024) k_tbox(const float *__restrict__ tpart, int64_t nblocks,
+                                               int64_t n, unsigned maxq, float *tbox,
+                                               uint32_t *sort_hist, uint32_t *sort_tile) {
+  __shared__ double sm[1024];
+  // the key pass counts the sort's digits into these
+  for (int t = threadIdx.x; t < 8 * 256; t += 1024) sort_hist[t] = 0u;
+  if (threadIdx.x < 8) sort_tile[threadIdx.x] = 0u;
+  double acc[6] = {0., 0., 0., 0., 0., 0.};
+  for (int64_t k = threadIdx.x; k < nblocks; k += 1024)
+    for (int q = 0; q < 6; ++q) acc[q] += (double)tpart[k * 6 + q];
+  double tot[6];
+  for (int q = 0; q < 6; ++q) {
+    sm[threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int h = 512; h; h >>= 1) {
+      if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
+      __syncthreads();
+    }
+    tot[q] = sm[0];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) {
+      const double mean = tot[a] / (double)n;
+      const double var = fmax(tot[3 + a] / (double)n - mean * mean, 0.0);
+      const double h = 5.0 * sqrt(var);
+      const float lo = (float)(mean - h), hi = (float)(mean + h);
+      tbox[a] = lo;
+      tbox[3 + a] = hi > lo ? (float)maxq / (hi - lo) : 0.0f;
+    }
+}
+
+// Morton keys of the SoA written by the moment pass, quantised in its box;
+// also counts the 8-bit digits of every radix-sort pass (the sort's
+// histogram) in shared memory, flushed once per block
+__global__ void __launch_bounds__(256) k_morton(int64_t n, const float4 *__restrict__ pos_u,
+                                                const float4 *__restrict__ dir_u, float halfL,
+                                                const float *tbox, unsigned maxq, int passes,
+                                                unsigned long long *key, uint32_t *val,
+                                                uint32_t *sort_hist) {
+  __shared__ uint32_t sh[8][256];
+  for (int t = threadIdx.x; t < 8 * 256; t += 256) (&sh[0][0])[t] = 0u;
+  __syncthreads();
+  const float lx = tbox[0], ly = tbox[1], lz = tbox[2], sx = tbox[3], sy = tbox[4], sz = tbox[5];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 p = pos_u[i], d = dir_u[i];
+    const unsigned qx = quant(fmaf(halfL, d.x, p.x), lx, sx, maxq),
+                   qy = quant(fmaf(halfL, d.y, p.y), ly, sy, maxq),
+                   qz = quant(fmaf(halfL, d.z, p.z), lz, sz, maxq);
+    const unsigned long long k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    key[i] = k;
+    val[i] = (uint32_t)i;
+    for (int q = 0; q < passes; ++q) atomicAdd(&sh[q][(k >> (8 * q)) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < passes * 256; t += 256) {
+    const uint32_t v = (&sh[0][0])[t];
+    if (v) atomicAdd(&sort_hist[t], v);
+  }
+}
+
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
                              const float box_scale[3], int bits, BuildBufs &w,
                              const float4 *inst_box, cudaStream_t s) {
   if (b.n <= 0) return cudaSuccess;
   unsigned maxq = (1u << bits) - 1u;
   int blocks = (int)((b.n + 255) / 256);
+  // one beam: quantise in the moment box of this step's centres (moments,
+  // box, then the keys); several instances: each instance's a-priori box
+  const bool one = inst_box == nullptr;
   k_propagate<<<blocks, 256, 0, s>>>(b, ct, 0.5f * L, make_float3(box_lo[0], box_lo[1], box_lo[2]),
                                      make_float3(box_scale[0], box_scale[1], box_scale[2]), maxq,
                                      w.pos_u, w.dir_u, w.key[0], w.val[0], w.inst_of, inst_box,
-                                     3 * bits);
+                                     3 * bits, one ? w.tpart : nullptr);
+  if (one) {
+    k_tbox<<<1, 1024, 0, s>>>(w.tpart, blocks, b.n, maxq, w.tbox, w.sort_hist, w.sort_tile);
+    const int mblocks = blocks < 4 * 152 ? blocks : 4 * 152;
+    k_morton<<<mblocks, 256, 0, s>>>(b.n, w.pos_u, w.dir_u, 0.5f * L, w.tbox, maxq,
+                                     (3 * bits + 7) / 8, w.key[0], w.val[0], w.sort_hist);
+  }
   return cudaGetLastError();
 }
 
@@ -418,83 +529,274 @@ __device__ __forceinline__ void seg_axis(float p, float dc, float Llo, float Lhi
   hi = __fadd_ru(fmaxf(phi, qhi), half);
 }
 
-// atom.add with acquire-release semantics at device scope: orders this
-// thread's earlier box stores before the increment and the increment before
-// its later loads (PTX memory model), without a full fence
-__device__ __forceinline__ unsigned atomic_add_acq_rel(unsigned *p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-
 __device__ __forceinline__ void write_slot(TLNode *nodes, uint32_t node, uint32_t slot,
                                            const TLBox &b) {
   float *f = reinterpret_cast<float *>(&nodes[node]);
   float *o = f + (slot ? 6 : 0);
-  __stcg(o + 0, b.lx);
-  __stcg(o + 1, b.ly);
-  __stcg(o + 2, b.lz);
-  __stcg(o + 3, b.hx);
-  __stcg(o + 4, b.hy);
-  __stcg(o + 5, b.hz);
+  o[0] = b.lx;
+  o[1] = b.ly;
+  o[2] = b.lz;
+  o[3] = b.hx;
+  o[4] = b.hy;
+  o[5] = b.hz;
 }
 
-__device__ __forceinline__ TLBox read_slot(const TLNode *nodes, uint32_t node, uint32_t slot) {
-  const float *f = reinterpret_cast<const float *>(&nodes[node]) + (slot ? 6 : 0);
-  TLBox b;
-  b.lx = __ldcg(f + 0);
-  b.ly = __ldcg(f + 1);
-  b.lz = __ldcg(f + 2);
-  b.hx = __ldcg(f + 3);
-  b.hy = __ldcg(f + 4);
-  b.hz = __ldcg(f + 5);
+// Refit as range unions.  Every subtree of the Karras hierarchy holds a
+// contiguous range [f, l] of the Morton-ordered photons, so its box is the
+// union (FP32 min / max: exact, order-free) of the photons' swept boxes over
+// that range, and every node can be finished on its own, with no bottom-up
+// chain of waits:
+//   k_refit_tile   one block per tile of kRTile photons: the tile's leaf boxes
+//                  in a shared-memory sparse table (level j holds the unions of
+//                  2^j consecutive boxes), so a range inside the tile is the
+//                  union of two entries.  Writes every photon's box into its
+//                  parent's slot, the box of every node whose range lies in
+//                  the tile into its parent's slot, the prefix and suffix
+//                  unions of every photon within its tile, and the tile box.
+//   k_refit_super  one block per kRSuper tiles: the same table over tile boxes.
+//   k_refit_cross  nodes whose range spans tiles: suffix of the first tile +
+//                  the tiles in between (two table entries per super-tile
+//                  end, plus whole super-tiles) + prefix of the last tile.
+// A node's range: f = first photon (written by the emit), l = f + both child
+// counts - 1.  A Karras node's index is one end of its range, so a node whose
+// range lies in a tile has its index there too.
+constexpr int kRTile = 256, kRTileLog = 8;
+constexpr int kRSuper = 512, kRSuperLog = 9;
+
+struct Box6 {
+  float v[6];  // lo xyz, hi xyz
+};
+
+__device__ __forceinline__ Box6 empty6() {
+  const float inf = __int_as_float(0x7f800000);
+  Box6 b;
+  b.v[0] = b.v[1] = b.v[2] = inf;
+  b.v[3] = b.v[4] = b.v[5] = -inf;
   return b;
 }
 
-__global__ void __launch_bounds__(256) k_refit(int64_t n, const float4 *__restrict__ pos,
-                                               const float4 *__restrict__ dir, float Llo, float Lhi,
-                                               float half, TLNode *nodes,
-                                               const uint32_t *__restrict__ parent_leaf,
-                                               const uint32_t *__restrict__ parent_node,
-                                               uint32_t *visit, unsigned *build_status) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n || (*build_status & TL_ST_TIMEOUT)) return;
-  const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
-  const float4 p = pos[i], d = dir[i];
-  TLBox b;
-  seg_axis(p.x, d.x, Llo, Lhi, half, b.lx, b.hx);
-  seg_axis(p.y, d.y, Llo, Lhi, half, b.ly, b.hy);
-  seg_axis(p.z, d.z, Llo, Lhi, half, b.lz, b.hz);
-  uint32_t ref = parent_leaf[i];
-  // a valid hierarchy is at most 64 + 27 levels deep; the bound and the index
-  // check only guard against a corrupted one
-  for (int depth = 0;; ++depth) {
-    const uint32_t node = ref >> 1, slot = ref & 1u;
-    if (node > super || depth > 160) {
-      atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
-      return;
+__device__ __forceinline__ void join6(Box6 &a, const Box6 &b) {
+  a.v[0] = fminf(a.v[0], b.v[0]);
+  a.v[1] = fminf(a.v[1], b.v[1]);
+  a.v[2] = fminf(a.v[2], b.v[2]);
+  a.v[3] = fmaxf(a.v[3], b.v[3]);
+  a.v[4] = fmaxf(a.v[4], b.v[4]);
+  a.v[5] = fmaxf(a.v[5], b.v[5]);
+}
+
+__device__ __forceinline__ TLBox to_box(const Box6 &b) {
+  TLBox t;
+  t.lx = b.v[0];
+  t.ly = b.v[1];
+  t.lz = b.v[2];
+  t.hx = b.v[3];
+  t.hy = b.v[4];
+  t.hz = b.v[5];
+  return t;
+}
+
+// shared-memory sparse table: tab[(j * 6 + q) * W + i], W entries per level
+template <int W>
+__device__ __forceinline__ Box6 tab_get(const float *tab, int j, int i) {
+  Box6 b;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) b.v[q] = tab[(j * 6 + q) * W + i];
+  return b;
+}
+
+template <int W>
+__device__ __forceinline__ Box6 tab_query(const float *tab, int a, int b) {
+  const int j = 31 - __clz(b - a + 1);
+  Box6 r = tab_get<W>(tab, j, a);
+  join6(r, tab_get<W>(tab, j, b - (1 << j) + 1));
+  return r;
+}
+
+// fills levels 1..LOG of a W-wide table whose level 0 is in place
+template <int W, int LOG>
+__device__ __forceinline__ void tab_build(float *tab) {
+  for (int j = 1; j <= LOG; ++j) {
+    const int h = 1 << (j - 1);
+    for (int i = threadIdx.x; i + (1 << j) <= W; i += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const float x = tab[((j - 1) * 6 + q) * W + i], y = tab[((j - 1) * 6 + q) * W + i + h];
+        tab[(j * 6 + q) * W + i] = q < 3 ? fminf(x, y) : fmaxf(x, y);
+      }
     }
-    write_slot(nodes, node, slot, b);
-    if (node == super) return;
-    // release our box, acquire the sibling's: the second arrival finishes the node
-    if (atomic_add_acq_rel(&visit[node], 1u) == 0u) return;
-    const TLBox o = read_slot(nodes, node, slot ^ 1u);
-    b.lx = fminf(b.lx, o.lx);
-    b.ly = fminf(b.ly, o.ly);
-    b.lz = fminf(b.lz, o.lz);
-    b.hx = fmaxf(b.hx, o.hx);
-    b.hy = fmaxf(b.hy, o.hy);
-    b.hz = fmaxf(b.hz, o.hz);
-    ref = parent_node[node];
+    __syncthreads();
   }
 }
 
-cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float half,
-                          cudaStream_t s) {
+__device__ __forceinline__ void put6(float *dst, const Box6 &b) {
+  float2 *d2 = reinterpret_cast<float2 *>(dst);
+  d2[0] = make_float2(b.v[0], b.v[1]);
+  d2[1] = make_float2(b.v[2], b.v[3]);
+  d2[2] = make_float2(b.v[4], b.v[5]);
+}
+
+__device__ __forceinline__ Box6 get6(const float *src) {
+  const float2 *s2 = reinterpret_cast<const float2 *>(src);
+  const float2 a = s2[0], b = s2[1], c = s2[2];
+  Box6 r;
+  r.v[0] = a.x;
+  r.v[1] = a.y;
+  r.v[2] = b.x;
+  r.v[3] = b.y;
+  r.v[4] = c.x;
+  r.v[5] = c.y;
+  return r;
+}
+
+// photon range [f, l] of inner node x
+__device__ __forceinline__ void node_range(const TLNode *nodes, const uint32_t *nfirst, int64_t x,
+                                           int64_t &f, int64_t &l) {
+  const int2 cnt = *(reinterpret_cast<const int2 *>(&nodes[x].c) + 1);
+  f = nfirst[x];
+  l = f + (int64_t)cnt.x + cnt.y - 1;
+}
+
+__global__ void __launch_bounds__(kRTile) k_refit_tile(
+    int64_t n, const float4 *__restrict__ pos, const float4 *__restrict__ dir, float Llo,
+    float Lhi, float half, TLNode *nodes, const uint32_t *__restrict__ parent_leaf,
+    const uint32_t *__restrict__ parent_node, const uint32_t *__restrict__ nfirst, float *pre,
+    float *suf, float *tilebox, unsigned *build_status) {
+  extern __shared__ float tab[];  // (kRTileLog + 1) levels x 6 x kRTile
+  __shared__ unsigned abandoned;
+  const int t = threadIdx.x;
+  // one read for the whole block: other blocks of this kernel may set the flag
+  if (t == 0) abandoned = *(volatile unsigned *)build_status & TL_ST_TIMEOUT;
+  __syncthreads();
+  if (abandoned) return;  // keys unsorted: the build is abandoned
+  const int64_t base = blockIdx.x * (int64_t)kRTile;
+  const int64_t p = base + t;
+  const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
+  const int cnt = n - base < kRTile ? (int)(n - base) : kRTile;
+  Box6 b = empty6();
+  if (p < n) {
+    const float4 ps = pos[p], d = dir[p];
+    seg_axis(ps.x, d.x, Llo, Lhi, half, b.v[0], b.v[3]);
+    seg_axis(ps.y, d.y, Llo, Lhi, half, b.v[1], b.v[4]);
+    seg_axis(ps.z, d.z, Llo, Lhi, half, b.v[2], b.v[5]);
+    const uint32_t ref = parent_leaf[p];
+    if ((ref >> 1) <= super) write_slot(nodes, ref >> 1, ref & 1u, to_box(b));
+    else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) tab[q * kRTile + t] = b.v[q];
+  __syncthreads();
+  tab_build<kRTile, kRTileLog>(tab);
+  if (p < n) {
+    put6(pre + 6 * p, tab_query<kRTile>(tab, 0, t));
+    put6(suf + 6 * p, tab_query<kRTile>(tab, t, cnt - 1));
+  }
+  if (t == 0) put6(tilebox + 6 * blockIdx.x, tab_query<kRTile>(tab, 0, cnt - 1));
+  // inner node p (the super root, index n - 1, has no parent)
+  if (p < (int64_t)super) {
+    int64_t f, l;
+    node_range(nodes, nfirst, p, f, l);
+    if (f >= base && l < base + cnt) {
+      const uint32_t ref = parent_node[p];
+      if ((ref >> 1) <= super && f <= l)
+        write_slot(nodes, ref >> 1, ref & 1u, to_box(tab_query<kRTile>(tab, (int)(f - base),
+                                                                       (int)(l - base))));
+      else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+    }
+  }
+}
+
+// tables over tile boxes: stab[((s * (kRSuperLog + 1) + j) * kRSuper + i) * 6 + q]
+__global__ void __launch_bounds__(kRSuper) k_refit_super(int64_t ntile, const float *tilebox,
+                                                         float *stab,
+                                                         const unsigned *build_status) {
+  extern __shared__ float tab[];  // (kRSuperLog + 1) levels x 6 x kRSuper
+  if (*build_status & TL_ST_TIMEOUT) return;
+  const int64_t s = blockIdx.x, t0 = s * kRSuper;
+  const int t = threadIdx.x;
+  const Box6 b = t0 + t < ntile ? get6(tilebox + 6 * (t0 + t)) : empty6();
+#pragma unroll
+  for (int q = 0; q < 6; ++q) tab[q * kRSuper + t] = b.v[q];
+  __syncthreads();
+  tab_build<kRSuper, kRSuperLog>(tab);
+  float *out = stab + s * (int64_t)(kRSuperLog + 1) * kRSuper * 6;
+  for (int j = 0; j <= kRSuperLog; ++j)
+    if (t + (1 << j) <= kRSuper) put6(out + ((int64_t)j * kRSuper + t) * 6, tab_get<kRSuper>(tab, j, t));
+}
+
+__device__ __forceinline__ Box6 super_query(const float *stab, int64_t s, int a, int b) {
+  const float *tb = stab + s * (int64_t)(kRSuperLog + 1) * kRSuper * 6;
+  const int j = 31 - __clz(b - a + 1);
+  Box6 r = get6(tb + ((int64_t)j * kRSuper + a) * 6);
+  join6(r, get6(tb + ((int64_t)j * kRSuper + b - (1 << j) + 1) * 6));
+  return r;
+}
+
+// union of the tile boxes a..b (a <= b)
+__device__ __forceinline__ Box6 tiles_union(const float *stab, int64_t a, int64_t b) {
+  const int64_t s0 = a >> kRSuperLog, s1 = b >> kRSuperLog;
+  const int a0 = (int)(a & (kRSuper - 1)), b1 = (int)(b & (kRSuper - 1));
+  if (s0 == s1) return super_query(stab, s0, a0, b1);
+  Box6 r = super_query(stab, s0, a0, kRSuper - 1);
+  join6(r, super_query(stab, s1, 0, b1));
+  for (int64_t s = s0 + 1; s < s1; ++s) join6(r, super_query(stab, s, 0, kRSuper - 1));
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_refit_cross(int64_t n, TLNode *nodes,
+                                                     const uint32_t *__restrict__ parent_node,
+                                                     const uint32_t *__restrict__ nfirst,
+                                                     const float *pre, const float *suf,
+                                                     const float *stab, unsigned *build_status) {
+  if (*build_status & TL_ST_TIMEOUT) return;
+  const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < (int64_t)super;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    int64_t f, l;
+    node_range(nodes, nfirst, x, f, l);
+    const int64_t t0 = f >> kRTileLog, t1 = l >> kRTileLog;
+    if (t0 == t1) continue;  // finished by its tile
+    if (f < 0 || l >= n || f > l) {
+      atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+      continue;
+    }
+    Box6 b = get6(suf + 6 * f);
+    join6(b, get6(pre + 6 * l));
+    if (t1 - t0 >= 2) join6(b, tiles_union(stab, t0 + 1, t1 - 1));
+    const uint32_t ref = parent_node[x];
+    if ((ref >> 1) <= super) write_slot(nodes, ref >> 1, ref & 1u, to_box(b));
+    else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+  }
+}
+
+int64_t refit_tiles(int64_t n) { return (n + kRTile - 1) / kRTile; }
+int64_t refit_supers(int64_t n) { return (refit_tiles(n) + kRSuper - 1) / kRSuper; }
+size_t refit_super_floats(int64_t n) {
+  return (size_t)refit_supers(n) * (kRSuperLog + 1) * kRSuper * 6;
+}
+
+cudaError_t refit_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_refit_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (kRTileLog + 1) * 6 * kRTile * (int)sizeof(float));
+  if (e) return e;
+  return cudaFuncSetAttribute(k_refit_super, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (kRSuperLog + 1) * 6 * kRSuper * (int)sizeof(float));
+}
+
+cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float half, int n_sm,
+                         cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_refit<<<(int)((n + 255) / 256), 256, 0, s>>>(n, w.pos, w.dir, Llo, Lhi, half, w.nodes,
-                                                 w.parent_leaf, w.parent_node, w.visit,
-                                                 w.build_status);
+  const int64_t tiles = refit_tiles(n), supers = refit_supers(n);
+  k_refit_tile<<<(unsigned)tiles, kRTile, (kRTileLog + 1) * 6 * kRTile * sizeof(float), s>>>(
+      n, w.pos, w.dir, Llo, Lhi, half, w.nodes, w.parent_leaf, w.parent_node, w.nfirst, w.rpre,
+      w.rsuf, w.rtile, w.build_status);
+  if (tiles > 1) {
+    k_refit_super<<<(unsigned)supers, kRSuper, (kRSuperLog + 1) * 6 * kRSuper * sizeof(float),
+                    s>>>(tiles, w.rtile, w.rsuper, w.build_status);
+    const int64_t nb = (n + 255) / 256;
+    const int blocks = (int)(nb < 8 * n_sm ? nb : 8 * n_sm);
+    k_refit_cross<<<blocks, 256, 0, s>>>(n, w.nodes, w.parent_node, w.nfirst, w.rpre, w.rsuf,
+                                         w.rsuper, w.build_status);
+  }
   return cudaGetLastError();
 }
 

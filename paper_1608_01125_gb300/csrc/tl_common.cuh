@@ -135,12 +135,16 @@ struct BuildBufs {
   uint32_t *val[2];
   TLNode *nodes;
   uint32_t *parent_leaf, *parent_node;
-  uint32_t *visit;
+  float *rpre, *rsuf;  // per photon: union of the swept boxes from its tile's start / to its end
+  float *rtile;        // per refit tile: union of its photons' swept boxes
+  float *rsuper;       // sparse tables over the tile boxes, one per super-tile
   // sort scratch
   uint32_t *sort_status;  // tiles * 256 per pass
   uint32_t *sort_hist;    // 8 * 256 global digit counts
   uint32_t *sort_tile;    // 8 tile counters
   int64_t sort_tiles;
+  int sort_epoch;  // epoch of the last eager sort pass (0: status words must be cleared)
+
   unsigned *build_status;  // shared status word of the context's builds
   // several independent instances in one beam (NULL / 0 for a single one)
   const uint32_t *inst_of;  // instance of each input photon
@@ -151,6 +155,8 @@ struct BuildBufs {
   uint32_t *nfirst;
   uint8_t *nlev;
   int key_bits;
+  float *tpart;  // per-block moments of the swept-box centres (6 floats per 256 photons)
+  float *tbox;   // this step's quantisation box: lo xyz, scale xyz
 };
 
 // Arguments of the traversal kernels (tl_traverse.cu).
@@ -178,9 +184,14 @@ cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float bo
                              const float4 *inst_box, cudaStream_t s);
 cudaError_t sort_prepare();
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
-                        int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s);
+                        int debug_stall, unsigned int *status, int *out_sel, bool hist_ready,
+                        cudaStream_t s);
 cudaError_t launch_gather(BuildBufs &w, int64_t n, int sel, cudaStream_t s);
 cudaError_t launch_karras(BuildBufs &w, int64_t n, int sel, int bucket, cudaStream_t s);
-cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float half, cudaStream_t s);
+cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float half, int n_sm,
+                         cudaStream_t s);
+int64_t refit_tiles(int64_t n);
+size_t refit_super_floats(int64_t n);
+cudaError_t refit_prepare();
 cudaError_t launch_beam_bounds(const TLBeam &b, double *out12, cudaStream_t s);
 }  // namespace tl

@@ -11,6 +11,12 @@
 // tile only ever waits on tiles whose blocks are already running.  Every wait
 // is bounded by spin_limit; on expiry the tile records TL_ST_TIMEOUT and
 // proceeds (the result is then invalid, and the host reports the error).
+//
+// Status words: 2 flag bits (aggregate / inclusive prefix published), a
+// 3-bit pass epoch and a 27-bit count (beams hold fewer than 2^27 photons).
+// Every pass rewrites every tile's 256 words, so a word left by the previous
+// pass carries the previous epoch and reads as "not published": the array
+// needs no clearing between passes.
 #include "tl_common.cuh"
 
 namespace tl {
@@ -21,15 +27,27 @@ constexpr int kSortTile = TL_SORT_TILE;
 constexpr int kRadix = 256;
 constexpr uint32_t kAgg = 1u << 30;     // tile aggregate published
 constexpr uint32_t kPre = 2u << 30;     // inclusive prefix published
-constexpr uint32_t kValMask = kAgg - 1u;
+constexpr uint32_t kFlagMask = 3u << 30;
+constexpr int kEpochShift = 27;
+constexpr uint32_t kEpochMask = 7u << kEpochShift;
+constexpr uint32_t kValMask = (1u << kEpochShift) - 1u;
 
 __global__ void __launch_bounds__(256) k_sort_hist(const unsigned long long *__restrict__ key,
                                                    int64_t n, int passes, uint32_t *hist) {
   __shared__ uint32_t sh[8][kRadix];
   for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {  // four independent loads in flight
+    unsigned long long k[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) k[u] = key[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k[u] >> (8 * p)) & 255u], 1u);
+  }
+  for (; i < n; i += stride) {
     unsigned long long k = key[i];
     for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 255u], 1u);
   }
@@ -72,7 +90,7 @@ __global__ void __launch_bounds__(256) k_sort_pass(
     const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
     unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
     const uint32_t *__restrict__ digit_base, uint32_t *status, uint32_t *tile_ctr,
-    long long spin_limit, int debug_stall, unsigned int *st_flags) {
+    uint32_t epoch, long long spin_limit, int debug_stall, unsigned int *st_flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -120,11 +138,12 @@ __global__ void __launch_bounds__(256) k_sort_pass(
     cnt = run;
     // publish the tile aggregate, then look back over preceding tiles
     uint32_t *my = status + (int64_t)tile * kRadix + d;
+    const uint32_t ep = epoch << kEpochShift;
     uint32_t excl = 0;
     if (tile == 0) {
-      if (!debug_stall) atomicExch(my, kPre | cnt);
+      if (!debug_stall) atomicExch(my, kPre | ep | cnt);
     } else {
-      atomicExch(my, kAgg | cnt);
+      atomicExch(my, kAgg | ep | cnt);
       // walk back over the preceding tiles four at a time (independent loads),
       // adding published aggregates until an inclusive prefix is found
       int64_t j = (int64_t)tile - 1;
@@ -134,11 +153,12 @@ __global__ void __launch_bounds__(256) k_sort_pass(
         uint32_t sv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          sv[q] = j - q >= 0 ? *(volatile uint32_t *)(status + (j - q) * kRadix + d) : (uint32_t)(2u << 30);
+          sv[q] = j - q >= 0 ? *(volatile uint32_t *)(status + (j - q) * kRadix + d) : (kPre | ep);
         int used = 0;
         for (int q = 0; q < 4 && !done; ++q) {
-          const uint32_t flag = sv[q] & ~kValMask;
-          if (flag == 0u) break;  // not published yet: reload from here
+          const uint32_t flag = sv[q] & kFlagMask;
+          // not published in this pass yet: reload from here
+          if (flag == 0u || (sv[q] & kEpochMask) != ep) break;
           if (j - q >= 0) excl += sv[q] & kValMask;
           ++used;
           if (flag == kPre) done = true;
@@ -152,7 +172,7 @@ __global__ void __launch_bounds__(256) k_sort_pass(
           __nanosleep(32);
         }
       }
-      atomicExch(my, kPre | ((excl + cnt) & kValMask));
+      atomicExch(my, kPre | ep | ((excl + cnt) & kValMask));
     }
     sm.gbase[d] = digit_base[d] + excl;
     sm.scan[d] = cnt;
@@ -196,28 +216,43 @@ cudaError_t sort_prepare() {
 }
 
 // Sort w.key[0]/w.val[0] by the low key_bits bits.  *out_sel receives the
-// buffer index holding the result.
+// buffer index holding the result.  hist_ready: the key producer has already
+// counted every pass's digits into a zeroed w.sort_hist and zeroed the tile
+// counters (the single-beam build does this while it writes the keys).
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
-                        int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s) {
+                        int debug_stall, unsigned int *status, int *out_sel, bool hist_ready,
+                        cudaStream_t s) {
   *out_sel = 0;
   if (n <= 1) return cudaSuccess;
   const int passes = (key_bits + 7) / 8;
   const int64_t tiles = (n + kSortTile - 1) / kSortTile;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(w.sort_hist, 0, sizeof(uint32_t) * 8 * kRadix, s))) return e;
-  if ((e = cudaMemsetAsync(w.sort_tile, 0, sizeof(uint32_t) * 8, s))) return e;
-  {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cap))) return e;
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (!hist_ready) {
+    if ((e = cudaMemsetAsync(w.sort_hist, 0, sizeof(uint32_t) * 8 * kRadix, s))) return e;
+    if ((e = cudaMemsetAsync(w.sort_tile, 0, sizeof(uint32_t) * 8, s))) return e;
     int64_t nb = (n + 255) / 256;
-    int blocks = (int)(nb < 2048 ? nb : 2048);
+    int blocks = (int)(nb < 2 * 152 ? nb : 2 * 152);
     k_sort_hist<<<blocks, 256, 0, s>>>(w.key[0], n, passes, w.sort_hist);
-    k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_hist, passes);
   }
+  k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_hist, passes);
   int sel = 0;
   for (int p = 0; p < passes; ++p) {
-    if ((e = cudaMemsetAsync(w.sort_status, 0, sizeof(uint32_t) * kRadix * tiles, s))) return e;
+    // a captured graph replays its arguments, so it clears the words before
+    // every pass; eager launches cycle the epoch 1..7 instead
+    uint32_t epoch = 1;
+    if (capturing || w.sort_epoch == 0) {
+      if ((e = cudaMemsetAsync(w.sort_status, 0, sizeof(uint32_t) * kRadix * tiles, s))) return e;
+      w.sort_epoch = capturing ? 0 : 1;
+    } else {
+      w.sort_epoch = w.sort_epoch % 7 + 1;
+      epoch = (uint32_t)w.sort_epoch;
+    }
     k_sort_pass<<<(unsigned)tiles, kSortThreads, sizeof(SortSmem), s>>>(
         w.key[sel], w.val[sel], w.key[sel ^ 1], w.val[sel ^ 1], n, 8 * p, w.sort_hist + p * kRadix,
-        w.sort_status, w.sort_tile + p, spin_limit, debug_stall && p == 0, status);
+        w.sort_status, w.sort_tile + p, epoch, spin_limit, debug_stall && p == 0, status);
     if ((e = cudaGetLastError())) return e;
     sel ^= 1;
   }

@@ -220,7 +220,15 @@ static int sur_cut(trilens_ctx *c, int L, unsigned *ncut) {
     unsigned st = 0;
     CK(cudaMemcpyAsync(ncut, s->cut_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&st, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->build_status_host, c->build_status, sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (*c->build_status_host & TL_ST_TIMEOUT) {  // the hierarchy of this step is invalid
+      c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
+      CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      return fail(c, TRILENS_ERR_TIMEOUT, "a device wait of the build reached spin_limit");
+    }
     if (left > 0) return fail(c, TRILENS_ERR_STACK, "cut traversal did not finish");
     if (!(st & TL_ST_FRONT_OVF)) {
       CK(tl::launch_features(a.A, a.B, s->cut, s->cut_count, s->cut_cap, s->feat, s->st,

