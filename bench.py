@@ -51,8 +51,8 @@ def algorithmic_bytes(phase: str, na: int, nb: int, key_bits: tuple, hits: float
         return 4 + 32 + 32, "photon"
     if phase == "emit":        # keys read, child refs + counts + parent written
         return 8 + 16 + 4, "photon"
-    if phase == "refit":       # sorted SoA read, parent, two child boxes per node
-        return 32 + 4 + 24 + 4, "photon"
+    if phase == "refit":       # sorted SoA, parent links and ranges read; two child boxes per node
+        return 32 + 8 + 4 + 4 + 48, "photon"
     if phase == "traverse":    # node records and sorted SoA of both trees once + output pairs
         return 64 + 32, "photon"
     return 8, "pair"
@@ -309,17 +309,19 @@ def run_ours(args, wl):
     # dominant phase and its roofline
     dom = max(phase_ms, key=lambda p: phase_ms[p])
     per_unit, unit_name = algorithmic_bytes(dom, wl.a.n, wl.b.n, None, hits / K, band / K)
-    n_launch = max(launches[dom], 1)
-    if dom == "sort":
-        units_per_launch = (wl.a.n + wl.b.n) / 2  # one pass of one beam
-        algo = per_unit * units_per_launch
-        launch_ms = phase_ms[dom] / n_launch
-    elif dom in ("propagate", "gather", "emit", "refit"):
+    builds = 2 * K * nsteps  # one build per beam and step
+    if dom == "sort":  # the unit is one digit pass over one beam
+        passes = max(launches[dom] - builds, 1)  # minus one scan per build
         algo = per_unit * (wl.a.n + wl.b.n) / 2
-        launch_ms = phase_ms[dom] / n_launch
+        launch_ms = phase_ms[dom] / passes
+    elif dom in ("propagate", "gather", "emit", "refit"):  # the unit is one beam's build phase
+        algo = per_unit * (wl.a.n + wl.b.n) / 2
+        launch_ms = phase_ms[dom] / builds
     else:
+        # the traversal of one step may take several launches (passes over the
+        # pairs a warp handed on); its unit is the step
         algo = per_unit * (wl.a.n + wl.b.n) + 8.0 * (hits + band) / (K * nsteps)
-        launch_ms = phase_ms[dom] / n_launch
+        launch_ms = phase_ms[dom] / (K * nsteps)
     achieved = algo / (launch_ms / 1e3) / 1e9
     cpu = cpu_baseline(wl, a_np, b_np) if (world == 1 and not args.no_cpu_baseline) else None
     line = {

@@ -28,6 +28,14 @@ int trilens_debug_stall_sort(trilens_ctx *c, int on);
  * >= 1).  INVALID for a NULL context or limit < 1. */
 int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit);
 
+/* Capacity of the traversal-seed lists the refit writes (children with at
+ * most n/64 photons of nodes with more; normally a few hundred).  cap
+ * below the list's length makes the next collisions start from the root pair
+ * instead -- the path taken when a list overflows -- so tests can check that
+ * both starts give the same hits.  cap <= 0 restores the allocated capacity.
+ * INVALID for a NULL context. */
+int trilens_debug_set_cut_cap(trilens_ctx *c, int32_t cap);
+
 /* Evaluate the device FP64 functions of the exact decision element-wise:
  * which = 0: sigma(x) of Eq. BWcross [m^2] (0 for x <= 1); which = 1: the
  * natural log of x (x >= 1 finite; the only arguments the decision uses).

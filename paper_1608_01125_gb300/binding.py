@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_stall_sort.restype = ctypes.c_int
         L.trilens_debug_set_spin_limit.argtypes = [vp, i64]
         L.trilens_debug_set_spin_limit.restype = ctypes.c_int
+        L.trilens_debug_set_cut_cap.argtypes = [vp, ctypes.c_int32]
+        L.trilens_debug_set_cut_cap.restype = ctypes.c_int
         L.trilens_debug_eval64.argtypes = [vp, vp, i64, i32, vp]
         L.trilens_debug_eval64.restype = ctypes.c_int
         L.trilens_debug_timing.argtypes = [vp, ctypes.c_int]
@@ -341,6 +343,9 @@ class Collider:
 
     def debug_set_spin_limit(self, limit: int):
         _check(lib().trilens_debug_set_spin_limit(self.ctx, int(limit)), self.ctx)
+
+    def debug_set_cut_cap(self, cap: int):
+        _check(lib().trilens_debug_set_cut_cap(self.ctx, int(cap)), self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

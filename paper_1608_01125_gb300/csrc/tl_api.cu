@@ -19,6 +19,9 @@ cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t s
                              const unsigned *build_status, cudaStream_t s);
 cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
                           int max_levels, cudaStream_t s);
+cudaError_t launch_seed_cut(const TravArgs &a, const uint32_t *cutA, const unsigned *cntA,
+                            uint32_t capA, const uint32_t *cutB, const unsigned *cntB,
+                            uint32_t capB, uint2 *F0, unsigned cap, int blocks, cudaStream_t s);
 cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm);
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
                             unsigned long long list_n, int from_frontier, int budget, int blocks,
@@ -100,11 +103,13 @@ static void free_beam(tl::BuildBufs &w) {
   cudaFree(w.rsuf);
   cudaFree(w.rtile);
   cudaFree(w.rsuper);
+  cudaFree(w.cut);
+  cudaFree(w.cut_n);
   cudaFree(w.nfirst);
-  cudaFree(w.tbox);
-  cudaFree(w.tpart);
+  cudaFree(w.nlast);
   cudaFree(w.nlev);
   cudaFree(w.sort_status);
+  cudaFree(w.sort_raw);
   cudaFree(w.sort_hist);
   cudaFree(w.sort_tile);
   memset(&w, 0, sizeof(w));
@@ -128,12 +133,21 @@ static int alloc_beam(trilens_ctx *c, tl::BuildBufs &w, int64_t n) {
   CK(dalloc(&w.rtile, 6 * (size_t)tl::refit_tiles((int64_t)m)));
   CK(dalloc(&w.rsuper, tl::refit_super_floats((int64_t)m)));
   CK(dalloc(&w.nfirst, m));
-  CK(dalloc(&w.tbox, 8));
-  CK(dalloc(&w.tpart, (size_t)((m + 255) / 256) * 6));
+  CK(dalloc(&w.nlast, m));
   CK(dalloc(&w.nlev, m));
+  // traversal seeds for beams of 2^17 photons or more: about 256-512 cut nodes
+  // (more where small siblings hang off long chains; past the capacity the
+  // traversal starts from the roots)
+  w.cut_S = n >= 131072 ? (uint32_t)(n >> 8) : 0u;
+  w.cut_cap = w.cut_S ? (uint32_t)(8 * (n / w.cut_S) + 32) : 0u;
+  w.cut_alloc = w.cut_cap;
+  CK(dalloc(&w.cut, std::max<size_t>(w.cut_cap, 1)));
+  CK(dalloc(&w.cut_n, 1));
   w.sort_tiles = (int64_t)((m + TL_SORT_TILE - 1) / TL_SORT_TILE);
   w.sort_epoch = 0;
   CK(dalloc(&w.sort_status, (size_t)w.sort_tiles * 256));
+  CK(dalloc(&w.sort_raw, 8 * 256));
+  CK(cudaMemsetAsync(w.sort_raw, 0, sizeof(uint32_t) * 8 * 256, c->stream));
   CK(dalloc(&w.sort_hist, 8 * 256));
   CK(dalloc(&w.sort_tile, 8));
   return TRILENS_OK;
@@ -182,7 +196,6 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFree(c->ctr);
   cudaFree(c->partials);
   cudaFree(c->build_status);
-  cudaFree(c->bounds_dev);
   surrogate_free(c);
   cudaFreeHost(c->ctr_host);
   cudaFreeHost(c->build_status_host);
@@ -256,7 +269,6 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
     nk.pref = (float)(0.5 * TL_PI * TL_RE * TL_RE);
   }
   // workspace
-  CK(dalloc(&c->bounds_dev, 24));
   CK(dalloc(&c->build_status, 1));
   CK(cudaMallocHost((void **)&c->build_status_host, sizeof(unsigned)));
   CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
@@ -273,11 +285,16 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
     c->bits[k] = std::min(21, std::max(4, (lg + 2) / 3 + 3));
     c->key_bits[k] = 3 * c->bits[k];
     c->w[k].key_bits = c->key_bits[k];
-    // one-time bounds of p0 and d for the Morton box
-    CK(tl::launch_beam_bounds(c->beam[k], c->bounds_dev, c->stream));
-    CK(cudaMemcpyAsync(c->bounds[k], c->bounds_dev, sizeof(double) * 12, cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    // one-time moments of p0 and d for the Morton box of every step
+    double *mom = nullptr;
+    CK(cudaMalloc((void **)&mom, sizeof(double) * 15 * (1 + 4 * 152)));
+    cudaError_t me = tl::launch_beam_moments(c->beam[k], mom, mom + 15, c->stream);
+    if (!me)
+      me = cudaMemcpyAsync(c->moments[k], mom, sizeof(double) * 15, cudaMemcpyDeviceToHost,
+                           c->stream);
+    if (!me) me = cudaStreamSynchronize(c->stream);
+    cudaFree(mom);
+    CK(me);
   }
   CK(tl::sort_prepare());
   CK(tl::refit_prepare());
@@ -294,7 +311,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   c->trav_blocks = bps * c->n_sm;
   c->expand_blocks = 2 * c->n_sm;
   c->front_target = (unsigned)std::min<long long>(2ll * c->trav_blocks * c->trav_warps, 1 << 16);
-  c->front_cap = 4 * c->front_target + 64;
+  c->front_cap = std::max(4 * c->front_target + 64, c->w[0].cut_cap * c->w[1].cut_cap + 64);
   CK(dalloc(&c->front[0], c->front_cap));
   CK(dalloc(&c->front[1], c->front_cap));
   c->spill_cap = std::max<unsigned long long>(1 << 20, 2ull * c->trav_blocks * c->trav_warps *
@@ -323,14 +340,22 @@ int trilens_build(trilens_ctx *c, int64_t step) {
   for (int k = 0; k < 2; ++k) {
     const int64_t n = c->beam[k].n;
     if (n <= 0) continue;
+    // Morton box of the step: per axis the mean of the swept boxes' centres
+    // c = p0 + T d +- 5 standard deviations, in closed form from the beam's
+    // moments (centres outside are clamped to the edge cells).  Unlike the
+    // extreme centres, the moments of a large beam barely change from one
+    // draw to the next, so neither do the cells a level of the hierarchy
+    // stands for.  (Batches use each instance's own box, below.)
     float lo[3], scale[3];
     const double maxq = (double)((1u << c->bits[k]) - 1u);
     for (int a = 0; a < 3; ++a) {
-      const double *bd = c->bounds[k];
-      double l = bd[a] + T * bd[3 + a];        // min p0 + T min d
-      double h = bd[6 + a] + T * bd[9 + a];    // max p0 + T max d
-      lo[a] = (float)l;
-      scale[a] = h > l ? (float)(maxq / (h - l)) : 0.0f;
+      const double *m = c->moments[k], nn = (double)n;
+      const double mean = (m[a] + T * m[3 + a]) / nn;
+      const double msq = (m[6 + a] + 2.0 * T * m[9 + a] + T * T * m[12 + a]) / nn;
+      const double h = 5.0 * std::sqrt(std::max(msq - mean * mean, 0.0));
+      const float l = (float)(mean - h), u = (float)(mean + h);
+      lo[a] = l;
+      scale[a] = u > l ? (float)(maxq / ((double)u - (double)l)) : 0.0f;
     }
     tl::BuildBufs &w = c->w[k];
     tmark(c, PH_PROP, k, 0);
@@ -340,11 +365,12 @@ int trilens_build(trilens_ctx *c, int64_t step) {
       CK(cudaMemsetAsync(c->inst_root[k], 0xff, sizeof(uint32_t) * c->n_inst, c->stream));
     }
     CK(tl::launch_propagate(c->beam[k], ct, (float)c->L64, lo, scale, c->bits[k], w,
-                            c->n_inst > 1 ? c->inst_box[k] : nullptr, c->stream));
+                            c->n_inst > 1 ? c->inst_box[k] : nullptr,
+                            n > 1 ? (c->key_bits[k] + 7) / 8 : 0, c->stream));
     tmark(c, PH_PROP, k, 1);
     tmark(c, PH_SORT, k, 0);
     CK(tl::launch_sort(w, n, c->key_bits[k], c->p.spin_limit, c->debug_stall_sort,
-                       c->build_status, &c->sel[k], c->n_inst <= 1, c->stream));
+                       c->build_status, &c->sel[k], c->stream));
     tmark(c, PH_SORT, k, 1);
     tmark(c, PH_GATHER, k, 0);
     CK(tl::launch_gather(w, n, c->sel[k], c->stream));
@@ -355,8 +381,8 @@ int trilens_build(trilens_ctx *c, int64_t step) {
     tmark(c, PH_REFIT, k, 0);
     CK(tl::launch_refit(w, n, c->L_lo, c->L_hi, c->half, c->n_sm, c->stream));
     tmark(c, PH_REFIT, k, 1);
-    c->phase_launches[PH_PROP] += c->n_inst > 1 ? 1 : 3;
-    c->phase_launches[PH_SORT] += n > 1 ? (c->n_inst <= 1 ? 1 : 2) + (c->key_bits[k] + 7) / 8 : 0;
+    c->phase_launches[PH_PROP] += 1;
+    c->phase_launches[PH_SORT] += n > 1 ? 1 + (c->key_bits[k] + 7) / 8 : 0;
     c->phase_launches[PH_GATHER] += 1;
     c->phase_launches[PH_EMIT] += 1;
     c->phase_launches[PH_REFIT] += tl::refit_tiles(n) > 1 ? 3 : 1;
@@ -405,10 +431,18 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
   TLCounters &h = *c->ctr_host;
   while (true) {
     tl::TravArgs a = trav_args(c, ct);
+    // large single problems start from the refit's cut lists; small ones and
+    // batches expand their root pairs breadth first
+    const bool use_cut = !seeds && c->n_inst <= 1 && c->w[0].cut_S && c->w[1].cut_S;
     tmark(c, PH_EXPAND, 0, 0);
     CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super,
-                            (c->n_inst > 1 || seeds) ? 0 : nonempty, c->build_status, c->stream));
-    if (!seeds) {
+                            (c->n_inst > 1 || seeds || use_cut) ? 0 : nonempty, c->build_status,
+                            c->stream));
+    if (use_cut) {
+      CK(tl::launch_seed_cut(a, c->w[0].cut, c->w[0].cut_n, c->w[0].cut_cap, c->w[1].cut,
+                             c->w[1].cut_n, c->w[1].cut_cap, c->front[0], c->front_cap,
+                             2 * c->n_sm, c->stream));
+    } else if (!seeds) {
       if (c->n_inst > 1)
         CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
                                      c->n_inst, c->stream));
@@ -623,6 +657,7 @@ int trilens_batch_create(trilens_ctx **out, const trilens_beam *a, const trilens
     c->w[k].inst_of = c->inst_of[k];
   }
   c->n_inst = n_inst;
+  for (int k = 0; k < 2; ++k) c->w[k].cut_S = 0;  // batches seed from instance roots
   int ib = 0;
   while ((1 << ib) < n_inst) ++ib;
   int lg = 0;
@@ -801,7 +836,8 @@ static int apply_tuning(trilens_ctx *c, int bucket, int depth, int warps, int bu
   c->trav_blocks = bps * c->n_sm;
   c->budget = budget;
   c->front_target = (unsigned)std::min<long long>(2ll * c->trav_blocks * c->trav_warps, 1 << 16);
-  const unsigned need_front = (unsigned)c->n_inst + 4 * c->front_target + 64;
+  const unsigned need_front = std::max((unsigned)c->n_inst + 4 * c->front_target + 64,
+                                      c->w[0].cut_cap * c->w[1].cut_cap + 64);
   if (need_front > c->front_cap) {
     c->front_cap = need_front;
     for (int k = 0; k < 2; ++k) {
@@ -1043,6 +1079,15 @@ int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int r
 int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit) {
   if (!c || limit < 1) return TRILENS_ERR_INVALID;
   c->p.spin_limit = limit;
+  return TRILENS_OK;
+}
+
+int trilens_debug_set_cut_cap(trilens_ctx *c, int32_t cap) {
+  if (!c) return TRILENS_ERR_INVALID;
+  for (int k = 0; k < 2; ++k) {
+    tl::BuildBufs &w = c->w[k];
+    w.cut_cap = (cap <= 0 || (uint32_t)cap > w.cut_alloc) ? w.cut_alloc : (uint32_t)cap;
+  }
   return TRILENS_OK;
 }
 

@@ -1,14 +1,16 @@
 // tl_build.cu -- per-step hierarchy build for one beam.
 //
 //   propagate   positions in closed form (FP64), FP32 SoA, Morton key of the
-//               swept box's centre (one pass over the FP64 input)
+//               swept box's centre in the step's moment box, and the radix
+//               sort's digit histogram (one pass over the FP64 input)
 //   gather      SoA into Morton order
 //   karras      inner nodes of the binary radix tree over the sorted keys
 //               (Karras 2012, "Maximizing parallelism in the construction of
 //               BVHs, octrees and k-d trees"), leaf buckets of <= B photons
-//   refit       bottom-up union of swept boxes (Sec. 2.1: each box covers the
-//               travel of its photons during the step), one atomic arrival
-//               counter per node, no waiting
+//   refit       every node's box as the union of its photons' swept boxes
+//               (Sec. 2.1: each box covers the travel of its photons during
+//               the step) over its contiguous photon range: sparse tables per
+//               tile and over tiles, no atomics and no waiting
 #include "tl_common.cuh"
 
 namespace tl {
@@ -20,71 +22,61 @@ __device__ __forceinline__ long long ord64(double x) {
   return i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
 }
 
-// min and max over the beam of p0 and d per axis (12 ordered int64s:
-// min px py pz dx dy dz, then max ...).  Used only to pick the Morton
-// quantisation box; no result depends on it.
-__global__ void k_beam_bounds(TLBeam b, long long *out) {
-  long long mn[6], mx[6];
-  for (int c = 0; c < 6; ++c) {
-    mn[c] = 0x7fffffffffffffffLL;
-    mx[c] = -0x7fffffffffffffffLL - 1;
-  }
+// One-time moments of a beam for the Morton box: per axis a the sums of p0,
+// d, p0^2, p0 d and d^2 (15 FP64 values), in a fixed order (per-block sums,
+// then one block over the blocks), so the box never depends on scheduling.
+// The swept-box centre at step k is c = p0 + T d (T = c t_k + c dt / 2), so
+// its mean and variance over the beam follow in closed form for every step.
+constexpr int kMomentBlocks = 4 * 152;
+
+__global__ void __launch_bounds__(256) k_beam_moments(TLBeam b, double *part) {
+  double m[15];
+  for (int q = 0; q < 15; ++q) m[q] = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double v[6] = {b.px[i], b.py[i], b.pz[i], b.dx[i], b.dy[i], b.dz[i]};
-    for (int c = 0; c < 6; ++c) {
-      long long o = ord64(v[c]);
-      mn[c] = min(mn[c], o);
-      mx[c] = max(mx[c], o);
+    const double p[3] = {b.px[i], b.py[i], b.pz[i]}, d[3] = {b.dx[i], b.dy[i], b.dz[i]};
+    for (int a = 0; a < 3; ++a) {
+      m[a] += p[a];
+      m[3 + a] += d[a];
+      m[6 + a] += p[a] * p[a];
+      m[9 + a] += p[a] * d[a];
+      m[12 + a] += d[a] * d[a];
     }
   }
-  for (int c = 0; c < 6; ++c) {
-    for (int off = 16; off; off >>= 1) {
-      mn[c] = min(mn[c], __shfl_xor_sync(0xffffffffu, mn[c], off));
-      mx[c] = max(mx[c], __shfl_xor_sync(0xffffffffu, mx[c], off));
-    }
-  }
-  if ((threadIdx.x & 31) == 0) {
-    for (int c = 0; c < 6; ++c) {
-      atomicMin(&out[c], mn[c]);
-      atomicMax(&out[6 + c], mx[c]);
-    }
+  __shared__ double sm[8][15];
+  for (int q = 0; q < 15; ++q)
+    for (int off = 16; off; off >>= 1) m[q] += __shfl_xor_sync(0xffffffffu, m[q], off);
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 15; ++q) sm[threadIdx.x >> 5][q] = m[q];
+  __syncthreads();
+  if (threadIdx.x < 15) {
+    double t = 0.0;
+    for (int w8 = 0; w8 < 8; ++w8) t += sm[w8][threadIdx.x];
+    part[blockIdx.x * 15 + threadIdx.x] = t;
   }
 }
 
-__global__ void k_bounds_init(long long *out) {
-  int c = threadIdx.x;
-  if (c < 6) out[c] = 0x7fffffffffffffffLL;
-  else if (c < 12) out[c] = -0x7fffffffffffffffLL - 1;
-}
-
-__global__ void k_bounds_decode(const long long *in, double *out) {
-  int c = threadIdx.x;
-  if (c < 12) {
-    long long i = in[c];
-    i = i >= 0 ? i : i ^ 0x7fffffffffffffffLL;
-    out[c] = __longlong_as_double(i);
+__global__ void k_beam_moments_final(const double *part, int nparts, double *out) {
+  if (threadIdx.x < 15) {
+    double t = 0.0;
+    for (int k = 0; k < nparts; ++k) t += part[k * 15 + threadIdx.x];
+    out[threadIdx.x] = t;
   }
 }
 
-cudaError_t launch_beam_bounds(const TLBeam &b, double *out12, cudaStream_t s) {
-  // out12 is device memory of 24 doubles: the first 12 receive the result,
-  // the last 12 are scratch for the ordered integers
-  long long *tmp = reinterpret_cast<long long *>(out12 + 12);
-  k_bounds_init<<<1, 32, 0, s>>>(tmp);
-  if (b.n > 0) {
-    int64_t nb = (b.n + 255) / 256;
-    int blocks = (int)(nb < 1024 ? nb : 1024);
-    k_beam_bounds<<<blocks, 256, 0, s>>>(b, tmp);
-  }
-  k_bounds_decode<<<1, 32, 0, s>>>(tmp, out12);
+// out15: device, 15 doubles; scratch: device, 15 * kMomentBlocks doubles
+cudaError_t launch_beam_moments(const TLBeam &b, double *out15, double *scratch, cudaStream_t s) {
+  const int64_t nb = (b.n + 255) / 256;
+  const int blocks = (int)(nb < 1 ? 1 : (nb < kMomentBlocks ? nb : kMomentBlocks));
+  k_beam_moments<<<blocks, 256, 0, s>>>(b, scratch);
+  k_beam_moments_final<<<1, 32, 0, s>>>(scratch, blocks, out15);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- instances
 
 // Per-instance min and max of p0 and d (12 ordered int64 per instance, laid
-// out like k_beam_bounds).  A warp whose lanes share one instance reduces
+// out as p0 min xyz, d min xyz, p0 max xyz, d max xyz).  A warp whose lanes share one instance reduces
 // first and issues one atomic per quantity.
 __global__ void k_inst_bounds(TLBeam b, const uint32_t *inst_of, long long *out) {
   const int lane = threadIdx.x & 31;
@@ -218,165 +210,75 @@ __device__ __forceinline__ unsigned quant(float c, float lo, float scale, unsign
   return (unsigned)f;
 }
 
-// One thread per photon: P = p0 + (c t_k) d in FP64 (the definition's
-// operation order), rounded to the FP32 SoA; key of the swept segment's
-// centre P + (L/2) d quantised in the beam's box.
-// With several instances (inst_of != NULL) each photon is quantised in its
-// own instance's box and its instance number sits above the Morton bits, so
-// one sort orders the photons by instance, then along the Morton curve.
+// Propagate p = p0 + c t_k d in FP64 (closed form), round to the FP32 SoA,
+// and key every photon by the Morton code of its swept box's centre in the
+// box (lo, scale) -- with several instances, its instance's box, and the
+// instance number above the Morton bits.  With passes > 0 also counts the
+// 8-bit digits of every radix-sort pass (the sort's histogram) in shared
+// memory, flushed once per block into the zeroed raw histogram.  A fixed
+// grid of at most kPropBlocks blocks, grid-stride.
+constexpr int kPropBlocks = 4 * 152;
+
 __global__ void __launch_bounds__(256) k_propagate(TLBeam b, double ct, float halfL, float3 lo,
                                                    float3 scale, unsigned maxq, float4 *pos_u,
                                                    float4 *dir_u, unsigned long long *key,
                                                    uint32_t *val, const uint32_t *inst_of,
                                                    const float4 *inst_box, int inst_shift,
-                                                   float *tpart) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tpart) {  // one beam: moments of this step's swept-box centres; keys come after
-    float m[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sum c, sum c^2 per axis
-    if (i < b.n) {
-      const double dx = b.dx[i], dy = b.dy[i], dz = b.dz[i];
-      const double Px = __dadd_rn(b.px[i], __dmul_rn(ct, dx));
-      const double Py = __dadd_rn(b.py[i], __dmul_rn(ct, dy));
-      const double Pz = __dadd_rn(b.pz[i], __dmul_rn(ct, dz));
-      const float4 p = make_float4(__double2float_rn(Px), __double2float_rn(Py),
-                                   __double2float_rn(Pz), __double2float_rn(b.E[i]));
-      const float4 d = make_float4(__double2float_rn(dx), __double2float_rn(dy),
-                                   __double2float_rn(dz), __int_as_float((int)i));
-      pos_u[i] = p;
-      dir_u[i] = d;
-      const float c3[3] = {fmaf(halfL, d.x, p.x), fmaf(halfL, d.y, p.y), fmaf(halfL, d.z, p.z)};
-      for (int a = 0; a < 3; ++a) {
-        m[a] = c3[a];
-        m[3 + a] = c3[a] * c3[a];
-      }
-    }
-    // fixed-order block reduction: the box does not depend on scheduling
-    __shared__ float sm[8][6];
-    for (int q = 0; q < 6; ++q)
-      for (int off = 16; off; off >>= 1) m[q] += __shfl_xor_sync(0xffffffffu, m[q], off);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
-      for (int q = 0; q < 6; ++q) sm[wid][q] = m[q];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-      float t = 0.f;
-      for (int w8 = 0; w8 < 8; ++w8) t += sm[w8][threadIdx.x];
-      tpart[(int64_t)blockIdx.x * 6 + threadIdx.x] = t;
-    }
-    return;
-  }
-  if (i >= b.n) return;
-  unsigned long long ikey = 0ull;
-  if (inst_of) {
-    const uint32_t q = inst_of[i];
-    const float4 bl = inst_box[2 * q], bs = inst_box[2 * q + 1];
-    lo = make_float3(bl.x, bl.y, bl.z);
-    scale = make_float3(bs.x, bs.y, bs.z);
-    ikey = (unsigned long long)q << inst_shift;
-  }
-  const double dx = b.dx[i], dy = b.dy[i], dz = b.dz[i];
-  const double Px = __dadd_rn(b.px[i], __dmul_rn(ct, dx));
-  const double Py = __dadd_rn(b.py[i], __dmul_rn(ct, dy));
-  const double Pz = __dadd_rn(b.pz[i], __dmul_rn(ct, dz));
-  float4 p = make_float4(__double2float_rn(Px), __double2float_rn(Py), __double2float_rn(Pz),
-                         __double2float_rn(b.E[i]));
-  float4 d = make_float4(__double2float_rn(dx), __double2float_rn(dy), __double2float_rn(dz),
-                         __int_as_float((int)i));
-  pos_u[i] = p;
-  dir_u[i] = d;
-  const float cx = fmaf(halfL, d.x, p.x), cy = fmaf(halfL, d.y, p.y), cz = fmaf(halfL, d.z, p.z);
-  const unsigned qx = quant(cx, lo.x, scale.x, maxq), qy = quant(cy, lo.y, scale.y, maxq),
-                 qz = quant(cz, lo.z, scale.z, maxq);
-  key[i] = ikey | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-  val[i] = (uint32_t)i;
-}
-
-// Quantisation box of one beam's step from the block moments: per axis the
-// mean of the swept-box centres +- 5 standard deviations (centres outside are
-// clamped to the edge cells).  Unlike the extreme centres, the moments of a
-// large beam barely change from one draw to the next, so the cells a level of
-// the tree stands for do not either.  Summed in FP64 in a fixed order.
-__global__ void __launch_bounds__(1024) k_tbox(const float *__restrict__ tpart, int64_t nblocks,
-                                               int64_t n, unsigned maxq, float *tbox,
-                                               uint32_t *sort_hist, uint32_t *sort_tile) {
-  __shared__ double sm[1024];
-  // the key pass counts the sort's digits into these
-  for (int t = threadIdx.x; t < 8 * 256; t += 1024) sort_hist[t] = 0u;
-  if (threadIdx.x < 8) sort_tile[threadIdx.x] = 0u;
-  double acc[6] = {0., 0., 0., 0., 0., 0.};
-  for (int64_t k = threadIdx.x; k < nblocks; k += 1024)
-    for (int q = 0; q < 6; ++q) acc[q] += (double)tpart[k * 6 + q];
-  double tot[6];
-  for (int q = 0; q < 6; ++q) {
-    sm[threadIdx.x] = acc[q];
-    __syncthreads();
-    for (int h = 512; h; h >>= 1) {
-      if (threadIdx.x < h) sm[threadIdx.x] += sm[threadIdx.x + h];
-      __syncthreads();
-    }
-    tot[q] = sm[0];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    for (int a = 0; a < 3; ++a) {
-      const double mean = tot[a] / (double)n;
-      const double var = fmax(tot[3 + a] / (double)n - mean * mean, 0.0);
-      const double h = 5.0 * sqrt(var);
-      const float lo = (float)(mean - h), hi = (float)(mean + h);
-      tbox[a] = lo;
-      tbox[3 + a] = hi > lo ? (float)maxq / (hi - lo) : 0.0f;
-    }
-}
-
-// Morton keys of the SoA written by the moment pass, quantised in its box;
-// also counts the 8-bit digits of every radix-sort pass (the sort's
-// histogram) in shared memory, flushed once per block
-__global__ void __launch_bounds__(256) k_morton(int64_t n, const float4 *__restrict__ pos_u,
-                                                const float4 *__restrict__ dir_u, float halfL,
-                                                const float *tbox, unsigned maxq, int passes,
-                                                unsigned long long *key, uint32_t *val,
-                                                uint32_t *sort_hist) {
+                                                   int passes, uint32_t *hist) {
   __shared__ uint32_t sh[8][256];
-  for (int t = threadIdx.x; t < 8 * 256; t += 256) (&sh[0][0])[t] = 0u;
-  __syncthreads();
-  const float lx = tbox[0], ly = tbox[1], lz = tbox[2], sx = tbox[3], sy = tbox[4], sz = tbox[5];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+  if (passes > 0) {
+    for (int t = threadIdx.x; t < 8 * 256; t += 256) (&sh[0][0])[t] = 0u;
+    __syncthreads();
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b.n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 p = pos_u[i], d = dir_u[i];
-    const unsigned qx = quant(fmaf(halfL, d.x, p.x), lx, sx, maxq),
-                   qy = quant(fmaf(halfL, d.y, p.y), ly, sy, maxq),
-                   qz = quant(fmaf(halfL, d.z, p.z), lz, sz, maxq);
-    const unsigned long long k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    unsigned long long ikey = 0ull;
+    float3 l3 = lo, s3 = scale;
+    if (inst_of) {
+      const uint32_t q = inst_of[i];
+      const float4 bl = inst_box[2 * q], bs = inst_box[2 * q + 1];
+      l3 = make_float3(bl.x, bl.y, bl.z);
+      s3 = make_float3(bs.x, bs.y, bs.z);
+      ikey = (unsigned long long)q << inst_shift;
+    }
+    const double dx = b.dx[i], dy = b.dy[i], dz = b.dz[i];
+    const double Px = __dadd_rn(b.px[i], __dmul_rn(ct, dx));
+    const double Py = __dadd_rn(b.py[i], __dmul_rn(ct, dy));
+    const double Pz = __dadd_rn(b.pz[i], __dmul_rn(ct, dz));
+    const float4 p = make_float4(__double2float_rn(Px), __double2float_rn(Py),
+                                 __double2float_rn(Pz), __double2float_rn(b.E[i]));
+    const float4 d = make_float4(__double2float_rn(dx), __double2float_rn(dy),
+                                 __double2float_rn(dz), __int_as_float((int)i));
+    pos_u[i] = p;
+    dir_u[i] = d;
+    const unsigned qx = quant(fmaf(halfL, d.x, p.x), l3.x, s3.x, maxq),
+                   qy = quant(fmaf(halfL, d.y, p.y), l3.y, s3.y, maxq),
+                   qz = quant(fmaf(halfL, d.z, p.z), l3.z, s3.z, maxq);
+    const unsigned long long k = ikey | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     key[i] = k;
     val[i] = (uint32_t)i;
     for (int q = 0; q < passes; ++q) atomicAdd(&sh[q][(k >> (8 * q)) & 255u], 1u);
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < passes * 256; t += 256) {
-    const uint32_t v = (&sh[0][0])[t];
-    if (v) atomicAdd(&sort_hist[t], v);
+  if (passes > 0) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < passes * 256; t += 256) {
+      const uint32_t v = (&sh[0][0])[t];
+      if (v) atomicAdd(&hist[t], v);
+    }
   }
 }
 
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
                              const float box_scale[3], int bits, BuildBufs &w,
-                             const float4 *inst_box, cudaStream_t s) {
+                             const float4 *inst_box, int passes, cudaStream_t s) {
   if (b.n <= 0) return cudaSuccess;
   unsigned maxq = (1u << bits) - 1u;
-  int blocks = (int)((b.n + 255) / 256);
-  // one beam: quantise in the moment box of this step's centres (moments,
-  // box, then the keys); several instances: each instance's a-priori box
-  const bool one = inst_box == nullptr;
-  k_propagate<<<blocks, 256, 0, s>>>(b, ct, 0.5f * L, make_float3(box_lo[0], box_lo[1], box_lo[2]),
-                                     make_float3(box_scale[0], box_scale[1], box_scale[2]), maxq,
-                                     w.pos_u, w.dir_u, w.key[0], w.val[0], w.inst_of, inst_box,
-                                     3 * bits, one ? w.tpart : nullptr);
-  if (one) {
-    k_tbox<<<1, 1024, 0, s>>>(w.tpart, blocks, b.n, maxq, w.tbox, w.sort_hist, w.sort_tile);
-    const int mblocks = blocks < 4 * 152 ? blocks : 4 * 152;
-    k_morton<<<mblocks, 256, 0, s>>>(b.n, w.pos_u, w.dir_u, 0.5f * L, w.tbox, maxq,
-                                     (3 * bits + 7) / 8, w.key[0], w.val[0], w.sort_hist);
-  }
+  const int64_t nb = (b.n + 255) / 256;
+  const int blocks = (int)(nb < kPropBlocks ? nb : kPropBlocks);
+  k_propagate<<<blocks, 256, 0, s>>>(
+      b, ct, 0.5f * L, make_float3(box_lo[0], box_lo[1], box_lo[2]),
+      make_float3(box_scale[0], box_scale[1], box_scale[2]), maxq, w.pos_u, w.dir_u, w.key[0],
+      w.val[0], w.inst_of, inst_box, 3 * bits, passes, w.sort_raw);
   return cudaGetLastError();
 }
 
@@ -403,14 +305,14 @@ cudaError_t launch_gather(BuildBufs &w, int64_t n, int sel, cudaStream_t s) {
 
 // ---------------------------------------------------------------- Karras
 
-// common prefix length of sorted keys i and j; equal keys fall back to the
-// indices (so every key is distinct); -1 outside [0, n)
-__device__ __forceinline__ int kdelta(const unsigned long long *__restrict__ key, int64_t n,
-                                      int64_t i, int64_t j) {
-  if (j < 0 || j >= n) return -1;
-  unsigned long long a = key[i], b = key[j];
-  if (a != b) return __clzll((long long)(a ^ b));
-  return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+// common prefix length of sorted keys i and j (ki = key i); equal keys fall
+// back to the indices (so every key is distinct); -1 outside [0, n).  32-bit
+// indices: a beam holds fewer than 2^27 photons.
+__device__ __forceinline__ int kdelta(const unsigned long long *__restrict__ key, int n, int i,
+                                      unsigned long long ki, int j) {
+  if ((unsigned)j >= (unsigned)n) return -1;
+  const unsigned long long kj = __ldg(key + j);
+  return ki != kj ? __clzll((long long)(ki ^ kj)) : 64 + __clz(i ^ j);
 }
 
 __device__ __forceinline__ void empty_box(float4 &b1, float4 &b2) {
@@ -429,8 +331,8 @@ __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__rest
                                                 int64_t n, int bucket, TLNode *nodes,
                                                 uint32_t *parent_leaf, uint32_t *parent_node,
                                                 const unsigned *build_status, uint32_t *inst_root,
-                                                int inst_shift, uint32_t *nfirst, uint8_t *nlev,
-                                                int key_bits) {
+                                                int inst_shift, uint32_t *nfirst,
+                                                uint32_t *nlast, uint8_t *nlev, int key_bits) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (*build_status & TL_ST_TIMEOUT) return;  // keys unsorted: the build is abandoned
   const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
@@ -452,25 +354,29 @@ __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__rest
     if (multi && one_inst)
       inst_root[key[0] >> inst_shift] = root_bucket ? (TL_FLAG | (super << 1)) : 0u;
     nfirst[super] = 0u;
+    nlast[super] = (uint32_t)(n - 1);
     nlev[super] = 0;
   }
   if (i >= n - 1) return;
-  int dl = kdelta(key, n, i, i - 1), dr = kdelta(key, n, i, i + 1);
-  int64_t d = dr > dl ? 1 : -1;
-  int dmin = dr > dl ? dl : dr;
-  int64_t lmax = 2;
-  while (kdelta(key, n, i, i + lmax * d) > dmin) lmax <<= 1;
-  int64_t l = 0;
-  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-    if (kdelta(key, n, i, i + (l + t) * d) > dmin) l += t;
-  int64_t j = i + l * d;
-  int dnode = kdelta(key, n, i, j);
-  int64_t s = 0, t = l;
+  const int n32 = (int)n, i32 = (int)i;
+  const unsigned long long ki = __ldg(key + i32);
+  const int dl = kdelta(key, n32, i32, ki, i32 - 1), dr = kdelta(key, n32, i32, ki, i32 + 1);
+  const int d = dr > dl ? 1 : -1;
+  const int dmin = dr > dl ? dl : dr;
+  int lmax = 2;
+  while (kdelta(key, n32, i32, ki, i32 + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (kdelta(key, n32, i32, ki, i32 + (l + t) * d) > dmin) l += t;
+  const int j32 = i32 + l * d;
+  const int dnode = kdelta(key, n32, i32, ki, j32);
+  int s = 0, t = l;
   do {
     t = (t + 1) >> 1;
-    if (kdelta(key, n, i, i + (s + t) * d) > dnode) s += t;
+    if (kdelta(key, n32, i32, ki, i32 + (s + t) * d) > dnode) s += t;
   } while (t > 1);
-  int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+  const int64_t j = j32;
+  int64_t gamma = i32 + s * d + (d < 0 ? -1 : 0);
   int64_t first = i < j ? i : j, last = i < j ? j : i;
   int64_t cl = gamma - first + 1, cr = last - gamma;
   bool lone = true, rone = true;  // child inside one instance
@@ -486,6 +392,7 @@ __global__ void __launch_bounds__(256) k_karras(const unsigned long long *__rest
     }
   }
   nfirst[i] = (uint32_t)first;
+  nlast[i] = (uint32_t)last;
   {
     const int lev = dnode - (64 - key_bits);  // equal keys: beyond key_bits
     nlev[i] = (uint8_t)(lev < 0 ? 0 : (lev > 255 ? 255 : lev));
@@ -505,8 +412,8 @@ cudaError_t launch_karras(BuildBufs &w, int64_t n, int sel, int bucket, cudaStre
   k_karras<<<(int)((threads + 255) / 256), 256, 0, s>>>(w.key[sel], n, bucket, w.nodes,
                                                         w.parent_leaf, w.parent_node,
                                                         w.build_status, w.inst_root,
-                                                        w.inst_shift, w.nfirst, w.nlev,
-                                                        w.key_bits);
+                                                        w.inst_shift, w.nfirst, w.nlast,
+                                                        w.nlev, w.key_bits);
   return cudaGetLastError();
 }
 
@@ -529,16 +436,18 @@ __device__ __forceinline__ void seg_axis(float p, float dc, float Llo, float Lhi
   hi = __fadd_ru(fmaxf(phi, qhi), half);
 }
 
+// slot 0 = floats 0..5 of the record (b0, b1.xy), slot 1 = floats 6..11
+// (b1.zw, b2): one 16-byte and one 8-byte store each
 __device__ __forceinline__ void write_slot(TLNode *nodes, uint32_t node, uint32_t slot,
                                            const TLBox &b) {
-  float *f = reinterpret_cast<float *>(&nodes[node]);
-  float *o = f + (slot ? 6 : 0);
-  o[0] = b.lx;
-  o[1] = b.ly;
-  o[2] = b.lz;
-  o[3] = b.hx;
-  o[4] = b.hy;
-  o[5] = b.hz;
+  TLNode &r = nodes[node];
+  if (slot == 0u) {
+    r.b0 = make_float4(b.lx, b.ly, b.lz, b.hx);
+    *reinterpret_cast<float2 *>(&r.b1.x) = make_float2(b.hy, b.hz);
+  } else {
+    *reinterpret_cast<float2 *>(&r.b1.z) = make_float2(b.lx, b.ly);
+    r.b2 = make_float4(b.lz, b.hx, b.hy, b.hz);
+  }
 }
 
 // Refit as range unions.  Every subtree of the Karras hierarchy holds a
@@ -560,7 +469,7 @@ __device__ __forceinline__ void write_slot(TLNode *nodes, uint32_t node, uint32_
 // A node's range: f = first photon (written by the emit), l = f + both child
 // counts - 1.  A Karras node's index is one end of its range, so a node whose
 // range lies in a tile has its index there too.
-constexpr int kRTile = 256, kRTileLog = 8;
+constexpr int kRTile = 256, kRTileLev = 8;  // levels 0..7 cover ranges of up to 256
 constexpr int kRSuper = 512, kRSuperLog = 9;
 
 struct Box6 {
@@ -604,9 +513,12 @@ __device__ __forceinline__ Box6 tab_get(const float *tab, int j, int i) {
   return b;
 }
 
-template <int W>
+// union over [a, b]: two entries of level j = floor(log2(b - a + 1)), capped
+// at the table's top level LEV - 1 (two top-level entries still cover any
+// range of up to 2^LEV boxes)
+template <int W, int LEV>
 __device__ __forceinline__ Box6 tab_query(const float *tab, int a, int b) {
-  const int j = 31 - __clz(b - a + 1);
+  const int j = min(31 - __clz(b - a + 1), LEV - 1);
   Box6 r = tab_get<W>(tab, j, a);
   join6(r, tab_get<W>(tab, j, b - (1 << j) + 1));
   return r;
@@ -648,20 +560,14 @@ __device__ __forceinline__ Box6 get6(const float *src) {
   return r;
 }
 
-// photon range [f, l] of inner node x
-__device__ __forceinline__ void node_range(const TLNode *nodes, const uint32_t *nfirst, int64_t x,
-                                           int64_t &f, int64_t &l) {
-  const int2 cnt = *(reinterpret_cast<const int2 *>(&nodes[x].c) + 1);
-  f = nfirst[x];
-  l = f + (int64_t)cnt.x + cnt.y - 1;
-}
 
 __global__ void __launch_bounds__(kRTile) k_refit_tile(
     int64_t n, const float4 *__restrict__ pos, const float4 *__restrict__ dir, float Llo,
     float Lhi, float half, TLNode *nodes, const uint32_t *__restrict__ parent_leaf,
-    const uint32_t *__restrict__ parent_node, const uint32_t *__restrict__ nfirst, float *pre,
-    float *suf, float *tilebox, unsigned *build_status) {
-  extern __shared__ float tab[];  // (kRTileLog + 1) levels x 6 x kRTile
+    const uint32_t *__restrict__ parent_node, const uint32_t *__restrict__ nfirst,
+    const uint32_t *__restrict__ nlast, float *pre, float *suf, float *tilebox,
+    unsigned *build_status) {
+  extern __shared__ float tab[];  // kRTileLev levels x 6 x kRTile
   __shared__ unsigned abandoned;
   const int t = threadIdx.x;
   // one read for the whole block: other blocks of this kernel may set the flag
@@ -672,44 +578,54 @@ __global__ void __launch_bounds__(kRTile) k_refit_tile(
   const int64_t p = base + t;
   const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
   const int cnt = n - base < kRTile ? (int)(n - base) : kRTile;
+  // every global load first (they do not depend on the table)
+  float4 ps = make_float4(0.f, 0.f, 0.f, 0.f), d = ps;
+  uint32_t lref = 0u, nref = 0u;
+  int64_t f = 0, l = -1;
+  if (p < n) {
+    ps = pos[p];
+    d = dir[p];
+    lref = parent_leaf[p];
+  }
+  const bool inner = p < (int64_t)super;  // the super root (index n - 1) has no parent
+  if (inner) {
+    f = nfirst[p];
+    l = nlast[p];
+    nref = parent_node[p];
+  }
   Box6 b = empty6();
   if (p < n) {
-    const float4 ps = pos[p], d = dir[p];
     seg_axis(ps.x, d.x, Llo, Lhi, half, b.v[0], b.v[3]);
     seg_axis(ps.y, d.y, Llo, Lhi, half, b.v[1], b.v[4]);
     seg_axis(ps.z, d.z, Llo, Lhi, half, b.v[2], b.v[5]);
-    const uint32_t ref = parent_leaf[p];
-    if ((ref >> 1) <= super) write_slot(nodes, ref >> 1, ref & 1u, to_box(b));
+    if ((lref >> 1) <= super) write_slot(nodes, lref >> 1, lref & 1u, to_box(b));
     else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
   }
 #pragma unroll
   for (int q = 0; q < 6; ++q) tab[q * kRTile + t] = b.v[q];
   __syncthreads();
-  tab_build<kRTile, kRTileLog>(tab);
+  tab_build<kRTile, kRTileLev - 1>(tab);
   if (p < n) {
-    put6(pre + 6 * p, tab_query<kRTile>(tab, 0, t));
-    put6(suf + 6 * p, tab_query<kRTile>(tab, t, cnt - 1));
+    put6(pre + 6 * p, tab_query<kRTile, kRTileLev>(tab, 0, t));
+    put6(suf + 6 * p, tab_query<kRTile, kRTileLev>(tab, t, cnt - 1));
   }
-  if (t == 0) put6(tilebox + 6 * blockIdx.x, tab_query<kRTile>(tab, 0, cnt - 1));
-  // inner node p (the super root, index n - 1, has no parent)
-  if (p < (int64_t)super) {
-    int64_t f, l;
-    node_range(nodes, nfirst, p, f, l);
-    if (f >= base && l < base + cnt) {
-      const uint32_t ref = parent_node[p];
-      if ((ref >> 1) <= super && f <= l)
-        write_slot(nodes, ref >> 1, ref & 1u, to_box(tab_query<kRTile>(tab, (int)(f - base),
-                                                                       (int)(l - base))));
-      else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
-    }
+  if (t == 0) put6(tilebox + 6 * blockIdx.x, tab_query<kRTile, kRTileLev>(tab, 0, cnt - 1));
+  // inner node p, if its range lies in the tile
+  if (inner && f >= base && l < base + cnt) {
+    if ((nref >> 1) <= super && f <= l)
+      write_slot(nodes, nref >> 1, nref & 1u,
+                 to_box(tab_query<kRTile, kRTileLev>(tab, (int)(f - base), (int)(l - base))));
+    else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
   }
 }
 
 // tables over tile boxes: stab[((s * (kRSuperLog + 1) + j) * kRSuper + i) * 6 + q]
 __global__ void __launch_bounds__(kRSuper) k_refit_super(int64_t ntile, const float *tilebox,
                                                          float *stab,
-                                                         const unsigned *build_status) {
+                                                         const unsigned *build_status,
+                                                         unsigned *cut_n) {
   extern __shared__ float tab[];  // (kRSuperLog + 1) levels x 6 x kRSuper
+  if (blockIdx.x == 0 && threadIdx.x == 0 && cut_n) *cut_n = 0u;  // filled by k_refit_cross
   if (*build_status & TL_ST_TIMEOUT) return;
   const int64_t s = blockIdx.x, t0 = s * kRSuper;
   const int t = threadIdx.x;
@@ -742,22 +658,36 @@ __device__ __forceinline__ Box6 tiles_union(const float *stab, int64_t a, int64_
   return r;
 }
 
+// Also lists the traversal seeds: the children with at most cut_S photons of
+// nodes with more (such a node spans tiles, as cut_S >= kRTile).
 __global__ void __launch_bounds__(256) k_refit_cross(int64_t n, TLNode *nodes,
                                                      const uint32_t *__restrict__ parent_node,
                                                      const uint32_t *__restrict__ nfirst,
+                                                     const uint32_t *__restrict__ nlast,
                                                      const float *pre, const float *suf,
-                                                     const float *stab, unsigned *build_status) {
+                                                     const float *stab, unsigned *build_status,
+                                                     uint32_t cut_S, uint32_t *cut,
+                                                     unsigned *cut_n, uint32_t cut_cap) {
   if (*build_status & TL_ST_TIMEOUT) return;
   const uint32_t super = (uint32_t)(n > 1 ? n - 1 : 0);
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < (int64_t)super;
        x += (int64_t)gridDim.x * blockDim.x) {
-    int64_t f, l;
-    node_range(nodes, nfirst, x, f, l);
-    const int64_t t0 = f >> kRTileLog, t1 = l >> kRTileLog;
+    const int64_t f = nfirst[x], l = nlast[x];
+    const int64_t t0 = f >> 8, t1 = l >> 8;
     if (t0 == t1) continue;  // finished by its tile
     if (f < 0 || l >= n || f > l) {
       atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
       continue;
+    }
+    if (cut_S && l - f + 1 > (int64_t)cut_S) {
+      const int2 cnt = *(reinterpret_cast<const int2 *>(&nodes[x].c) + 1);  // child counts
+      for (uint32_t sl = 0; sl < 2; ++sl)
+        if ((uint32_t)(sl ? cnt.y : cnt.x) <= cut_S) {
+          // a count above cut_cap (long chains of small siblings) tells the
+          // traversal to start from the roots instead
+          const unsigned k = atomicAdd(cut_n, 1u);
+          if (k < cut_cap) cut[k] = ((uint32_t)x << 1) | sl;
+        }
     }
     Box6 b = get6(suf + 6 * f);
     join6(b, get6(pre + 6 * l));
@@ -776,7 +706,7 @@ size_t refit_super_floats(int64_t n) {
 
 cudaError_t refit_prepare() {
   cudaError_t e = cudaFuncSetAttribute(k_refit_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (kRTileLog + 1) * 6 * kRTile * (int)sizeof(float));
+                                       kRTileLev * 6 * kRTile * (int)sizeof(float));
   if (e) return e;
   return cudaFuncSetAttribute(k_refit_super, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (kRSuperLog + 1) * 6 * kRSuper * (int)sizeof(float));
@@ -786,16 +716,18 @@ cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float ha
                          cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t tiles = refit_tiles(n), supers = refit_supers(n);
-  k_refit_tile<<<(unsigned)tiles, kRTile, (kRTileLog + 1) * 6 * kRTile * sizeof(float), s>>>(
-      n, w.pos, w.dir, Llo, Lhi, half, w.nodes, w.parent_leaf, w.parent_node, w.nfirst, w.rpre,
-      w.rsuf, w.rtile, w.build_status);
+  k_refit_tile<<<(unsigned)tiles, kRTile, kRTileLev * 6 * kRTile * sizeof(float), s>>>(
+      n, w.pos, w.dir, Llo, Lhi, half, w.nodes, w.parent_leaf, w.parent_node, w.nfirst, w.nlast,
+      w.rpre, w.rsuf, w.rtile, w.build_status);
   if (tiles > 1) {
     k_refit_super<<<(unsigned)supers, kRSuper, (kRSuperLog + 1) * 6 * kRSuper * sizeof(float),
-                    s>>>(tiles, w.rtile, w.rsuper, w.build_status);
+                    s>>>(tiles, w.rtile, w.rsuper, w.build_status, w.cut_S ? w.cut_n : nullptr);
     const int64_t nb = (n + 255) / 256;
     const int blocks = (int)(nb < 8 * n_sm ? nb : 8 * n_sm);
-    k_refit_cross<<<blocks, 256, 0, s>>>(n, w.nodes, w.parent_node, w.nfirst, w.rpre, w.rsuf,
-                                         w.rsuper, w.build_status);
+    k_refit_cross<<<blocks, 256, 0, s>>>(n, w.nodes, w.parent_node, w.nfirst, w.nlast, w.rpre,
+                                         w.rsuf,
+                                         w.rsuper, w.build_status, w.cut_S, w.cut, w.cut_n,
+                                         w.cut_cap);
   }
   return cudaGetLastError();
 }

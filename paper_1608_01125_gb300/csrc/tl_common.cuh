@@ -138,9 +138,15 @@ struct BuildBufs {
   float *rpre, *rsuf;  // per photon: union of the swept boxes from its tile's start / to its end
   float *rtile;        // per refit tile: union of its photons' swept boxes
   float *rsuper;       // sparse tables over the tile boxes, one per super-tile
+  // traversal seeds: the children with at most cut_S photons of the nodes with
+  // more, as (node << 1) | slot, written by the refit (cut_S = 0: none)
+  uint32_t *cut;
+  unsigned *cut_n;
+  uint32_t cut_S, cut_cap, cut_alloc;
   // sort scratch
   uint32_t *sort_status;  // tiles * 256 per pass
-  uint32_t *sort_hist;    // 8 * 256 global digit counts
+  uint32_t *sort_raw;     // 8 * 256 digit counts of the keys (zero between sorts)
+  uint32_t *sort_hist;    // 8 * 256 digit offsets (exclusive scan of sort_raw)
   uint32_t *sort_tile;    // 8 tile counters
   int64_t sort_tiles;
   int sort_epoch;  // epoch of the last eager sort pass (0: status words must be cleared)
@@ -153,10 +159,9 @@ struct BuildBufs {
   // per inner node: first photon of its range and its level (Morton prefix
   // length in bits below the key's top bit), for the level-L cut
   uint32_t *nfirst;
+  uint32_t *nlast;   // last photon of every inner node's range (and the super root's)
   uint8_t *nlev;
   int key_bits;
-  float *tpart;  // per-block moments of the swept-box centres (6 floats per 256 photons)
-  float *tbox;   // this step's quantisation box: lo xyz, scale xyz
 };
 
 // Arguments of the traversal kernels (tl_traverse.cu).
@@ -181,11 +186,11 @@ struct TravArgs {
 
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
                              const float box_scale[3], int bits, BuildBufs &w,
-                             const float4 *inst_box, cudaStream_t s);
+                             const float4 *inst_box, int passes, cudaStream_t s);
+cudaError_t launch_beam_moments(const TLBeam &b, double *out15, double *scratch, cudaStream_t s);
 cudaError_t sort_prepare();
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
-                        int debug_stall, unsigned int *status, int *out_sel, bool hist_ready,
-                        cudaStream_t s);
+                        int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s);
 cudaError_t launch_gather(BuildBufs &w, int64_t n, int sel, cudaStream_t s);
 cudaError_t launch_karras(BuildBufs &w, int64_t n, int sel, int bucket, cudaStream_t s);
 cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float half, int n_sm,
@@ -193,5 +198,4 @@ cudaError_t launch_refit(BuildBufs &w, int64_t n, float Llo, float Lhi, float ha
 int64_t refit_tiles(int64_t n);
 size_t refit_super_floats(int64_t n);
 cudaError_t refit_prepare();
-cudaError_t launch_beam_bounds(const TLBeam &b, double *out12, cudaStream_t s);
 }  // namespace tl

@@ -24,7 +24,8 @@ struct trilens_ctx {
   float L_lo = 0, L_hi = 0, half = 0;
   TLNarrowConst nk{};
   int bits[2]{}, key_bits[2]{};
-  double bounds[2][12]{};
+  // per beam and axis: sums of p0, d, p0^2, p0 d, d^2 (one-time, fixed order)
+  double moments[2][15]{};
   // build workspace
   tl::BuildBufs w[2]{};
   int sel[2]{};
@@ -46,7 +47,6 @@ struct trilens_ctx {
   int yield_blocks = 0;
   unsigned *build_status = nullptr;  // device status of the builds (sort waits)
   unsigned *build_status_host = nullptr;
-  double *bounds_dev = nullptr;
   // results
   trilens_step_stats last{};
   double tot_count = 0, tot_weighted = 0;

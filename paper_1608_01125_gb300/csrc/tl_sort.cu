@@ -1,7 +1,8 @@
 // tl_sort.cu -- stable LSD radix sort of (64-bit key, 32-bit value) pairs.
 //
-// 8-bit digits.  One histogram pass counts every digit of every pass at once;
-// then one kernel per digit pass ranks a 2048-key tile in shared memory
+// 8-bit digits.  The key kernel counts every digit of every pass while it
+// writes the keys; one scan turns the counts into digit offsets; then one
+// kernel per digit pass ranks a 2048-key tile in shared memory
 // (warp match-any ranking keeps the order of equal digits), obtains the
 // tile's global offsets by decoupled look-back over the preceding tiles'
 // published digit counts (Merrill & Garland 2016, "Single-pass parallel
@@ -32,37 +33,15 @@ constexpr int kEpochShift = 27;
 constexpr uint32_t kEpochMask = 7u << kEpochShift;
 constexpr uint32_t kValMask = (1u << kEpochShift) - 1u;
 
-__global__ void __launch_bounds__(256) k_sort_hist(const unsigned long long *__restrict__ key,
-                                                   int64_t n, int passes, uint32_t *hist) {
-  __shared__ uint32_t sh[8][kRadix];
-  for (int i = threadIdx.x; i < 8 * kRadix; i += blockDim.x) (&sh[0][0])[i] = 0;
-  __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + 3 * stride < n; i += 4 * stride) {  // four independent loads in flight
-    unsigned long long k[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) k[u] = key[i + u * stride];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k[u] >> (8 * p)) & 255u], 1u);
-  }
-  for (; i < n; i += stride) {
-    unsigned long long k = key[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&sh[p][(k >> (8 * p)) & 255u], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
-    uint32_t v = (&sh[0][0])[i];
-    if (v) atomicAdd(&hist[i], v);
-  }
-}
-
-// exclusive scan of each pass's 256 digit counts, in place (one block of 256)
-__global__ void k_sort_scan(uint32_t *hist, int passes) {
+// exclusive scan of each pass's 256 digit counts (raw, counted by the key
+// kernel) into hist (one block of 256); then clears the raw counts and the
+// tile counters for the next sort
+__global__ void k_sort_scan(uint32_t *raw, uint32_t *hist, uint32_t *tile_ctr, int passes) {
   __shared__ uint32_t s[kRadix];
+  if (threadIdx.x < 8) tile_ctr[threadIdx.x] = 0u;
   for (int p = 0; p < passes; ++p) {
-    uint32_t v = hist[p * kRadix + threadIdx.x];
+    uint32_t v = raw[p * kRadix + threadIdx.x];
+    raw[p * kRadix + threadIdx.x] = 0u;
     s[threadIdx.x] = v;
     __syncthreads();
     for (int off = 1; off < kRadix; off <<= 1) {
@@ -86,7 +65,7 @@ struct SortSmem {
   uint32_t tile;
 };
 
-__global__ void __launch_bounds__(256) k_sort_pass(
+__global__ void __launch_bounds__(256, 4) k_sort_pass(
     const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
     unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
     const uint32_t *__restrict__ digit_base, uint32_t *status, uint32_t *tile_ctr,
@@ -216,12 +195,11 @@ cudaError_t sort_prepare() {
 }
 
 // Sort w.key[0]/w.val[0] by the low key_bits bits.  *out_sel receives the
-// buffer index holding the result.  hist_ready: the key producer has already
-// counted every pass's digits into a zeroed w.sort_hist and zeroed the tile
-// counters (the single-beam build does this while it writes the keys).
+// buffer index holding the result.  The key kernel has counted every pass's
+// digits into w.sort_raw (which the scan clears again, as it does the tile
+// counters; both are zero when allocated).
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
-                        int debug_stall, unsigned int *status, int *out_sel, bool hist_ready,
-                        cudaStream_t s) {
+                        int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s) {
   *out_sel = 0;
   if (n <= 1) return cudaSuccess;
   const int passes = (key_bits + 7) / 8;
@@ -230,14 +208,7 @@ cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_li
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((e = cudaStreamIsCapturing(s, &cap))) return e;
   const bool capturing = cap != cudaStreamCaptureStatusNone;
-  if (!hist_ready) {
-    if ((e = cudaMemsetAsync(w.sort_hist, 0, sizeof(uint32_t) * 8 * kRadix, s))) return e;
-    if ((e = cudaMemsetAsync(w.sort_tile, 0, sizeof(uint32_t) * 8, s))) return e;
-    int64_t nb = (n + 255) / 256;
-    int blocks = (int)(nb < 2 * 152 ? nb : 2 * 152);
-    k_sort_hist<<<blocks, 256, 0, s>>>(w.key[0], n, passes, w.sort_hist);
-  }
-  k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_hist, passes);
+  k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_raw, w.sort_hist, w.sort_tile, passes);
   int sel = 0;
   for (int p = 0; p < passes; ++p) {
     // a captured graph replays its arguments, so it clears the words before

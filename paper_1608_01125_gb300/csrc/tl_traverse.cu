@@ -131,6 +131,57 @@ __global__ void k_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *roo
 
 // ------------------------------------------------------------ frontier
 
+// Seeds from the two cut lists written by the refit: every pair (cut node of
+// A, cut node of B) whose boxes overlap (Eq. CollDet).  Every photon lies in
+// exactly one cut node of its beam and a box contains its descendants' boxes,
+// so every overlapping pair of leaf buckets lies below exactly one seed: the
+// traversal from the seeds reaches the same leaf pairs as from the roots.
+__global__ void __launch_bounds__(256) k_seed_cut(TravArgs a, const uint32_t *cutA,
+                                                  const unsigned *cntA, uint32_t capA,
+                                                  const uint32_t *cutB, const unsigned *cntB,
+                                                  uint32_t capB, uint2 *F0, unsigned cap) {
+  TLCounters *ctr = a.ctr;
+  if (ctr->status & TL_ST_TIMEOUT) return;  // the build failed: nothing to traverse
+  const unsigned na = *cntA, nb = *cntB;
+  if (na > capA || nb > capB) {  // a list overflowed: start from the root pair
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      F0[0] = make_uint2(a.A.super, a.B.super);
+      ctr->counts[0] = 1u;
+    }
+    return;
+  }
+  const unsigned long long total = (unsigned long long)na * nb;
+  const unsigned long long rounded = (total + 31ull) & ~31ull;
+  const int lane = threadIdx.x & 31;
+  unsigned long long tests = 0;
+  for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+       q < rounded; q += (unsigned long long)gridDim.x * blockDim.x) {
+    bool ok = false;
+    uint2 o = make_uint2(0u, 0u);
+    if (q < total) {
+      const uint32_t ea = cutA[q / nb], eb = cutB[q % nb];
+      const Side sa = side_of(a.A, ea >> 1, (int)(ea & 1u));
+      const Side sb = side_of(a.B, eb >> 1, (int)(eb & 1u));
+      ++tests;
+      ok = tl_overlap(sa.box, sb.box);
+      o = make_uint2(sa.sref, sb.sref);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (m) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(&ctr->counts[0], (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (ok) {
+        const unsigned idx = base + __popc(m & ((1u << lane) - 1u));
+        if (idx < cap) F0[idx] = o;
+        else atomicOr(&ctr->status, (unsigned)TL_ST_FRONT_OVF);
+      }
+    }
+  }
+  for (int off = 16; off; off >>= 1) tests += __shfl_xor_sync(0xffffffffu, tests, off);
+  if (lane == 0 && tests) atomicAdd(&ctr->node_tests, tests);
+}
+
 // One block expands the root pair breadth first, level by level, until the
 // frontier holds at least `target` pairs (or nothing is left to expand).
 // Bucket pairs pass through unchanged; failed overlap tests prune.
@@ -525,6 +576,13 @@ size_t traverse_smem(int warps, int depth) {
 cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t sb, int nonempty,
                              const unsigned *build_status, cudaStream_t s) {
   k_step_init<<<1, 128, 0, s>>>(ctr, F0, sa, sb, nonempty, build_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seed_cut(const TravArgs &a, const uint32_t *cutA, const unsigned *cntA,
+                            uint32_t capA, const uint32_t *cutB, const unsigned *cntB,
+                            uint32_t capB, uint2 *F0, unsigned cap, int blocks, cudaStream_t s) {
+  k_seed_cut<<<blocks, 256, 0, s>>>(a, cutA, cntA, capA, cutB, cntB, capB, F0, cap);
   return cudaGetLastError();
 }
 

@@ -129,6 +129,30 @@ def test_duplicate_photons():
     check_against_oracle(a, b, [0], 10.0, 1e16)
 
 
+def test_seed_lists_of_large_beams():
+    # beams of 2^17 photons or more start the traversal from the refit's seed
+    # lists (children with at most n/256 photons of nodes with more): ragged
+    # sizes, many refit tiles and super-tiles, a duplicated half
+    a, _ = synth.beams(synth.tiny_headon(n=140000, seed=11))
+    _, b = synth.beams(synth.tiny_headon(n=200001, seed=12))
+    check_against_oracle(a, b, [0, 1], 10.0, 3e13, method="tree")
+    for k in a:
+        a[k] = np.concatenate([a[k][:70000], np.repeat(a[k][:2188], 32)])
+    check_against_oracle(a, b, [0], 10.0, 3e13, method="tree")
+
+
+def test_seed_list_overflow_starts_from_roots():
+    a, _ = synth.beams(synth.tiny_headon(n=140000, seed=13))
+    _, b = synth.beams(synth.tiny_headon(n=140000, seed=14))
+    h, r = oracle.tree(a, b, 1, 10.0, 3e13, nthreads=os.cpu_count() or 1, cap=1 << 22)
+    for cap in (1, 0):  # 1: the lists overflow; 0: back to the allocated capacity
+        with binding.Collider(a, b, 10.0, 3e13) as col:
+            col.debug_set_cut_cap(cap)
+            got, st = col.step_hits(1)
+        assert np.array_equal(sorted_pairs(got), h.astype(np.int64)), cap
+        assert st["count"] == r["count"]
+
+
 @pytest.mark.parametrize("kw", [dict(leaf_bucket=1), dict(leaf_bucket=8), dict(leaf_bucket=32),
                                 dict(stack_depth=64), dict(block_shape=1),
                                 dict(block_shape=8, stack_depth=128)])
