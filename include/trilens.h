@@ -132,6 +132,21 @@ int trilens_step_stats_get(trilens_ctx *c, trilens_step_stats *out);
 int trilens_yield(trilens_ctx *c, int32_t mode, int32_t level_L, double *count,
                   double *weighted);
 
+/* Run time steps first_step .. first_step+steps-1 of a single (non-batch)
+ * context -- trilens_build + trilens_collide_step for each, in step order --
+ * as one captured CUDA graph on the context's stream, with no host round
+ * trip between steps (the traversal's passes run inside one cooperative
+ * launch per step, so no step needs the host).  The graph is captured on the
+ * first call and replayed while (first_step, steps) stay the same.  Adds the
+ * run's yield to the cumulative yield; out (host, may be NULL) receives the
+ * run's totals: step = steps, count, weighted, the checksums (hsum summed,
+ * hxor xored over the steps) and the work counters.  Hit lists are not
+ * returned.  On an internal overflow the buffer grows and the whole run is
+ * repeated (the result is that of a complete run).  Synchronises the stream
+ * at the end.  INVALID for a batch context, first_step < 0 or steps < 1;
+ * TIMEOUT if a device wait ran out. */
+int trilens_run(trilens_ctx *c, int64_t first_step, int64_t steps, trilens_step_stats *out);
+
 /* Zero the cumulative yield. */
 int trilens_reset_yield(trilens_ctx *c);
 

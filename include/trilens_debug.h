@@ -36,6 +36,12 @@ int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit);
  * INVALID for a NULL context. */
 int trilens_debug_set_cut_cap(trilens_ctx *c, int32_t cap);
 
+/* Replace the internal hit, band and hand-on buffers with buffers of cap
+ * pairs each (>= 1), so that the next collisions overflow them and exercise
+ * the regrow-and-repeat path.  Synchronises the stream.  INVALID for a NULL
+ * context or cap < 1. */
+int trilens_debug_shrink_buffers(trilens_ctx *c, int64_t cap);
+
 /* Evaluate the device FP64 functions of the exact decision element-wise:
  * which = 0: sigma(x) of Eq. BWcross [m^2] (0 for x <= 1); which = 1: the
  * natural log of x (x >= 1 finite; the only arguments the decision uses).

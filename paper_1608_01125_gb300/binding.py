@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
         L.trilens_yield.restype = ctypes.c_int
         L.trilens_reset_yield.argtypes = [vp]
         L.trilens_reset_yield.restype = ctypes.c_int
+        L.trilens_run.argtypes = [vp, i64, i64, ctypes.POINTER(StepStats)]
+        L.trilens_run.restype = ctypes.c_int
         L.trilens_destroy.argtypes = [vp]
         L.trilens_destroy.restype = None
         L.trilens_status_str.argtypes = [ctypes.c_int]
@@ -104,6 +106,8 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_set_spin_limit.restype = ctypes.c_int
         L.trilens_debug_set_cut_cap.argtypes = [vp, ctypes.c_int32]
         L.trilens_debug_set_cut_cap.restype = ctypes.c_int
+        L.trilens_debug_shrink_buffers.argtypes = [vp, i64]
+        L.trilens_debug_shrink_buffers.restype = ctypes.c_int
         L.trilens_debug_eval64.argtypes = [vp, vp, i64, i32, vp]
         L.trilens_debug_eval64.restype = ctypes.c_int
         L.trilens_debug_timing.argtypes = [vp, ctypes.c_int]
@@ -247,6 +251,14 @@ class Collider:
         h = buf[:n].cpu().numpy().view(np.uint32).astype(np.int64)
         return h, self.stats()
 
+    def run(self, first_step: int, steps: int) -> dict:
+        """Build and collide steps first_step .. first_step+steps-1 as one
+        captured graph (trilens_run); returns the run's totals."""
+        s = StepStats()
+        _check(lib().trilens_run(self.ctx, int(first_step), int(steps), ctypes.byref(s)),
+               self.ctx)
+        return s.as_dict()
+
     def stats(self) -> dict:
         s = StepStats()
         _check(lib().trilens_step_stats_get(self.ctx, ctypes.byref(s)), self.ctx)
@@ -346,6 +358,9 @@ class Collider:
 
     def debug_set_cut_cap(self, cap: int):
         _check(lib().trilens_debug_set_cut_cap(self.ctx, int(cap)), self.ctx)
+
+    def debug_shrink_buffers(self, cap: int = 64):
+        _check(lib().trilens_debug_shrink_buffers(self.ctx, int(cap)), self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

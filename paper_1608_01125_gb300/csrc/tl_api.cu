@@ -33,8 +33,8 @@ cudaError_t launch_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *ro
                                   const uint32_t *rootB, int n_inst, cudaStream_t s);
 cudaError_t launch_yield_inst(const TravArgs &a, const uint32_t *inst_of_a, double *yields,
                               int blocks, cudaStream_t s);
-cudaError_t launch_step_finish(const TLCounters *ctr, const unsigned long long *left,
-                               unsigned *run_status, cudaStream_t s);
+cudaError_t launch_step_finish(const TLCounters *ctr, unsigned *run_status, TLRunAcc *acc,
+                               cudaStream_t s);
 }  // namespace tl
 
 enum { PH_PROP = 0, PH_SORT, PH_GATHER, PH_EMIT, PH_REFIT, PH_EXPAND, PH_TRAV, PH_BAND, PH_YIELD };
@@ -191,6 +191,7 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFree(c->front[1]);
   cudaFree(c->spill[0]);
   cudaFree(c->spill[1]);
+  cudaFree(c->run_acc);
   cudaFree(c->hits);
   cudaFree(c->band);
   cudaFree(c->ctr);
@@ -207,7 +208,6 @@ void trilens_destroy(trilens_ctx *c) {
     for (int a = 0; a < 8; ++a) cudaFree(c->owned[k][a]);
   }
   cudaFree(c->inst_tmp);
-  cudaFree(c->spill_n);
   cudaFree(c->run_status);
   cudaFreeHost(c->run_status_host);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -416,12 +416,12 @@ tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   a.hit_cap = c->hit_cap;
   a.band = c->band;
   a.band_cap = c->band_cap;
-  a.spill = c->spill[0];
+  a.spill[0] = c->spill[0];
+  a.spill[1] = c->spill[1];
   a.spill_cap = c->spill_cap;
+  a.spin_limit = c->p.spin_limit;
   a.stack_depth = c->p.stack_depth;
   a.build_status = c->build_status;
-  a.spill_ctr = &c->ctr->spill;
-  a.in_count = nullptr;
   return a;
 }
 
@@ -460,30 +460,6 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
                              c->trav_warps, c->stream));
     tmark(c, PH_TRAV, 0, 1);
     c->phase_launches[PH_TRAV] += 1;
-    CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    int sp = 0, passes = 0;
-    while (h.spill > 0 && !(h.status & TL_ST_SPILL_OVF) && passes < 256) {
-      // descend the pairs that did not fit on a stack, writing new overflow
-      // to the other spill list
-      const unsigned long long nlist = h.spill;
-      tl::TravArgs a2 = a;
-      a2.spill = c->spill[sp ^ 1];
-      CK(cudaMemsetAsync(&c->ctr->spill, 0, sizeof(unsigned long long), c->stream));
-      CK(cudaMemsetAsync(&c->ctr->cursor, 0, sizeof(unsigned), c->stream));
-      tmark(c, PH_TRAV, 1, 0);
-      CK(tl::launch_traverse(a2, c->front[0], c->front[1], c->spill[sp], nlist, 0, c->budget,
-                             c->trav_blocks, c->trav_warps, c->stream));
-      tmark(c, PH_TRAV, 1, 1);
-      c->phase_launches[PH_TRAV] += 1;
-      CK(cudaMemcpyAsync(&h, c->ctr, sizeof(TLCounters), cudaMemcpyDeviceToHost, c->stream));
-      CK(cudaStreamSynchronize(c->stream));
-      tcollect(c);
-      sp ^= 1;
-      ++passes;
-    }
-    if (h.spill > 0 && !(h.status & TL_ST_SPILL_OVF))
-      return fail(c, TRILENS_ERR_STACK, "traversal still overflowing after %d passes", passes);
     if (!a.fp64) {
       tmark(c, PH_BAND, 0, 0);
       CK(tl::launch_band(a, c->n_sm * 4, c->stream));
@@ -527,6 +503,8 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
       again = true;
     }
     if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
+    if (st & TL_ST_PASSES)
+      return fail(c, TRILENS_ERR_STACK, "traversal work left after %d passes", TL_MAX_PASSES);
     if (!again) break;
     if (++retries > 8) return fail(c, TRILENS_ERR_STACK, "buffers kept overflowing");
   }
@@ -576,6 +554,8 @@ int trilens_collide_step(trilens_ctx *c, int64_t step, uint32_t *hits, int64_t c
 }
 
 // ---- batches of independent instances ------------------------------------
+
+static int ensure_graph(trilens_ctx *c);
 
 static int batch_prepare(trilens_ctx *c, const trilens_beam *const src[2], int32_t n_inst) {
   // concatenate each side's instances into library-owned arrays
@@ -683,10 +663,7 @@ int trilens_batch_create(trilens_ctx **out, const trilens_beam *a, const trilens
       CK(dalloc(&c->front[k], c->front_cap));
     }
   }
-  CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  CK(dalloc(&c->spill_n, 2));
-  CK(dalloc(&c->run_status, 1));
-  CK(cudaMallocHost((void **)&c->run_status_host, sizeof(unsigned)));
+  if ((rc = ensure_graph(c))) return rc;
   CK(cudaStreamSynchronize(c->stream));
   *out = c;
   return TRILENS_OK;
@@ -699,30 +676,27 @@ static int graph_collide(trilens_ctx *c, int64_t step, double *yields) {
   const double ct = TL_C * ((double)step * c->p.dt_fs);
   const int nonempty = c->beam[0].n > 0 && c->beam[1].n > 0;
   tl::TravArgs a = trav_args(c, ct);
+  const bool use_cut = c->n_inst <= 1 && c->w[0].cut_S && c->w[1].cut_S;
   CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super,
-                          c->n_inst > 1 ? 0 : nonempty, c->build_status, c->stream));
-  if (c->n_inst > 1)
-    CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
-                                 c->n_inst, c->stream));
-  CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
-                       c->stream));
-  const int P = c->graph_passes;
-  for (int pass = 0; pass < P; ++pass) {
-    const int out = pass & 1, in = out ^ 1;
-    CK(cudaMemsetAsync(&c->spill_n[out], 0, sizeof(unsigned long long), c->stream));
-    CK(cudaMemsetAsync(&c->ctr->cursor, 0, sizeof(unsigned), c->stream));
-    tl::TravArgs ap = a;
-    ap.spill = c->spill[out];
-    ap.spill_ctr = &c->spill_n[out];
-    ap.in_count = pass ? &c->spill_n[in] : nullptr;
-    CK(tl::launch_traverse(ap, c->front[0], c->front[1], pass ? c->spill[in] : nullptr, 0,
-                           pass ? 0 : 1, c->budget, c->trav_blocks, c->trav_warps, c->stream));
+                          (c->n_inst > 1 || use_cut) ? 0 : nonempty, c->build_status, c->stream));
+  if (use_cut) {
+    CK(tl::launch_seed_cut(a, c->w[0].cut, c->w[0].cut_n, c->w[0].cut_cap, c->w[1].cut,
+                           c->w[1].cut_n, c->w[1].cut_cap, c->front[0], c->front_cap,
+                           2 * c->n_sm, c->stream));
+  } else {
+    if (c->n_inst > 1)
+      CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
+                                   c->n_inst, c->stream));
+    CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
+                         c->stream));
   }
+  CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->budget, c->trav_blocks,
+                         c->trav_warps, c->stream));
   if (!a.fp64) CK(tl::launch_band(a, c->n_sm * 4, c->stream));
   CK(tl::launch_yield(a, c->partials, c->yield_blocks, c->stream));
   if (yields && c->n_inst > 1)
     CK(tl::launch_yield_inst(a, c->inst_of[0], yields, c->yield_blocks, c->stream));
-  CK(tl::launch_step_finish(c->ctr, &c->spill_n[(P - 1) & 1], c->run_status, c->stream));
+  CK(tl::launch_step_finish(c->ctr, c->run_status, c->run_acc, c->stream));
   return TRILENS_OK;
 }
 
@@ -738,6 +712,8 @@ static int capture_run(trilens_ctx *c, int64_t first, int64_t steps, double *yie
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   int rc = TRILENS_OK;
   cudaError_t e = cudaMemsetAsync(c->run_status, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess && c->run_acc)
+    e = cudaMemsetAsync(c->run_acc, 0, sizeof(TLRunAcc), c->stream);
   if (e == cudaSuccess && yields && c->n_inst > 1)
     e = cudaMemsetAsync(yields, 0, sizeof(double) * 2 * c->n_inst, c->stream);
   if (e != cudaSuccess) rc = fail(c, TRILENS_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
@@ -763,11 +739,9 @@ static int capture_run(trilens_ctx *c, int64_t first, int64_t steps, double *yie
   return TRILENS_OK;
 }
 
-int trilens_batch_run(trilens_ctx *c, int64_t first_step, int64_t steps, double *yields) {
-  if (!c) return TRILENS_ERR_INVALID;
-  if (first_step < 0 || steps < 1 || !c->cap_stream)
-    return fail(c, TRILENS_ERR_INVALID, "batch_run needs a batch context, first_step >= 0, steps >= 1");
-  CK(cudaSetDevice(c->device));
+// Capture (if needed) and replay a multi-step run; on an overflow grow the
+// buffer and run again.
+static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double *yields) {
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (!c->gexec || c->g_first != first_step || c->g_steps != steps || c->g_yields != yields) {
       int rc = capture_run(c, first_step, steps, yields);
@@ -788,25 +762,75 @@ int trilens_batch_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
     }
     if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF | TL_ST_PASSES)))
       return TRILENS_OK;
-    // grow what overflowed and capture again
+    // grow what overflowed (to the largest size a step asked for) and capture again
+    TLRunAcc m;
+    CK(cudaMemcpyAsync(&m, c->run_acc, sizeof(TLRunAcc), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     int rc;
-    if (st & TL_ST_HIT_OVF && (rc = grow(c, &c->hits, &c->hit_cap, 2 * c->hit_cap))) return rc;
-    if (st & TL_ST_BAND_OVF && (rc = grow(c, &c->band, &c->band_cap, 2 * c->band_cap))) return rc;
+    if (st & TL_ST_HIT_OVF && (rc = grow(c, &c->hits, &c->hit_cap, m.max_hits + m.max_band)))
+      return rc;
+    if (st & TL_ST_BAND_OVF && (rc = grow(c, &c->band, &c->band_cap, m.max_band))) return rc;
     if (st & TL_ST_SPILL_OVF) {
       unsigned long long cap = c->spill_cap;
-      if ((rc = grow(c, &c->spill[0], &cap, 2 * c->spill_cap))) return rc;
+      if ((rc = grow(c, &c->spill[0], &cap, m.max_handed))) return rc;
       cudaFree(c->spill[1]);
       CK(dalloc(&c->spill[1], cap));
       c->spill_cap = cap;
     }
-    if (st & TL_ST_PASSES) c->graph_passes *= 2;
+    if (st & TL_ST_PASSES)
+      return fail(c, TRILENS_ERR_STACK, "traversal work left after %d passes", TL_MAX_PASSES);
     if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
       c->gexec = nullptr;
     }
   }
-  return fail(c, TRILENS_ERR_STACK, "batch run kept overflowing");
+  return fail(c, TRILENS_ERR_STACK, "captured run kept overflowing");
+}
+
+// graph resources of a context (a batch context makes them when created)
+static int ensure_graph(trilens_ctx *c) {
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (!c->run_status) CK(dalloc(&c->run_status, 1));
+  if (!c->run_status_host) CK(cudaMallocHost((void **)&c->run_status_host, sizeof(unsigned)));
+  if (!c->run_acc) CK(dalloc(&c->run_acc, 1));
+  return TRILENS_OK;
+}
+
+int trilens_batch_run(trilens_ctx *c, int64_t first_step, int64_t steps, double *yields) {
+  if (!c) return TRILENS_ERR_INVALID;
+  if (first_step < 0 || steps < 1 || c->n_inst < 2 || !c->cap_stream)
+    return fail(c, TRILENS_ERR_INVALID, "batch_run needs a batch context, first_step >= 0, steps >= 1");
+  CK(cudaSetDevice(c->device));
+  return replay_run(c, first_step, steps, yields);
+}
+
+int trilens_run(trilens_ctx *c, int64_t first_step, int64_t steps, trilens_step_stats *out) {
+  if (!c) return TRILENS_ERR_INVALID;
+  if (first_step < 0 || steps < 1 || c->n_inst > 1)
+    return fail(c, TRILENS_ERR_INVALID, "run needs a single context, first_step >= 0, steps >= 1");
+  CK(cudaSetDevice(c->device));
+  int rc = ensure_graph(c);
+  if (rc) return rc;
+  if ((rc = replay_run(c, first_step, steps, nullptr))) return rc;
+  TLRunAcc h;
+  CK(cudaMemcpyAsync(&h, c->run_acc, sizeof(TLRunAcc), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->tot_count += (double)h.count;
+  c->tot_weighted += h.weighted;
+  if (out) {
+    out->step = steps;
+    out->count = (int64_t)h.count;
+    out->weighted = h.weighted;
+    out->hsum = h.hsum;
+    out->hxor = h.hxor;
+    out->narrow_tests = (int64_t)h.narrow_tests;
+    out->node_tests = (int64_t)h.node_tests;
+    out->leaf_pairs = (int64_t)h.leaf_pairs;
+    out->band = (int64_t)h.band;
+    out->retries = 0;
+  }
+  return TRILENS_OK;
 }
 
 int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const trilens_params *p,
@@ -988,7 +1012,7 @@ int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
   // coordinate descent over the four knobs, each swept with the others
   // fixed at the best so far; results never depend on them, only time does
   int best[4] = {c->p.leaf_bucket, c->p.stack_depth, c->p.block_shape, c->budget};
-  static const int cand[4][5] = {{2, 4, 8, 16, 0}, {128, 256, 512, 0, 0}, {2, 4, 8, 0, 0},
+  static const int cand[4][5] = {{1, 2, 4, 8, 16}, {128, 256, 512, 0, 0}, {2, 4, 8, 0, 0},
                                  {16, 64, 256, 0, 0}};
   double best_ms = 1e30;
   int rc = apply_tuning(c, best[0], best[1], best[2], best[3]);
@@ -1079,6 +1103,28 @@ int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int r
 int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit) {
   if (!c || limit < 1) return TRILENS_ERR_INVALID;
   c->p.spin_limit = limit;
+  return TRILENS_OK;
+}
+
+int trilens_debug_shrink_buffers(trilens_ctx *c, int64_t cap) {
+  if (!c || cap < 1) return TRILENS_ERR_INVALID;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->gexec) {  // a captured run holds the old buffers
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  const unsigned long long n = (unsigned long long)cap;
+  cudaFree(c->hits);
+  cudaFree(c->band);
+  cudaFree(c->spill[0]);
+  cudaFree(c->spill[1]);
+  c->hits = c->band = c->spill[0] = c->spill[1] = nullptr;
+  c->hit_cap = c->band_cap = c->spill_cap = n;
+  CK(dalloc(&c->hits, n));
+  CK(dalloc(&c->band, n));
+  CK(dalloc(&c->spill[0], n));
+  CK(dalloc(&c->spill[1], n));
   return TRILENS_OK;
 }
 

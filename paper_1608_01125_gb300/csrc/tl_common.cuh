@@ -56,14 +56,16 @@ enum {
   TL_ST_FRONT_OVF = 8,
   TL_ST_TIMEOUT = 16,
   TL_ST_LEAFQ = 32,
-  TL_ST_PASSES = 64  // graph mode: traversal work left after the fixed passes
+  TL_ST_PASSES = 64  // traversal work left after TL_MAX_PASSES passes
 };
 
 // Per-step device counters; zeroed by the step's init kernel.
+#define TL_MAX_PASSES 64
+
 struct TLCounters {
   unsigned long long hits;         // colliding pairs found (may exceed capacity)
   unsigned long long band;         // FP32 band pairs queued for FP64
-  unsigned long long spill;        // stack overflow pairs written to the spill list
+  unsigned long long spill;        // largest list of pairs handed from one pass to the next
   unsigned long long narrow_tests; // photon pairs tested
   unsigned long long node_tests;   // box pair tests
   unsigned long long leaf_pairs;   // overlapping bucket pairs
@@ -73,7 +75,11 @@ struct TLCounters {
   unsigned int cursor;             // traversal work cursor
   unsigned int status;             // TL_ST_* bits
   unsigned int reduce_done;        // blocks finished in the yield reduction
-  unsigned int pad[3];
+  unsigned int passes;             // traversal passes run
+  unsigned int bar_arrive;         // grid barrier between traversal passes: arrivals
+  unsigned int bar_gen;            //   and the last pass every block has finished
+  unsigned long long handed[2];    // pairs handed on by even / odd passes
+  unsigned int pass_cursor[TL_MAX_PASSES];  // work cursor of each pass
   // results of the yield reduction for this step
   unsigned long long count;
   double weighted;
@@ -81,11 +87,14 @@ struct TLCounters {
 };
 
 // Cumulative totals across steps.
-struct TLTotals {
-  double count;
+// Totals of a captured multi-step run (accumulated on the device, step by
+// step, in step order).
+struct TLRunAcc {
+  unsigned long long count;
   double weighted;
-  unsigned long long steps;
-  unsigned long long pad;
+  unsigned long long hsum, hxor;
+  unsigned long long narrow_tests, node_tests, leaf_pairs, band;
+  unsigned long long max_hits, max_band, max_handed;  // largest per-step list sizes
 };
 
 // FP64 input beam on the device.
@@ -176,12 +185,11 @@ struct TravArgs {
   unsigned long long hit_cap;
   uint2 *band;
   unsigned long long band_cap;
-  uint2 *spill;
+  uint2 *spill[2];    // pairs handed on by even / odd traversal passes
   unsigned long long spill_cap;
   int stack_depth;
   const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal
-  unsigned long long *spill_ctr;        // where pairs handed to the next pass are counted
-  const unsigned long long *in_count;   // device count of the input list (NULL: argument)
+  long long spin_limit;          // iteration limit of the wait between passes
 };
 
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],

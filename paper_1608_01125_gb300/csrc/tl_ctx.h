@@ -64,10 +64,9 @@ struct trilens_ctx {
   cudaGraphExec_t gexec = nullptr;
   int64_t g_first = -1, g_steps = 0;
   double *g_yields = nullptr;
-  unsigned long long *spill_n = nullptr;  // device, counts of the two spill lists
+  TLRunAcc *run_acc = nullptr;       // device totals of a captured single-context run
   unsigned *run_status = nullptr;
   unsigned *run_status_host = nullptr;
-  int graph_passes = 12;
   // per-phase timing (events on the context's stream) and launch counts
   int timing = 0;
   cudaEvent_t ev[9][2][2]{};   // [phase][beam or 0][start, end]

@@ -54,8 +54,10 @@ __device__ __forceinline__ int tl_narrow32(const float4 pa, const float4 da, con
   const float SA = (fabsf(pa.x) + fabsf(pb.x)) + (fabsf(pa.y) + fabsf(pb.y)) +
                    (fabsf(pa.z) + fabsf(pb.z));
   const float nq = sqrtf(d2);
-  const float nd = sqrtf(dd);
-  const float rnd = 1.0f / nd;
+  // over-estimates of 1/|dD| and |dD| for the bounds: rsqrtf is within 2 ulp
+  // (4u relative) of 1/sqrt(dd), so 1 + 8u covers it and the product's rounding
+  const float rnd = rsqrtf(dd) * (1.0f + 8.0f * u);
+  const float nd = dd * rnd;
   const float at = fabsf(tau);
   const float dq =
       2.0f * (2.0f * u * SA + 4.0f * u * (nq * rnd + at) + 7.1f * u * at * nd + 4.1f * u * nq);

@@ -162,6 +162,21 @@ def test_tuning_never_changes_results(kw):
     check_against_oracle(a, b, [0], wl.dt, wl.kappa, **kw)
 
 
+@pytest.mark.parametrize("budget", [2, 5, 0])
+def test_handing_work_to_later_passes_never_changes_results(budget):
+    # a small budget hands most items on to later passes of the same launch
+    # (a grid barrier between passes); 0 never hands on
+    wl = synth.tiny_headon(n=6000, seed=15)
+    a, b = synth.beams(wl)
+    h, r = oracle.bruteforce(a, b, 0, wl.dt, wl.kappa, cap=1 << 20)
+    for prec in (binding.FP64, binding.FP32_BAND):
+        with binding.Collider(a, b, wl.dt, wl.kappa, precision=prec) as col:
+            col.set_tuning(2, 64, 2, budget)
+            got, st = col.step_hits(0)
+        assert np.array_equal(sorted_pairs(got), h.astype(np.int64)), (prec, budget)
+        assert st["count"] == r["count"] and st["hsum"] == r["hsum"]
+
+
 def _adversarial_beams(dt, kappa, seed=0):
     """Pairs placed on the decision boundaries of the definition: impact
     parameter r(1 +- 2^-k), closest approach at t* = 0 and dt(1 +- 2^-k) and
