@@ -53,6 +53,14 @@ __device__ __forceinline__ int tl_narrow32(const float4 pa, const float4 da, con
 
   const float SA = (fabsf(pa.x) + fabsf(pb.x)) + (fabsf(pa.y) + fabsf(pb.y)) +
                    (fabsf(pa.z) + fabsf(pb.z));
+  // Quick miss, before the bounds: if |dD|^2 >= 2^-30, |tau| <= 2^10,
+  // |q|^2 >= 2^-12 and SA <= 2^18 |q|, every term of dq below is a small
+  // fraction of |q| (2u SA <= |q|/32, 4u |q|/|dD| <= |q|/128, 4u |tau| <=
+  // |q|/64, 7.1u |tau||dD| <= |q|/18), so dq <= 0.23 |q| and ed2 <= 0.5 d2:
+  // d2 >= 2.5 r2max then puts the FP64 distance beyond every radius.
+  if (dd >= 0x1p-30f && fabsf(tau) <= 1024.0f && d2 >= fmaxf(2.5f * k.r2max, 0x1p-12f) &&
+      SA * SA <= 0x1p36f * d2)
+    return TL_MISS;
   const float nq = sqrtf(d2);
   // over-estimates of 1/|dD| and |dD| for the bounds: rsqrtf is within 2 ulp
   // (4u relative) of 1/sqrt(dd), so 1 + 8u covers it and the product's rounding
