@@ -242,9 +242,12 @@ def run_ours(args, wl):
             band += st["band"]
         return hits, tests, band
 
+    work = {}
+
     def graph_run():
         # the same steps as one captured CUDA graph (trilens_run)
         r = col.run(first, nsteps)
+        work.update(node_tests=r["node_tests"], leaf_pairs=r["leaf_pairs"])
         return r["count"], r["narrow_tests"], r["band"]
 
     tuned = col.autotune([2, 4, 40], os.path.join(ROOT, "paper_1608_01125_gb300",
@@ -349,6 +352,7 @@ def run_ours(args, wl):
         "collided_pairs_per_s": world * hits / (ms / 1e3),
         "narrow_tests_per_s": world * tests / (ms / 1e3),
         "hits_per_run": hits / K, "narrow_tests_per_run": tests / K, "band_per_run": band / K,
+        "node_tests_per_run": work.get("node_tests"), "leaf_pairs_per_run": work.get("leaf_pairs"),
         "path": "trilens_run: all steps of a run as one captured CUDA graph",
         "phase_ms_per_run": {p: phase_ms[p] / K for p in PHASES},
         "phase_source": "the same runs built and collided step by step with CUDA events "

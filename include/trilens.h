@@ -135,8 +135,8 @@ int trilens_yield(trilens_ctx *c, int32_t mode, int32_t level_L, double *count,
 /* Run time steps first_step .. first_step+steps-1 of a single (non-batch)
  * context -- trilens_build + trilens_collide_step for each, in step order --
  * as one captured CUDA graph on the context's stream, with no host round
- * trip between steps (the traversal's passes run inside one cooperative
- * launch per step, so no step needs the host).  The graph is captured on the
+ * trip between steps (each step's traversal is one launch whose warps share
+ * a device work queue, so no step needs the host).  The graph is captured on the
  * first call and replayed while (first_step, steps) stay the same.  Adds the
  * run's yield to the cumulative yield; out (host, may be NULL) receives the
  * run's totals: step = steps, count, weighted, the checksums (hsum summed,

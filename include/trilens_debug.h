@@ -28,6 +28,14 @@ int trilens_debug_stall_sort(trilens_ctx *c, int on);
  * >= 1).  INVALID for a NULL context or limit < 1. */
 int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit);
 
+/* Morton resolution of a single context's keys: bits per axis (4..21; the
+ * default is a few bits beyond one cell per photon).  The hit set never
+ * depends on it (the hierarchy only prunes); tests use it to check that, and
+ * to time the sort (ceil(3 bits / 8) digit passes) against tree quality.
+ * The next collisions need a fresh build.  INVALID for a NULL or batch
+ * context or bits outside 4..21. */
+int trilens_debug_set_key_bits(trilens_ctx *c, int32_t bits);
+
 /* Capacity of the traversal-seed lists the refit writes (children with at
  * most n/64 photons of nodes with more; normally a few hundred).  cap
  * below the list's length makes the next collisions start from the root pair

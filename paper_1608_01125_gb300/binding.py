@@ -108,6 +108,8 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_set_cut_cap.restype = ctypes.c_int
         L.trilens_debug_shrink_buffers.argtypes = [vp, i64]
         L.trilens_debug_shrink_buffers.restype = ctypes.c_int
+        L.trilens_debug_set_key_bits.argtypes = [vp, ctypes.c_int32]
+        L.trilens_debug_set_key_bits.restype = ctypes.c_int
         L.trilens_debug_eval64.argtypes = [vp, vp, i64, i32, vp]
         L.trilens_debug_eval64.restype = ctypes.c_int
         L.trilens_debug_timing.argtypes = [vp, ctypes.c_int]
@@ -358,6 +360,9 @@ class Collider:
 
     def debug_set_cut_cap(self, cap: int):
         _check(lib().trilens_debug_set_cut_cap(self.ctx, int(cap)), self.ctx)
+
+    def debug_set_key_bits(self, bits: int):
+        _check(lib().trilens_debug_set_key_bits(self.ctx, int(bits)), self.ctx)
 
     def debug_shrink_buffers(self, cap: int = 64):
         _check(lib().trilens_debug_shrink_buffers(self.ctx, int(cap)), self.ctx)

@@ -189,8 +189,7 @@ void trilens_destroy(trilens_ctx *c) {
   free_beam(c->w[1]);
   cudaFree(c->front[0]);
   cudaFree(c->front[1]);
-  cudaFree(c->spill[0]);
-  cudaFree(c->spill[1]);
+  cudaFree(c->queue);
   cudaFree(c->run_acc);
   cudaFree(c->hits);
   cudaFree(c->band);
@@ -281,8 +280,10 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
     int64_t n = std::max<int64_t>(c->beam[k].n, 2);
     int lg = 0;
     while ((1ll << lg) < n) ++lg;
-    // Morton resolution: a few bits per axis beyond one cell per photon
-    c->bits[k] = std::min(21, std::max(4, (lg + 2) / 3 + 3));
+    // Morton resolution: one bit per axis beyond one cell per photon (at 2 x 1M
+    // head-on: 24-bit keys, 3 sort passes; 27 or 30 bits traverse as fast but
+    // take 4 passes; 21 bits slow the traversal by a third)
+    c->bits[k] = std::min(21, std::max(4, (lg + 2) / 3 + 1));
     c->key_bits[k] = 3 * c->bits[k];
     c->w[k].key_bits = c->key_bits[k];
     // one-time moments of p0 and d for the Morton box of every step
@@ -314,10 +315,15 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   c->front_cap = std::max(4 * c->front_target + 64, c->w[0].cut_cap * c->w[1].cut_cap + 64);
   CK(dalloc(&c->front[0], c->front_cap));
   CK(dalloc(&c->front[1], c->front_cap));
-  c->spill_cap = std::max<unsigned long long>(1 << 20, 2ull * c->trav_blocks * c->trav_warps *
-                                                          (unsigned long long)c->p.stack_depth);
-  CK(dalloc(&c->spill[0], c->spill_cap));
-  CK(dalloc(&c->spill[1], c->spill_cap));
+  {
+    const int rcq = alloc_queue(c, std::max<unsigned long long>(
+                                       1 << 20, 2ull * c->trav_blocks * c->trav_warps *
+                                                    (unsigned long long)c->p.stack_depth));
+    if (rcq) {
+      trilens_destroy(c);
+      return rcq;
+    }
+  }
   c->hit_cap = std::max<unsigned long long>(1 << 16, 2ull * (c->beam[0].n + c->beam[1].n));
   CK(dalloc(&c->hits, c->hit_cap));
   c->band_cap = std::max<unsigned long long>(1 << 16, (c->beam[0].n + c->beam[1].n) / 4);
@@ -416,9 +422,8 @@ tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   a.hit_cap = c->hit_cap;
   a.band = c->band;
   a.band_cap = c->band_cap;
-  a.spill[0] = c->spill[0];
-  a.spill[1] = c->spill[1];
-  a.spill_cap = c->spill_cap;
+  a.queue = reinterpret_cast<unsigned long long *>(c->queue);
+  a.queue_cap = c->queue_cap;
   a.spin_limit = c->p.spin_limit;
   a.stack_depth = c->p.stack_depth;
   a.build_status = c->build_status;
@@ -478,6 +483,8 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
     const unsigned st = h.status | *c->build_status_host;
     if (st & TL_ST_TIMEOUT) {
       c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
+      // a traversal cut short may leave items in the queue
+      CK(cudaMemsetAsync(c->queue, 0xff, sizeof(uint2) * (size_t)c->queue_cap, c->stream));
       CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
       CK(cudaStreamSynchronize(c->stream));
       return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit=%lld",
@@ -493,18 +500,12 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
       if ((rc = grow(c, &c->hits, &c->hit_cap, h.hits + (again ? h.band : 0)))) return rc;
       again = true;
     }
-    if (st & TL_ST_SPILL_OVF) {
-      cudaFree(c->spill[1]);
-      c->spill[1] = nullptr;
-      unsigned long long cap = c->spill_cap;
-      if ((rc = grow(c, &c->spill[0], &cap, std::max(h.spill, c->spill_cap * 2)))) return rc;
-      CK(dalloc(&c->spill[1], cap));
-      c->spill_cap = cap;
+    if (st & TL_ST_SPILL_OVF) {  // the queue: larger, and every slot the sentinel again
+      const unsigned long long need = h.q_tail + h.q_tail / 4 + 1024;
+      if ((rc = alloc_queue(c, std::max(need, 2 * c->queue_cap)))) return rc;
       again = true;
     }
     if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
-    if (st & TL_ST_PASSES)
-      return fail(c, TRILENS_ERR_STACK, "traversal work left after %d passes", TL_MAX_PASSES);
     if (!again) break;
     if (++retries > 8) return fail(c, TRILENS_ERR_STACK, "buffers kept overflowing");
   }
@@ -756,11 +757,13 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
     const unsigned st = *c->run_status_host | *c->build_status_host;
     if (st & TL_ST_TIMEOUT) {
       c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
+      // a traversal cut short may leave items in the queue
+      CK(cudaMemsetAsync(c->queue, 0xff, sizeof(uint2) * (size_t)c->queue_cap, c->stream));
       CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
       CK(cudaStreamSynchronize(c->stream));
       return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit");
     }
-    if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF | TL_ST_PASSES)))
+    if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF)))
       return TRILENS_OK;
     // grow what overflowed (to the largest size a step asked for) and capture again
     TLRunAcc m;
@@ -770,15 +773,10 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
     if (st & TL_ST_HIT_OVF && (rc = grow(c, &c->hits, &c->hit_cap, m.max_hits + m.max_band)))
       return rc;
     if (st & TL_ST_BAND_OVF && (rc = grow(c, &c->band, &c->band_cap, m.max_band))) return rc;
-    if (st & TL_ST_SPILL_OVF) {
-      unsigned long long cap = c->spill_cap;
-      if ((rc = grow(c, &c->spill[0], &cap, m.max_handed))) return rc;
-      cudaFree(c->spill[1]);
-      CK(dalloc(&c->spill[1], cap));
-      c->spill_cap = cap;
+    if (st & TL_ST_SPILL_OVF) {  // the queue: larger, and every slot the sentinel again
+      const unsigned long long need = m.max_handed + m.max_handed / 4 + 1024;
+      if ((rc = alloc_queue(c, std::max(need, 2 * c->queue_cap)))) return rc;
     }
-    if (st & TL_ST_PASSES)
-      return fail(c, TRILENS_ERR_STACK, "traversal work left after %d passes", TL_MAX_PASSES);
     if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
     if (c->gexec) {
       cudaGraphExecDestroy(c->gexec);
@@ -870,15 +868,11 @@ static int apply_tuning(trilens_ctx *c, int bucket, int depth, int warps, int bu
       CK(dalloc(&c->front[k], c->front_cap));
     }
   }
-  const unsigned long long need_spill =
+  const unsigned long long need_queue =
       2ull * c->trav_blocks * c->trav_warps * (unsigned long long)depth;
-  if (need_spill > c->spill_cap) {
-    for (int k = 0; k < 2; ++k) {
-      cudaFree(c->spill[k]);
-      c->spill[k] = nullptr;
-      CK(dalloc(&c->spill[k], need_spill));
-    }
-    c->spill_cap = need_spill;
+  if (need_queue > c->queue_cap) {
+    const int rcq = alloc_queue(c, need_queue);
+    if (rcq) return rcq;
   }
   if (c->gexec) {  // a captured run holds the old shapes
     cudaGraphExecDestroy(c->gexec);
@@ -1117,14 +1111,28 @@ int trilens_debug_shrink_buffers(trilens_ctx *c, int64_t cap) {
   const unsigned long long n = (unsigned long long)cap;
   cudaFree(c->hits);
   cudaFree(c->band);
-  cudaFree(c->spill[0]);
-  cudaFree(c->spill[1]);
-  c->hits = c->band = c->spill[0] = c->spill[1] = nullptr;
-  c->hit_cap = c->band_cap = c->spill_cap = n;
+  c->hits = c->band = nullptr;
+  c->hit_cap = c->band_cap = n;
   CK(dalloc(&c->hits, n));
   CK(dalloc(&c->band, n));
-  CK(dalloc(&c->spill[0], n));
-  CK(dalloc(&c->spill[1], n));
+  const int rc = alloc_queue(c, n);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return TRILENS_OK;
+}
+
+int trilens_debug_set_key_bits(trilens_ctx *c, int32_t bits) {
+  if (!c || c->n_inst > 1 || bits < 4 || bits > 21) return TRILENS_ERR_INVALID;
+  for (int k = 0; k < 2; ++k) {
+    c->bits[k] = bits;
+    c->key_bits[k] = 3 * bits;
+    c->w[k].key_bits = c->key_bits[k];
+  }
+  if (c->gexec) {  // a captured run holds the old pass count
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  c->built_step = -1;
   return TRILENS_OK;
 }
 

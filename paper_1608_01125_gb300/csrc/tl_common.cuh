@@ -52,20 +52,17 @@ __device__ __forceinline__ bool tl_overlap(const TLBox &a, const TLBox &b) {
 enum {
   TL_ST_HIT_OVF = 1,
   TL_ST_BAND_OVF = 2,
-  TL_ST_SPILL_OVF = 4,
+  TL_ST_SPILL_OVF = 4,  // the traversal queue overflowed (or a slot was not free)
   TL_ST_FRONT_OVF = 8,
   TL_ST_TIMEOUT = 16,
-  TL_ST_LEAFQ = 32,
-  TL_ST_PASSES = 64  // traversal work left after TL_MAX_PASSES passes
+  TL_ST_LEAFQ = 32
 };
 
 // Per-step device counters; zeroed by the step's init kernel.
-#define TL_MAX_PASSES 64
-
 struct TLCounters {
   unsigned long long hits;         // colliding pairs found (may exceed capacity)
   unsigned long long band;         // FP32 band pairs queued for FP64
-  unsigned long long spill;        // largest list of pairs handed from one pass to the next
+  unsigned long long q_tail;       // traversal queue: slots reserved (items handed on)
   unsigned long long narrow_tests; // photon pairs tested
   unsigned long long node_tests;   // box pair tests
   unsigned long long leaf_pairs;   // overlapping bucket pairs
@@ -75,18 +72,15 @@ struct TLCounters {
   unsigned int cursor;             // traversal work cursor
   unsigned int status;             // TL_ST_* bits
   unsigned int reduce_done;        // blocks finished in the yield reduction
-  unsigned int passes;             // traversal passes run
-  unsigned int bar_arrive;         // grid barrier between traversal passes: arrivals
-  unsigned int bar_gen;            //   and the last pass every block has finished
-  unsigned long long handed[2];    // pairs handed on by even / odd passes
-  unsigned int pass_cursor[TL_MAX_PASSES];  // work cursor of each pass
+  unsigned int pad0;
+  unsigned long long q_head;       // traversal items taken (the frontier's, then the queue's)
+  unsigned long long q_done;       // traversal items finished
   // results of the yield reduction for this step
   unsigned long long count;
   double weighted;
   unsigned long long hsum, hxor;
 };
 
-// Cumulative totals across steps.
 // Totals of a captured multi-step run (accumulated on the device, step by
 // step, in step order).
 struct TLRunAcc {
@@ -94,7 +88,7 @@ struct TLRunAcc {
   double weighted;
   unsigned long long hsum, hxor;
   unsigned long long narrow_tests, node_tests, leaf_pairs, band;
-  unsigned long long max_hits, max_band, max_handed;  // largest per-step list sizes
+  unsigned long long max_hits, max_band, max_handed;  // largest per-step list and queue sizes
 };
 
 // FP64 input beam on the device.
@@ -185,8 +179,8 @@ struct TravArgs {
   unsigned long long hit_cap;
   uint2 *band;
   unsigned long long band_cap;
-  uint2 *spill[2];    // pairs handed on by even / odd traversal passes
-  unsigned long long spill_cap;
+  unsigned long long *queue;  // traversal work queue: (ref A, ref B) pairs, sentinel when free
+  unsigned long long queue_cap;
   int stack_depth;
   const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal
   long long spin_limit;          // iteration limit of the wait between passes

@@ -35,8 +35,8 @@ struct trilens_ctx {
   int budget = 64;  // traversal iterations per work item before it is split
   unsigned front_target = 0, front_cap = 0;
   uint2 *front[2]{};
-  uint2 *spill[2]{};
-  unsigned long long spill_cap = 0;
+  uint2 *queue = nullptr;  // traversal work queue (every free slot holds the sentinel)
+  unsigned long long queue_cap = 0;
   uint2 *hits = nullptr;
   unsigned long long hit_cap = 0;
   uint2 *band = nullptr;
@@ -103,6 +103,17 @@ static inline cudaError_t dalloc(T **p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+// (re)allocate the traversal queue with cap slots, every slot the sentinel
+static inline int alloc_queue(trilens_ctx *c, unsigned long long cap) {
+  cudaFree(c->queue);
+  c->queue = nullptr;
+  c->queue_cap = 0;
+  CK(dalloc(&c->queue, (size_t)cap));
+  CK(cudaMemsetAsync(c->queue, 0xff, sizeof(uint2) * (size_t)cap, c->stream));
+  c->queue_cap = cap;
+  return TRILENS_OK;
 }
 
 static inline int grow(trilens_ctx *c, uint2 **buf, unsigned long long *cap, unsigned long long need) {

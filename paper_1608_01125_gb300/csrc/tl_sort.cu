@@ -32,6 +32,7 @@ constexpr uint32_t kFlagMask = 3u << 30;
 constexpr int kEpochShift = 27;
 constexpr uint32_t kEpochMask = 7u << kEpochShift;
 constexpr uint32_t kValMask = (1u << kEpochShift) - 1u;
+constexpr int kLookback = 8;  // preceding tiles' words read per look-back round trip
 
 // exclusive scan of each pass's 256 digit counts (raw, counted by the key
 // kernel) into hist (one block of 256); then clears the raw counts and the
@@ -123,18 +124,18 @@ __global__ void __launch_bounds__(256, 4) k_sort_pass(
       if (!debug_stall) atomicExch(my, kPre | ep | cnt);
     } else {
       atomicExch(my, kAgg | ep | cnt);
-      // walk back over the preceding tiles four at a time (independent loads),
+      // walk back over the preceding tiles kLookback at a time (independent loads),
       // adding published aggregates until an inclusive prefix is found
       int64_t j = (int64_t)tile - 1;
       long long spins = 0;
       bool done = false;
       while (j >= 0 && !done) {
-        uint32_t sv[4];
+        uint32_t sv[kLookback];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < kLookback; ++q)
           sv[q] = j - q >= 0 ? *(volatile uint32_t *)(status + (j - q) * kRadix + d) : (kPre | ep);
         int used = 0;
-        for (int q = 0; q < 4 && !done; ++q) {
+        for (int q = 0; q < kLookback && !done; ++q) {
           const uint32_t flag = sv[q] & kFlagMask;
           // not published in this pass yet: reload from here
           if (flag == 0u || (sv[q] & kEpochMask) != ep) break;

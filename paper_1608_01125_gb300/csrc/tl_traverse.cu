@@ -320,62 +320,21 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
 
 // ------------------------------------------------------------ traversal
 
-// Grid barrier between traversal passes (the launch is cooperative, so every
-// block is resident and the wait ends).  The last block to arrive decides for
-// everyone whether another pass follows (something was handed on, no list
-// overflowed, fewer than TL_MAX_PASSES passes), clears the counter the next
-// pass writes, and releases the others with the decision in the top bit of
-// the release word (which the next release cannot overwrite before every
-// block has read it: it needs every block's next arrival).  Returns true when
-// another pass follows.  Every wait is bounded by spin_limit; on expiry the
-// block records TL_ST_TIMEOUT and stops.
-__device__ __forceinline__ bool pass_barrier(TLCounters *ctr, int pass, long long spin_limit) {
-  __shared__ int more;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();  // this block's lists and counters, before the arrival
-    const unsigned target = gridDim.x * (unsigned)(pass + 1);
-    const unsigned gen = (unsigned)(pass + 1);
-    if (atomicAdd(&ctr->bar_arrive, 1u) == target - 1u) {
-      __threadfence();
-      const unsigned long long left = *(volatile unsigned long long *)&ctr->handed[pass & 1];
-      const unsigned st = *(volatile unsigned *)&ctr->status;
-      int go = left != 0ull && !(st & (TL_ST_SPILL_OVF | TL_ST_TIMEOUT));
-      if (go && pass + 1 >= TL_MAX_PASSES) {
-        atomicOr(&ctr->status, (unsigned)TL_ST_PASSES);
-        go = 0;
-      }
-      if (left > ctr->spill) ctr->spill = left;
-      if (!go) ctr->passes = gen;
-      ctr->handed[(pass + 1) & 1] = 0ull;  // the next pass's output (read two passes ago)
-      __threadfence();
-      atomicExch(&ctr->bar_gen, gen | (go ? 0u : 0x80000000u));
-      more = go;
-    } else {
-      long long spins = 0;
-      unsigned ns = 32;
-      unsigned g;
-      while (((g = *(volatile unsigned *)&ctr->bar_gen) & 0x7fffffffu) < gen) {
-        if (++spins > spin_limit) {
-          atomicOr(&ctr->status, (unsigned)TL_ST_TIMEOUT);
-          break;
-        }
-        __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
-      }
-      more = ((g & 0x7fffffffu) >= gen) && !(g & 0x80000000u);
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return more != 0;
+// Persistent warps share one work queue.  The frontier's items come first
+// (indices below n0), then the queue's slots: a warp that spends `budget`
+// iterations on one item hands the rest of it (its whole stack) to the queue,
+// where idle warps take the pieces at once; a warp whose stack is full hands
+// on the pair that does not fit.  Free queue slots hold a sentinel: a taker
+// swaps the sentinel back in as it reads (atomic exchange), and waits while
+// its slot is still free and work is in flight.  The traversal ends when the
+// items finished equal n0 plus the items handed on.  Every wait is bounded by
+// spin_limit (then TL_ST_TIMEOUT).
+constexpr unsigned long long kQFree = 0xffffffffffffffffull;
+
+__device__ __forceinline__ unsigned long long pack2(uint2 v) {
+  return (unsigned long long)v.x | ((unsigned long long)v.y << 32);
 }
 
-// Persistent warps, all passes in one cooperative launch.  Pass 0 takes the
-// frontier (or a given list); a warp that spends `budget` iterations on one
-// item hands the rest of it (its whole stack) to the list of the next pass,
-// where its pieces spread over all warps.  After each pass the grid meets at
-// a barrier; the traversal ends when a pass hands nothing on.
 template <bool FP64>
 __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, const uint2 *F1,
                                                   const uint2 *list, unsigned long long list_n,
@@ -388,106 +347,144 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
       smem_raw + sizeof(uint2) * (size_t)D * (blockDim.x >> 5))[warp];
   TLCounters *ctr = a.ctr;
   const uint2 *src0;
-  unsigned long long nsrc0;
+  unsigned long long n0;
   if (from_frontier) {
     const unsigned lvl = ctr->final_level;
     src0 = (lvl & 1u) ? F1 : F0;
-    nsrc0 = ctr->counts[lvl];
+    n0 = ctr->counts[lvl];
   } else {
     src0 = list;
-    nsrc0 = list_n;
+    n0 = list_n;
   }
+  unsigned long long *Q = a.queue;
+  const unsigned long long qcap = a.queue_cap;
   const unsigned lt = (1u << lane) - 1u;
-  int nq = 0;
+  int sp = 0, nq = 0, iters = 0;
+  bool holding = false;  // this warp holds an item (counted in flight)
+  bool handed = false;   // ... and has handed pieces of it on
   unsigned long long node_tests = 0, narrow_tests = 0, leaf_pairs = 0;
-  for (int pass = 0;; ++pass) {
-    const uint2 *src = src0;
-    unsigned long long nsrc = nsrc0;
-    if (pass > 0) {
-      src = a.spill[(pass - 1) & 1];
-      nsrc = *(volatile unsigned long long *)&ctr->handed[(pass - 1) & 1];
-      if (nsrc > a.spill_cap) nsrc = a.spill_cap;  // overflowed: flagged by its producer
-    }
-    uint2 *out = a.spill[pass & 1];
-    unsigned long long *out_n = &ctr->handed[pass & 1];
-    unsigned *cursor = &ctr->pass_cursor[pass];
-    int sp = 0, iters = 0;
-    while (true) {
-      if (sp > 0 && budget > 0 && iters >= budget) {
-        // this item is large: hand the rest of it (the whole stack) to the next pass
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(out_n, (unsigned long long)sp);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        for (int e = lane; e < sp; e += 32) {
-          if (base + e < a.spill_cap) out[base + e] = stack[e];
-          else atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
-        }
-        __syncwarp();
-        sp = 0;
-      }
-      if (sp == 0) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(cursor, 1u);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= nsrc) break;
-        // L2 load: the list may have been written by other SMs in this launch
-        if (lane == 0) stack[0] = __ldcg(src + base);
-        __syncwarp();
-        sp = 1;
-        iters = 0;
-      }
-      ++iters;
-      const int npop = min(sp, 8);
-      sp -= npop;
-      const int p = lane >> 2, combo = lane & 3;
-      const bool active = p < npop;
-      const uint2 pr = active ? stack[sp + p] : make_uint2(0u, 0u);
-      __syncwarp();
-      bool ok = false, leafleaf = false, tested = false;
-      uint2 o = make_uint2(0u, 0u);
-      if (active) {
-        if ((pr.x & TL_FLAG) && (pr.y & TL_FLAG)) {
-          if (combo == 0) {  // a bucket pair taken from the frontier
-            const Side sa = side_of(a.A, pr.x, 0), sb = side_of(a.B, pr.y, 0);
-            ok = leafleaf = true;
-            o = make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt));
-          }
+  while (true) {
+    if (sp > 0 && budget > 0 && iters >= budget) {
+      // this item is large: hand the rest of it (the whole stack) to the queue;
+      // the handed pieces are counted before this item is counted finished
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(&ctr->q_tail, (unsigned long long)sp);
+      handed = true;
+      base = __shfl_sync(0xffffffffu, base, 0);
+      for (int e = lane; e < sp; e += 32) {
+        if (base + e < qcap) {
+          if (atomicExch(Q + base + e, pack2(stack[e])) != kQFree)
+            atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);  // a slot was not free
         } else {
-          Side sa, sb;
-          if (child_pair(a.A, a.B, pr, combo, sa, sb)) {
-            tested = true;
-            ok = tl_overlap(sa.box, sb.box);
-            leafleaf = sa.bucket && sb.bucket;
-            o = leafleaf ? make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt))
-                         : make_uint2(sa.sref, sb.sref);
+          atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+        }
+      }
+      __syncwarp();
+      sp = 0;
+    }
+    if (sp == 0) {
+      int got = 0;
+      uint2 item = make_uint2(0u, 0u);
+      if (lane == 0) {
+        if (holding) {
+          if (handed) __threadfence();  // this item's hand-ons (q_tail) before its finish
+          atomicAdd(&ctr->q_done, 1ull);
+          holding = false;
+        }
+        handed = false;
+        const unsigned long long i = atomicAdd(&ctr->q_head, 1ull);
+        if (i < n0) {
+          item = __ldcg(src0 + i);
+          got = 1;
+        } else if (i - n0 < qcap) {
+          unsigned long long *slot = Q + (i - n0);
+          long long spins = 0;
+          unsigned ns = 32;
+          while (true) {
+            const unsigned long long v = atomicExch(slot, kQFree);
+            if (v != kQFree) {
+              item = make_uint2((unsigned)v, (unsigned)(v >> 32));
+              got = 1;
+              break;
+            }
+            // finished items first, then hand-ons: equal means nothing was in
+            // flight at the first read, so nothing more can come
+            const unsigned long long done = *(volatile unsigned long long *)&ctr->q_done;
+            __threadfence();
+            const unsigned long long tail = *(volatile unsigned long long *)&ctr->q_tail;
+            if (done >= n0 + tail) break;
+            if (*(volatile unsigned *)&ctr->status & (TL_ST_SPILL_OVF | TL_ST_TIMEOUT)) break;
+            if (++spins > a.spin_limit) {
+              atomicOr(&ctr->status, (unsigned)TL_ST_TIMEOUT);
+              break;
+            }
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
           }
         }
+        // an index past the queue's end: its producer flagged the overflow
       }
-      const unsigned mtest = __ballot_sync(0xffffffffu, tested);
-      if (lane == 0) node_tests += (unsigned long long)__popc(mtest);
-      const unsigned mpush = __ballot_sync(0xffffffffu, ok && !leafleaf);
-      const unsigned mleaf = __ballot_sync(0xffffffffu, ok && leafleaf);
-      if (ok && !leafleaf) {
-        const int slot = sp + __popc(mpush & lt);
-        if (slot < D) {
-          stack[slot] = o;
-        } else {  // the stack is full: this pair goes to the next pass
-          const unsigned long long idx = atomicAdd(out_n, 1ull);
-          if (idx < a.spill_cap) out[idx] = o;
-          else atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+      got = __shfl_sync(0xffffffffu, got, 0);
+      if (!got) break;
+      if (lane == 0) {
+        stack[0] = item;
+        holding = true;
+      }
+      __syncwarp();
+      sp = 1;
+      iters = 0;
+    }
+    ++iters;
+    const int npop = min(sp, 8);
+    sp -= npop;
+    const int p = lane >> 2, combo = lane & 3;
+    const bool active = p < npop;
+    const uint2 pr = active ? stack[sp + p] : make_uint2(0u, 0u);
+    __syncwarp();
+    bool ok = false, leafleaf = false, tested = false;
+    uint2 o = make_uint2(0u, 0u);
+    if (active) {
+      if ((pr.x & TL_FLAG) && (pr.y & TL_FLAG)) {
+        if (combo == 0) {  // a bucket pair taken from the frontier
+          const Side sa = side_of(a.A, pr.x, 0), sb = side_of(a.B, pr.y, 0);
+          ok = leafleaf = true;
+          o = make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt));
+        }
+      } else {
+        Side sa, sb;
+        if (child_pair(a.A, a.B, pr, combo, sa, sb)) {
+          tested = true;
+          ok = tl_overlap(sa.box, sb.box);
+          leafleaf = sa.bucket && sb.bucket;
+          o = leafleaf ? make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt))
+                       : make_uint2(sa.sref, sb.sref);
         }
       }
-      sp = min(sp + __popc(mpush), D);
-      if (ok && leafleaf) ws.leafq[nq + __popc(mleaf & lt)] = o;
-      nq += __popc(mleaf);
-      __syncwarp();
-      if (nq >= 32) {
-        leaf_pairs += nq;
-        flush_leaves<FP64>(a, ws, nq, lane, narrow_tests);
-        nq = 0;
+    }
+    const unsigned mtest = __ballot_sync(0xffffffffu, tested);
+    if (lane == 0) node_tests += (unsigned long long)__popc(mtest);
+    const unsigned mpush = __ballot_sync(0xffffffffu, ok && !leafleaf);
+    const unsigned mleaf = __ballot_sync(0xffffffffu, ok && leafleaf);
+    if (sp + __popc(mpush) > D) handed = true;  // (warp-uniform)
+    if (ok && !leafleaf) {
+      const int slot = sp + __popc(mpush & lt);
+      if (slot < D) {
+        stack[slot] = o;
+      } else {  // the stack is full: this pair goes to the queue
+        const unsigned long long idx = atomicAdd(&ctr->q_tail, 1ull);
+        if (idx >= qcap || atomicExch(Q + idx, pack2(o)) != kQFree)
+          atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
       }
     }
-    if (!pass_barrier(ctr, pass, a.spin_limit)) break;
+    sp = min(sp + __popc(mpush), D);
+    if (ok && leafleaf) ws.leafq[nq + __popc(mleaf & lt)] = o;
+    nq += __popc(mleaf);
+    __syncwarp();
+    if (nq >= 32) {
+      leaf_pairs += nq;
+      flush_leaves<FP64>(a, ws, nq, lane, narrow_tests);
+      nq = 0;
+    }
   }
   if (nq) {
     leaf_pairs += nq;
@@ -638,7 +635,7 @@ __global__ void k_step_finish(const TLCounters *ctr, unsigned *run_status, TLRun
     acc->band += ctr->band;
     if (ctr->hits > acc->max_hits) acc->max_hits = ctr->hits;
     if (ctr->band > acc->max_band) acc->max_band = ctr->band;
-    if (ctr->spill > acc->max_handed) acc->max_handed = ctr->spill;
+    if (ctr->q_tail > acc->max_handed) acc->max_handed = ctr->q_tail;
   }
 }
 
@@ -687,23 +684,16 @@ cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm) 
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
                             unsigned long long list_n, int from_frontier, int budget, int blocks,
                             int warps, cudaStream_t s) {
-  // cooperative: every block resident at once (blocks is the occupancy limit),
-  // so the blocks may wait for one another between passes
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)blocks);
-  cfg.blockDim = dim3((unsigned)(warps * 32));
-  cfg.dynamicSmemBytes = traverse_smem(warps, a.stack_depth);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  // a warp only waits for work that warps holding items (running ones) hand
+  // on, so no block needs another to be resident
+  const size_t smem = traverse_smem(warps, a.stack_depth);
   if (a.fp64)
-    return cudaLaunchKernelEx(&cfg, k_traverse<true>, a, F0, F1, list, list_n, from_frontier,
-                              budget);
-  return cudaLaunchKernelEx(&cfg, k_traverse<false>, a, F0, F1, list, list_n, from_frontier,
-                            budget);
+    k_traverse<true><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier,
+                                                       budget);
+  else
+    k_traverse<false><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier,
+                                                        budget);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_band(const TravArgs &a, int blocks, cudaStream_t s) {

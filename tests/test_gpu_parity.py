@@ -163,9 +163,9 @@ def test_tuning_never_changes_results(kw):
 
 
 @pytest.mark.parametrize("budget", [2, 5, 0])
-def test_handing_work_to_later_passes_never_changes_results(budget):
-    # a small budget hands most items on to later passes of the same launch
-    # (a grid barrier between passes); 0 never hands on
+def test_handing_work_on_never_changes_results(budget):
+    # a small budget hands most items on through the traversal's work queue,
+    # where other warps take them up; 0 never hands on
     wl = synth.tiny_headon(n=6000, seed=15)
     a, b = synth.beams(wl)
     h, r = oracle.bruteforce(a, b, 0, wl.dt, wl.kappa, cap=1 << 20)
@@ -175,6 +175,19 @@ def test_handing_work_to_later_passes_never_changes_results(budget):
             got, st = col.step_hits(0)
         assert np.array_equal(sorted_pairs(got), h.astype(np.int64)), (prec, budget)
         assert st["count"] == r["count"] and st["hsum"] == r["hsum"]
+
+
+@pytest.mark.parametrize("bits", [4, 7, 13, 21])
+def test_morton_resolution_never_changes_results(bits):
+    # coarse keys (many equal keys, ordered by index) to 63-bit keys (8 sort passes)
+    wl = synth.tiny_headon(n=6000, seed=16)
+    a, b = synth.beams(wl)
+    h, r = oracle.bruteforce(a, b, 0, wl.dt, wl.kappa, cap=1 << 20)
+    with binding.Collider(a, b, wl.dt, wl.kappa) as col:
+        col.debug_set_key_bits(bits)
+        got, st = col.step_hits(0)
+    assert np.array_equal(sorted_pairs(got), h.astype(np.int64)), bits
+    assert st["count"] == r["count"] and st["hsum"] == r["hsum"]
 
 
 def _adversarial_beams(dt, kappa, seed=0):
