@@ -109,6 +109,7 @@ static void free_beam(tl::BuildBufs &w) {
   cudaFree(w.nlast);
   cudaFree(w.nlev);
   cudaFree(w.sort_status);
+  cudaFree(w.sort_ep);
   cudaFree(w.sort_raw);
   cudaFree(w.sort_hist);
   cudaFree(w.sort_tile);
@@ -146,6 +147,7 @@ static int alloc_beam(trilens_ctx *c, tl::BuildBufs &w, int64_t n) {
   w.sort_tiles = (int64_t)((m + TL_SORT_TILE - 1) / TL_SORT_TILE);
   w.sort_epoch = 0;
   CK(dalloc(&w.sort_status, (size_t)w.sort_tiles * 256));
+  CK(dalloc(&w.sort_ep, 9));
   CK(dalloc(&w.sort_raw, 8 * 256));
   CK(cudaMemsetAsync(w.sort_raw, 0, sizeof(uint32_t) * 8 * 256, c->stream));
   CK(dalloc(&w.sort_hist, 8 * 256));
@@ -378,9 +380,12 @@ int trilens_build(trilens_ctx *c, int64_t step) {
     CK(tl::launch_sort(w, n, c->key_bits[k], c->p.spin_limit, c->debug_stall_sort,
                        c->build_status, &c->sel[k], c->stream));
     tmark(c, PH_SORT, k, 1);
-    tmark(c, PH_GATHER, k, 0);
-    CK(tl::launch_gather(w, n, c->sel[k], c->stream));
-    tmark(c, PH_GATHER, k, 1);
+    if (n <= 1) {  // no sort: copy the one photon (a longer beam is gathered by the sort)
+      tmark(c, PH_GATHER, k, 0);
+      CK(tl::launch_gather(w, n, c->sel[k], c->stream));
+      tmark(c, PH_GATHER, k, 1);
+      c->phase_launches[PH_GATHER] += 1;
+    }
     tmark(c, PH_EMIT, k, 0);
     CK(tl::launch_karras(w, n, c->sel[k], c->p.leaf_bucket, c->stream));
     tmark(c, PH_EMIT, k, 1);
@@ -389,7 +394,6 @@ int trilens_build(trilens_ctx *c, int64_t step) {
     tmark(c, PH_REFIT, k, 1);
     c->phase_launches[PH_PROP] += 1;
     c->phase_launches[PH_SORT] += n > 1 ? 1 + (c->key_bits[k] + 7) / 8 : 0;
-    c->phase_launches[PH_GATHER] += 1;
     c->phase_launches[PH_EMIT] += 1;
     c->phase_launches[PH_REFIT] += tl::refit_tiles(n) > 1 ? 3 : 1;
   }

@@ -152,7 +152,8 @@ struct BuildBufs {
   uint32_t *sort_hist;    // 8 * 256 digit offsets (exclusive scan of sort_raw)
   uint32_t *sort_tile;    // 8 tile counters
   int64_t sort_tiles;
-  int sort_epoch;  // epoch of the last eager sort pass (0: status words must be cleared)
+  int sort_epoch;  // 0: the status words must be cleared before the next sort
+  uint32_t *sort_ep;  // device: epochs of the passes of the current sort, and the last one
 
   unsigned *build_status;  // shared status word of the context's builds
   // several independent instances in one beam (NULL / 0 for a single one)

@@ -17,7 +17,8 @@
 // 3-bit pass epoch and a 27-bit count (beams hold fewer than 2^27 photons).
 // Every pass rewrites every tile's 256 words, so a word left by the previous
 // pass carries the previous epoch and reads as "not published": the array
-// needs no clearing between passes.
+// needs no clearing between passes.  The epochs live on the device (the scan
+// picks them), so a captured graph's replays cycle them too.
 #include "tl_common.cuh"
 
 namespace tl {
@@ -36,10 +37,21 @@ constexpr int kLookback = 8;  // preceding tiles' words read per look-back round
 
 // exclusive scan of each pass's 256 digit counts (raw, counted by the key
 // kernel) into hist (one block of 256); then clears the raw counts and the
-// tile counters for the next sort
-__global__ void k_sort_scan(uint32_t *raw, uint32_t *hist, uint32_t *tile_ctr, int passes) {
+// tile counters for the next sort.  Also picks the passes' epochs: ep[8] is
+// the last epoch used, ep[p] that of pass p (1..7, cycling), so that a
+// replayed graph moves on as eager launches do.
+__global__ void k_sort_scan(uint32_t *raw, uint32_t *hist, uint32_t *tile_ctr, uint32_t *ep,
+                            int passes) {
   __shared__ uint32_t s[kRadix];
   if (threadIdx.x < 8) tile_ctr[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) {
+    uint32_t e = ep[8];
+    for (int p = 0; p < passes; ++p) {
+      e = e % 7u + 1u;
+      ep[p] = e;
+    }
+    ep[8] = e;
+  }
   for (int p = 0; p < passes; ++p) {
     uint32_t v = raw[p * kRadix + threadIdx.x];
     raw[p * kRadix + threadIdx.x] = 0u;
@@ -70,7 +82,9 @@ __global__ void __launch_bounds__(256, 4) k_sort_pass(
     const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
     unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
     const uint32_t *__restrict__ digit_base, uint32_t *status, uint32_t *tile_ctr,
-    uint32_t epoch, long long spin_limit, int debug_stall, unsigned int *st_flags) {
+    const uint32_t *epoch_p, long long spin_limit, int debug_stall, unsigned int *st_flags,
+    const float4 *__restrict__ pos_u, const float4 *__restrict__ dir_u, float4 *__restrict__ pos,
+    float4 *__restrict__ dir) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -118,7 +132,7 @@ __global__ void __launch_bounds__(256, 4) k_sort_pass(
     cnt = run;
     // publish the tile aggregate, then look back over preceding tiles
     uint32_t *my = status + (int64_t)tile * kRadix + d;
-    const uint32_t ep = epoch << kEpochShift;
+    const uint32_t ep = *epoch_p << kEpochShift;
     uint32_t excl = 0;
     if (tile == 0) {
       if (!debug_stall) atomicExch(my, kPre | ep | cnt);
@@ -184,7 +198,13 @@ __global__ void __launch_bounds__(256, 4) k_sort_pass(
     const uint32_t g = sm.gbase[d] + (uint32_t)j - sm.dexcl[d];
     if ((int64_t)g < n) {  // always true unless a wait expired (then the result is discarded)
       kout[g] = kk;
-      vout[g] = sm.vals[j];
+      if (pos) {  // last pass: gather the photon itself into Morton order
+        const uint32_t src = sm.vals[j];
+        pos[g] = pos_u[src];
+        dir[g] = dir_u[src];
+      } else {
+        vout[g] = sm.vals[j];
+      }
     }
   }
 }
@@ -195,10 +215,12 @@ cudaError_t sort_prepare() {
                               (int)sizeof(SortSmem));
 }
 
-// Sort w.key[0]/w.val[0] by the low key_bits bits.  *out_sel receives the
-// buffer index holding the result.  The key kernel has counted every pass's
-// digits into w.sort_raw (which the scan clears again, as it does the tile
-// counters; both are zero when allocated).
+// Sort w.key[0]/w.val[0] by the low key_bits bits and gather the SoA into
+// w.pos / w.dir in the sorted order (the last pass does it).  *out_sel
+// receives the buffer index holding the sorted keys.  The key kernel has
+// counted every pass's digits into w.sort_raw (which the scan clears again, as
+// it does the tile counters; both are zero when allocated).  n <= 1: nothing
+// is sorted or gathered.
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,
                         int debug_stall, unsigned int *status, int *out_sel, cudaStream_t s) {
   *out_sel = 0;
@@ -209,22 +231,20 @@ cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_li
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((e = cudaStreamIsCapturing(s, &cap))) return e;
   const bool capturing = cap != cudaStreamCaptureStatusNone;
-  k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_raw, w.sort_hist, w.sort_tile, passes);
+  if (w.sort_epoch == 0) {  // fresh buffers, or a wait expired: clear the words once
+    if ((e = cudaMemsetAsync(w.sort_status, 0, sizeof(uint32_t) * kRadix * tiles, s))) return e;
+    if ((e = cudaMemsetAsync(w.sort_ep, 0, sizeof(uint32_t) * 9, s))) return e;
+    if (!capturing) w.sort_epoch = 1;
+  }
+  k_sort_scan<<<1, kRadix, 0, s>>>(w.sort_raw, w.sort_hist, w.sort_tile, w.sort_ep, passes);
   int sel = 0;
   for (int p = 0; p < passes; ++p) {
-    // a captured graph replays its arguments, so it clears the words before
-    // every pass; eager launches cycle the epoch 1..7 instead
-    uint32_t epoch = 1;
-    if (capturing || w.sort_epoch == 0) {
-      if ((e = cudaMemsetAsync(w.sort_status, 0, sizeof(uint32_t) * kRadix * tiles, s))) return e;
-      w.sort_epoch = capturing ? 0 : 1;
-    } else {
-      w.sort_epoch = w.sort_epoch % 7 + 1;
-      epoch = (uint32_t)w.sort_epoch;
-    }
+    const bool last = p == passes - 1;
     k_sort_pass<<<(unsigned)tiles, kSortThreads, sizeof(SortSmem), s>>>(
         w.key[sel], w.val[sel], w.key[sel ^ 1], w.val[sel ^ 1], n, 8 * p, w.sort_hist + p * kRadix,
-        w.sort_status, w.sort_tile + p, epoch, spin_limit, debug_stall && p == 0, status);
+        w.sort_status, w.sort_tile + p, w.sort_ep + p, spin_limit, debug_stall && p == 0, status,
+        last ? w.pos_u : nullptr, last ? w.dir_u : nullptr, last ? w.pos : nullptr,
+        last ? w.dir : nullptr);
     if ((e = cudaGetLastError())) return e;
     sel ^= 1;
   }
