@@ -201,7 +201,9 @@ int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const tr
  *   stack_depth  traversal stack entries per warp, in shared memory (64..4096)
  *   block_shape  traversal warps per block (1..16)
  *   budget       traversal iterations a warp spends on one work item before it
- *                hands the rest to the next pass (0 = never) */
+ *                hands the rest on, as chunks of 8 node pairs, to the step's
+ *                device work queue, where idle warps take them (0 = never;
+ *                default 16) */
 
 /* Set the knobs; the next trilens_collide_step needs a fresh trilens_build.
  * INVALID if a knob is out of range or the shape does not fit an SM. */

@@ -62,7 +62,7 @@ enum {
 struct TLCounters {
   unsigned long long hits;         // colliding pairs found (may exceed capacity)
   unsigned long long band;         // FP32 band pairs queued for FP64
-  unsigned long long q_tail;       // traversal queue: slots reserved (items handed on)
+  unsigned long long q_tail;       // traversal queue: chunks reserved (items handed on)
   unsigned long long narrow_tests; // photon pairs tested
   unsigned long long node_tests;   // box pair tests
   unsigned long long leaf_pairs;   // overlapping bucket pairs
@@ -180,8 +180,8 @@ struct TravArgs {
   unsigned long long hit_cap;
   uint2 *band;
   unsigned long long band_cap;
-  unsigned long long *queue;  // traversal work queue: (ref A, ref B) pairs, sentinel when free
-  unsigned long long queue_cap;
+  unsigned long long *queue;  // traversal work queue: chunks of 8 (ref A, ref B) pairs
+  unsigned long long queue_cap;  // in pairs
   int stack_depth;
   const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal
   long long spin_limit;          // iteration limit of the wait between passes

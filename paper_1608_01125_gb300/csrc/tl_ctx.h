@@ -32,7 +32,7 @@ struct trilens_ctx {
   int64_t built_step = -1;
   // traversal workspace
   int n_sm = 0, trav_warps = 4, trav_blocks = 0, expand_blocks = 0;
-  int budget = 64;  // traversal iterations per work item before it is split
+  int budget = 16;  // traversal iterations per work item before it is handed on
   unsigned front_target = 0, front_cap = 0;
   uint2 *front[2]{};
   uint2 *queue = nullptr;  // traversal work queue (every free slot holds the sentinel)

@@ -321,14 +321,16 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
 // ------------------------------------------------------------ traversal
 
 // Persistent warps share one work queue.  The frontier's items come first
-// (indices below n0), then the queue's slots: a warp that spends `budget`
-// iterations on one item hands the rest of it (its whole stack) to the queue,
-// where idle warps take the pieces at once; a warp whose stack is full hands
-// on the pair that does not fit.  Free queue slots hold a sentinel: a taker
-// swaps the sentinel back in as it reads (atomic exchange), and waits while
-// its slot is still free and work is in flight.  The traversal ends when the
-// items finished equal n0 plus the items handed on.  Every wait is bounded by
-// spin_limit (then TL_ST_TIMEOUT).
+// (indices below n0), then the queue's chunks of up to 8 node pairs each (64
+// bytes): a warp that spends `budget` iterations on one item hands the rest of
+// it (its whole stack) on as chunks, which idle warps take at once, popping 8
+// pairs in their first iteration; a warp whose stack is full hands on the pair
+// that does not fit as a chunk of one.  Unused and free entries hold a
+// sentinel.  A writer fills a chunk's entries 1..7, fences, then swaps entry 0
+// in; a taker swaps the sentinel back into entry 0 as it reads it (atomic
+// exchange) and waits while it is still free and work is in flight.  The
+// traversal ends when the chunks finished equal n0 plus the chunks handed on.
+// Every wait is bounded by spin_limit (then TL_ST_TIMEOUT).
 constexpr unsigned long long kQFree = 0xffffffffffffffffull;
 
 __device__ __forceinline__ unsigned long long pack2(uint2 v) {
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
     n0 = list_n;
   }
   unsigned long long *Q = a.queue;
-  const unsigned long long qcap = a.queue_cap;
+  const unsigned long long qcap = a.queue_cap >> 3;  // chunks of 8 pairs
   const unsigned lt = (1u << lane) - 1u;
   int sp = 0, nq = 0, iters = 0;
   bool holding = false;  // this warp holds an item (counted in flight)
@@ -367,16 +369,23 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
   unsigned long long node_tests = 0, narrow_tests = 0, leaf_pairs = 0;
   while (true) {
     if (sp > 0 && budget > 0 && iters >= budget) {
-      // this item is large: hand the rest of it (the whole stack) to the queue;
-      // the handed pieces are counted before this item is counted finished
+      // this item is large: hand the rest of it (the whole stack) on as chunks;
+      // they are counted before this item is counted finished
+      const int nch = (sp + 7) >> 3;
       unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(&ctr->q_tail, (unsigned long long)sp);
+      if (lane == 0) base = atomicAdd(&ctr->q_tail, (unsigned long long)nch);
       handed = true;
       base = __shfl_sync(0xffffffffu, base, 0);
-      for (int e = lane; e < sp; e += 32) {
-        if (base + e < qcap) {
-          if (atomicExch(Q + base + e, pack2(stack[e])) != kQFree)
-            atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);  // a slot was not free
+      for (int e = lane; e < nch * 8; e += 32) {  // entries 1..7 of every chunk
+        if ((e & 7) != 0 && base + (e >> 3) < qcap)
+          Q[(base + (e >> 3)) * 8 + (e & 7)] = e < sp ? pack2(stack[e]) : kQFree;
+      }
+      __threadfence();
+      __syncwarp();
+      for (int c = lane; c < nch; c += 32) {  // then entry 0: the chunk is ready
+        if (base + c < qcap) {
+          if (atomicExch(Q + (base + c) * 8, pack2(stack[c * 8])) != kQFree)
+            atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);  // a chunk was not free
         } else {
           atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
         }
@@ -385,7 +394,8 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
       sp = 0;
     }
     if (sp == 0) {
-      int got = 0;
+      int got = 0;  // 1: a frontier item; 2: a queue chunk
+      unsigned long long chunk = 0;
       uint2 item = make_uint2(0u, 0u);
       if (lane == 0) {
         if (holding) {
@@ -399,14 +409,16 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
           item = __ldcg(src0 + i);
           got = 1;
         } else if (i - n0 < qcap) {
-          unsigned long long *slot = Q + (i - n0);
+          chunk = i - n0;
+          unsigned long long *slot = Q + chunk * 8;
           long long spins = 0;
           unsigned ns = 32;
           while (true) {
             const unsigned long long v = atomicExch(slot, kQFree);
             if (v != kQFree) {
               item = make_uint2((unsigned)v, (unsigned)(v >> 32));
-              got = 1;
+              got = 2;
+              __threadfence();  // entry 0 seen: the chunk's other entries are written
               break;
             }
             // finished items first, then hand-ons: equal means nothing was in
@@ -428,12 +440,20 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
       }
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) break;
+      sp = 1;
+      if (got == 2) {  // entries 1..7 of the chunk: the written ones come first
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        unsigned long long v = kQFree;
+        if (lane >= 1 && lane < 8) v = __ldcg(Q + chunk * 8 + lane);
+        const unsigned mv = __ballot_sync(0xffffffffu, v != kQFree);
+        if (v != kQFree) stack[lane] = make_uint2((unsigned)v, (unsigned)(v >> 32));
+        sp = 1 + __popc(mv);
+      }
       if (lane == 0) {
         stack[0] = item;
         holding = true;
       }
       __syncwarp();
-      sp = 1;
       iters = 0;
     }
     ++iters;
@@ -472,10 +492,16 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
       const int slot = sp + __popc(mpush & lt);
       if (slot < D) {
         stack[slot] = o;
-      } else {  // the stack is full: this pair goes to the queue
+      } else {  // the stack is full: this pair goes to the queue as a chunk of one
         const unsigned long long idx = atomicAdd(&ctr->q_tail, 1ull);
-        if (idx >= qcap || atomicExch(Q + idx, pack2(o)) != kQFree)
+        if (idx < qcap) {
+          for (int k = 1; k < 8; ++k) Q[idx * 8 + k] = kQFree;
+          __threadfence();
+          if (atomicExch(Q + idx * 8, pack2(o)) != kQFree)
+            atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+        } else {
           atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+        }
       }
     }
     sp = min(sp + __popc(mpush), D);
