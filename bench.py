@@ -200,6 +200,23 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def slowest_rank_ms(ms: float, world: int, device=None) -> float:
+    """The largest of every rank's time (ranks run replicas; the job ends with
+    the slowest).  A collective only when there are several ranks."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units all ranks processed per second of the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def config_of(wl, l2):
     return {"workload": wl.name, "photons_per_beam": wl.a.n, "time_steps": wl.steps,
             "dt_fs": wl.dt, "kappa": wl.kappa, "precision": "fp32 + fp64 band",
@@ -293,13 +310,10 @@ def run_ours(args, wl):
         sw_ms.append(e0.elapsed_time(e1))
     phase_ms, launches = col.phase_ms(reset=True)
     col.timing(False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_rank_ms(ms, world, dev)
     K = args.steps
     units_rank = wl.a.n * wl.b.n * nsteps * K
-    value = world * units_rank / (ms / 1e3)
+    value = whole_job_rate(units_rank, world, ms)
 
     # end to end through the public API with host buffers: every step copies
     # the two beams from pinned host memory, runs, and reads the yield back
@@ -318,7 +332,8 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = world * wl.a.n * wl.b.n * nsteps / (statistics.mean(e2e_ms) / 1e3)
+    e2e_value = whole_job_rate(wl.a.n * wl.b.n * nsteps, world,
+                               slowest_rank_ms(statistics.mean(e2e_ms), world, dev))
 
     if rank != 0:
         if world > 1:
