@@ -81,6 +81,12 @@ def lib():
             L.oracle_tree.argtypes = [pb, pb, ctypes.c_int64, d, d, ctypes.c_int, ctypes.c_int, pu,
                                       ctypes.c_int64, pr]
             L.oracle_tree.restype = ctypes.c_int
+            L.oracle_pair_products.argtypes = [pb, pb, pu, ctypes.c_int64, ctypes.c_uint64,
+                                               ctypes.POINTER(ctypes.c_double)]
+            L.oracle_pair_products.restype = ctypes.c_int
+            L.oracle_com_direction.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                               ctypes.POINTER(ctypes.c_double)]
+            L.oracle_com_direction.restype = None
             _lib = L
     return _lib
 
@@ -152,3 +158,27 @@ def tree(a: dict, b: dict, step: int, dt: float, kappa: float, leaf_size: int = 
          nthreads: int = 1, cap: int = 1 << 16):
     """The paper's k-d hierarchy with depth-first dual traversal; same output."""
     return _run(lib().oracle_tree, a, b, step, dt, kappa, (int(leaf_size), int(nthreads)), cap)
+
+
+def pair_products(a: dict, b: dict, hits, seed: int):
+    """Electron and positron four-momenta [MeV] of each hit (i, j): (n, 8) float64
+    = electron (E, px, py, pz), positron (E, px, py, pz)."""
+    A, ka = _beam(a)
+    B, kb = _beam(b)
+    h = np.ascontiguousarray(np.asarray(hits, dtype=np.uint32).reshape(-1, 2))
+    out = np.zeros((len(h), 8), dtype=np.float64)
+    rc = lib().oracle_pair_products(ctypes.byref(A), ctypes.byref(B),
+                                    h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), len(h),
+                                    ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError("a hit's photon pair is below threshold")
+    return out
+
+
+def com_direction(seed: int, i: int, j: int) -> np.ndarray:
+    """The CoM direction drawn for hit (i, j)."""
+    n = (ctypes.c_double * 3)()
+    lib().oracle_com_direction(ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), i, j, n)
+    return np.array(list(n))
+

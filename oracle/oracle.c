@@ -524,3 +524,79 @@ int oracle_tree(const oracle_beam *a, const oracle_beam *b, int64_t step, double
   unpose(&B);
   return err ? -1 : 0;
 }
+
+/* ---- pair products (Sec. 1: Eq. pTotal, Eq. Lorentz) ----------------------- */
+
+/* uniform double in [0, 1) from the top 53 bits of a splitmix64 output */
+static double unit_draw(uint64_t key, uint64_t t) {
+  return (double)(oracle_splitmix64(key + t) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* Marsaglia (1972): x1, x2 uniform in (-1, 1) until S = x1^2 + x2^2 is in
+ * (0, 1); then n = (2 x1 sqrt(1 - S), 2 x2 sqrt(1 - S), 1 - 2 S) is uniform on
+ * the unit sphere.  At most 64 tries (then n = z; never reached in practice). */
+void oracle_com_direction(uint64_t seed, uint32_t i, uint32_t j, double n[3]) {
+  const uint64_t key = seed ^ (((uint64_t)i << 32) | (uint64_t)j);
+  for (uint64_t t = 0; t < 128; t += 2) {
+    const double x1 = 2.0 * unit_draw(key, t) - 1.0;
+    const double x2 = 2.0 * unit_draw(key, t + 1) - 1.0;
+    const double S = x1 * x1 + x2 * x2;
+    if (S < 1.0 && S > 0.0) {
+      const double r = sqrt(1.0 - S);
+      n[0] = 2.0 * x1 * r;
+      n[1] = 2.0 * x2 * r;
+      n[2] = 1.0 - 2.0 * S;
+      return;
+    }
+  }
+  n[0] = 0.0;
+  n[1] = 0.0;
+  n[2] = 1.0;
+}
+
+/* Lorentz boost of the four-momentum (e, q) by velocity beta (|beta| < 1,
+ * gamma given): e' = gamma (e + beta.q), q' = q + beta (gamma^2/(gamma+1)
+ * beta.q + gamma e) */
+static void boost(const double beta[3], double gamma, double e, const double q[3],
+                  double out[4]) {
+  const double bq = beta[0] * q[0] + beta[1] * q[1] + beta[2] * q[2];
+  const double k = gamma * gamma / (gamma + 1.0) * bq + gamma * e;
+  out[0] = gamma * (e + bq);
+  out[1] = q[0] + beta[0] * k;
+  out[2] = q[1] + beta[1] * k;
+  out[3] = q[2] + beta[2] * k;
+}
+
+int oracle_pair_products(const oracle_beam *a, const oracle_beam *b, const uint32_t *hits,
+                         int64_t n_hits, uint64_t seed, double *out) {
+  int rc = 0;
+  for (int64_t k = 0; k < n_hits; ++k) {
+    const uint32_t i = hits[2 * k], j = hits[2 * k + 1];
+    const double E1 = a->E[i], E2 = b->E[j];
+    const double d1[3] = {a->dx[i], a->dy[i], a->dz[i]}, d2[3] = {b->dx[j], b->dy[j], b->dz[j]};
+    const double E = E1 + E2;
+    const double P[3] = {E1 * d1[0] + E2 * d2[0], E1 * d1[1] + E2 * d2[1],
+                         E1 * d1[2] + E2 * d2[2]};
+    const double cs = d1[0] * d2[0] + d1[1] * d2[1] + d1[2] * d2[2];
+    const double M2 = 2.0 * (E1 * E2) * (1.0 - cs); /* invariant mass squared */
+    const double m = O_MEC2;
+    double *o = out + 8 * k;
+    if (!(M2 > 4.0 * m * m)) { /* below threshold: no pair */
+      for (int q = 0; q < 8; ++q) o[q] = 0.0;
+      rc = -1;
+      continue;
+    }
+    const double M = sqrt(M2);
+    const double ep = 0.5 * M;                 /* CoM energy of each particle */
+    const double pp = sqrt(0.25 * M2 - m * m); /* CoM momentum (Eq. pTotal) */
+    double n[3];
+    oracle_com_direction(seed, i, j, n);
+    const double beta[3] = {P[0] / E, P[1] / E, P[2] / E};
+    const double gamma = E / M;
+    const double qe[3] = {pp * n[0], pp * n[1], pp * n[2]};
+    const double qp[3] = {-qe[0], -qe[1], -qe[2]};
+    boost(beta, gamma, ep, qe, o);
+    boost(beta, gamma, ep, qp, o + 4);
+  }
+  return rc;
+}

@@ -51,6 +51,22 @@ int oracle_pair_detail(const oracle_beam *a, int64_t i, const oracle_beam *b, in
                        int64_t step, double dt, double kappa, double out[6]);
 uint64_t oracle_splitmix64(uint64_t x);
 
+/* Pair products of collisions (Sec. 1, Eq. pTotal and Eq. Lorentz): for each
+ * hit (hits[2k] = i in a, hits[2k+1] = j in b) the electron and the positron
+ * made from photons i and j.  The photons' total energy E and momentum P
+ * (units of MeV, c = 1) fix the centre-of-mass (CoM) frame; there each
+ * particle has energy M/2 (M^2 = E^2 - P^2 = 2 E_i E_j (1 - cos)) and momentum
+ * p' = sqrt(M^2/4 - m^2), the electron along a random unit vector n and the
+ * positron opposite; both are boosted back to the lab.  n is uniform on the
+ * sphere: Marsaglia (1972) from uniforms of splitmix64 (the counter-based
+ * stream of key = seed ^ ((i << 32) | j), draws splitmix64(key + t), t = 0, 1,
+ * ...).  out[8k .. 8k+7] = electron (E, px, py, pz), positron (E, px, py, pz)
+ * [MeV].  Returns 0, or -1 if a hit's pair is below threshold. */
+int oracle_pair_products(const oracle_beam *a, const oracle_beam *b, const uint32_t *hits,
+                         int64_t n_hits, uint64_t seed, double *out);
+/* the same CoM direction draw, exposed for tests: n[3] for (seed, i, j) */
+void oracle_com_direction(uint64_t seed, uint32_t i, uint32_t j, double n[3]);
+
 /* All pairs.  Hits (i, j) written as uint32 pairs in lexicographic order,
  * at most cap of them; res->count is the true number. */
 int oracle_bruteforce(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
