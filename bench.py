@@ -174,6 +174,42 @@ def cpu_baseline(wl, a, b):
                       f"{threads} threads, {dt:.1f} s"}
 
 
+# FP64 operations per hit of the pair products, counted from the kernel: 26
+# for the photons' sums, the invariant mass and the CoM momentum, ~16 for the
+# direction (1.27 Marsaglia tries of 2 draws), 4 divisions, 2 x 16 for the two
+# boosts; 3 square roots; divisions and square roots counted as one each
+PAIR_FP64_OPS = 26 + 16 + 4 + 32 + 3
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (no measured figure here)
+
+
+def pair_products_timing(col, A, B, stream, step=2, seed=2024, reps=5):
+    """The pair products (electron and positron of each collision) of the
+    collision-peak step's hits: device time per call with CUDA events."""
+    import torch
+
+    from paper_1608_01125_gb300 import binding
+    h, _ = col.step_hits(step)
+    hits = torch.as_tensor(h.astype("uint32").view("int32"), device=A["px"].device).reshape(-1, 2)
+    out = binding.pair_products(A, B, hits, seed)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        binding.pair_products(A, B, hits, seed, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = min(ts)
+    n = int(hits.shape[0])
+    flops = n * PAIR_FP64_OPS / (ms / 1e3) / 1e12
+    return {"step": step, "hits": n, "ms": ms, "hits_per_s": n / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": flops, "peak": FP64_NOMINAL_TFLOPS,
+                         "unit": "FP64 TFLOP/s", "peak_source": "nominal",
+                         "frac": flops / FP64_NOMINAL_TFLOPS,
+                         "bytes_per_hit": 8 + 2 * 32 + 64}}
+
+
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -310,6 +346,7 @@ def run_ours(args, wl):
         sw_ms.append(e0.elapsed_time(e1))
     phase_ms, launches = col.phase_ms(reset=True)
     col.timing(False)
+    pairs = pair_products_timing(col, A, B, stream) if rank == 0 else None
     ms = slowest_rank_ms(ms, world, dev)
     K = args.steps
     units_rank = wl.a.n * wl.b.n * nsteps * K
@@ -377,6 +414,7 @@ def run_ours(args, wl):
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": read_traffic(dom), "algorithmic_bytes_per_launch": algo,
                      "launch_ms": launch_ms},
+        "pair_products": pairs,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 16},

@@ -147,6 +147,24 @@ int trilens_yield(trilens_ctx *c, int32_t mode, int32_t level_L, double *count,
  * TIMEOUT if a device wait ran out. */
 int trilens_run(trilens_ctx *c, int64_t first_step, int64_t steps, trilens_step_stats *out);
 
+/* The electron and the positron of each collision (Sec. 1, Eq. pTotal and
+ * Eq. Lorentz).  hits: device, n_hits (i, j) uint32 pairs (i indexes beam a,
+ * j beam b), e.g. a trilens_collide_step hit list.  For each, the photons'
+ * total energy E and momentum P (MeV, c = 1) define the centre-of-mass (CoM)
+ * frame, where each particle has energy M/2 (M^2 = E^2 - |P|^2) and momentum
+ * p' = sqrt(M^2/4 - m_e^2); the electron flies along a random direction n
+ * uniform on the sphere, the positron opposite, and both are boosted back to
+ * the lab.  n is drawn from a counter-based splitmix64 stream keyed by
+ * seed ^ ((i << 32) | j) (Marsaglia's method), so a hit's products depend
+ * only on (seed, i, j).  out: device, n_hits x 8 doubles = electron (E, px,
+ * py, pz), positron (E, px, py, pz) [MeV]; a hit whose indices are out of
+ * range or whose pair is below threshold gets zeros.  FP64, every operation
+ * rounded to nearest in a fixed order.  Asynchronous on `stream` (the current
+ * device); allocates nothing.  INVALID for a bad beam, negative n_hits, or
+ * NULL arrays with n_hits > 0. */
+int trilens_pair_products(const trilens_beam *a, const trilens_beam *b, const uint32_t *hits,
+                          int64_t n_hits, uint64_t seed, double *out, trilens_stream_t stream);
+
 /* Zero the cumulative yield. */
 int trilens_reset_yield(trilens_ctx *c);
 

@@ -92,6 +92,9 @@ def lib() -> ctypes.CDLL:
         L.trilens_reset_yield.restype = ctypes.c_int
         L.trilens_run.argtypes = [vp, i64, i64, ctypes.POINTER(StepStats)]
         L.trilens_run.restype = ctypes.c_int
+        L.trilens_pair_products.argtypes = [ctypes.POINTER(Beam), ctypes.POINTER(Beam), vp, i64,
+                                            ctypes.c_uint64, vp, vp]
+        L.trilens_pair_products.restype = ctypes.c_int
         L.trilens_destroy.argtypes = [vp]
         L.trilens_destroy.restype = None
         L.trilens_status_str.argtypes = [ctypes.c_int]
@@ -420,6 +423,25 @@ def yield_reduce_noalloc(hits, n_hits: int, w_a=None, w_b=None, out=None, stream
     ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
     _check(lib().trilens_yield_reduce_noalloc(ptr(hits), int(n_hits), ptr(w_a), ptr(w_b), ptr(out),
                                              ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def pair_products(beam_a: dict, beam_b: dict, hits, seed: int, out=None, stream=None):
+    """Electron and positron four-momenta [MeV] of each hit (trilens_pair_products):
+    beams as device tensors (to_device), hits an (n, 2) int32 CUDA tensor of
+    (i, j); returns an (n, 8) float64 CUDA tensor = electron (E, px, py, pz),
+    positron (E, px, py, pz)."""
+    torch = _torch()
+    n = int(hits.shape[0]) if hits.dim() == 2 else int(hits.numel() // 2)
+    if out is None:
+        out = torch.empty((n, 8), dtype=torch.float64, device=hits.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ba, bb = beam_struct(beam_a), beam_struct(beam_b)
+    _check(lib().trilens_pair_products(ctypes.byref(ba), ctypes.byref(bb),
+                                       ctypes.c_void_p(hits.data_ptr()), n,
+                                       ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
+                                       ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(st.cuda_stream)))
     return out
 
 

@@ -33,6 +33,9 @@ cudaError_t launch_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *ro
                                   const uint32_t *rootB, int n_inst, cudaStream_t s);
 cudaError_t launch_yield_inst(const TravArgs &a, const uint32_t *inst_of_a, double *yields,
                               int blocks, cudaStream_t s);
+cudaError_t launch_pair_products(const TLBeam &a, const TLBeam &b, const uint32_t *hits,
+                                 int64_t n_hits, unsigned long long seed, double *out, int n_sm,
+                                 cudaStream_t s);
 cudaError_t launch_step_finish(const TLCounters *ctr, unsigned *run_status, TLRunAcc *acc,
                                cudaStream_t s);
 }  // namespace tl
@@ -1041,6 +1044,31 @@ int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
   cache_store(cache_path, key, best, best_ms);
   if (chosen)
     for (int i = 0; i < 4; ++i) chosen[i] = best[i];
+  return TRILENS_OK;
+}
+
+int trilens_pair_products(const trilens_beam *a, const trilens_beam *b, const uint32_t *hits,
+                          int64_t n_hits, uint64_t seed, double *out, trilens_stream_t stream) {
+  if (!beam_ok(a) || !beam_ok(b) || n_hits < 0 || n_hits >= (1ll << 40)) return TRILENS_ERR_INVALID;
+  if (n_hits == 0) return TRILENS_OK;
+  if (!hits || !out || a->n == 0 || b->n == 0) return TRILENS_ERR_INVALID;
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return TRILENS_ERR_CUDA;
+  TLBeam ta, tb;
+  const trilens_beam *bs[2] = {a, b};
+  TLBeam *ts[2] = {&ta, &tb};
+  for (int k = 0; k < 2; ++k) {
+    TLBeam &t = *ts[k];
+    t.n = bs[k]->n;
+    t.px = bs[k]->px; t.py = bs[k]->py; t.pz = bs[k]->pz;
+    t.dx = bs[k]->dx; t.dy = bs[k]->dy; t.dz = bs[k]->dz;
+    t.E = bs[k]->E; t.w = bs[k]->w;
+  }
+  if (tl::launch_pair_products(ta, tb, hits, n_hits, (unsigned long long)seed, out, n_sm,
+                               (cudaStream_t)stream) != cudaSuccess)
+    return TRILENS_ERR_CUDA;
   return TRILENS_OK;
 }
 

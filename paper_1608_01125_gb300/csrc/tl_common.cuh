@@ -48,6 +48,15 @@ __device__ __forceinline__ bool tl_overlap(const TLBox &a, const TLBox &b) {
          b.lz <= a.hz;
 }
 
+// splitmix64 (Steele, Lea, Flood 2014; Vigna's published constants): the
+// hit-set checksum and the counter-based stream of the pair products
+__device__ __forceinline__ unsigned long long smix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 // device status bits (OR-ed into TLCounters::status)
 enum {
   TL_ST_HIT_OVF = 1,

@@ -547,12 +547,6 @@ __global__ void __launch_bounds__(256) k_band(TravArgs a) {
 // ------------------------------------------------------------ yield
 
 // splitmix64 (Steele, Lea & Flood 2014; Vigna's constants)
-__device__ __forceinline__ unsigned long long smix64(unsigned long long x) {
-  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 struct Partial {
   unsigned long long count;
