@@ -70,4 +70,15 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.trilens_build(None, 0) == binding.ERR_INVALID
     assert lib.trilens_collide_step(None, 0, None, 0, None) == binding.ERR_INVALID
     assert lib.trilens_debug_eval64(None, None, -1, 0, None) == binding.ERR_INVALID
+    assert lib.trilens_run(None, 0, 1, None) == binding.ERR_INVALID
+    for name in ("trilens_debug_set_cut_cap", "trilens_debug_set_key_bits"):
+        assert getattr(lib, name)(None, 8) == binding.ERR_INVALID
+    assert lib.trilens_debug_shrink_buffers(None, 64) == binding.ERR_INVALID
+    # pair products: argument checks before any device work; no hits is a no-op
+    pp = lib.trilens_pair_products
+    assert pp(None, ctypes.byref(empty), None, 0, 0, None, None) == binding.ERR_INVALID
+    assert pp(ctypes.byref(empty), ctypes.byref(bad_n), None, 0, 0, None, None) == binding.ERR_INVALID
+    assert pp(ctypes.byref(empty), ctypes.byref(empty), None, -1, 0, None, None) == binding.ERR_INVALID
+    assert pp(ctypes.byref(empty), ctypes.byref(empty), None, 0, 0, None, None) == 0
+    assert pp(ctypes.byref(empty), ctypes.byref(empty), None, 3, 0, None, None) == binding.ERR_INVALID
     lib.trilens_destroy(None)

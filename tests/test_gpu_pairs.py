@@ -48,7 +48,7 @@ def test_small_headon_bit_exact():
 def test_crossing_90deg_bit_exact():
     wl = synth.crossing90_5e7(n=3000, seed=6)
     a, b = synth.beams(wl)
-    check_case(a, b, 128, wl.dt, 1e16, seed=99, min_hits=100)
+    check_case(a, b, 128, wl.dt, 1e18, seed=99, min_hits=500)
 
 
 def test_full_size_headon_peak_step_bit_exact():
