@@ -677,9 +677,9 @@ int trilens_batch_create(trilens_ctx **out, const trilens_beam *a, const trilens
   return TRILENS_OK;
 }
 
-// One step of a captured run: the collide sequence without host checks.  The
-// traversal runs a fixed number of passes with device-side list counts; work
-// left after them, and every overflow, is flagged in run_status.
+// One step of a captured run: the collide sequence without host checks (the
+// traversal needs none: its warps share a device work queue); every overflow
+// is flagged in run_status, and the step's totals are added on the device.
 static int graph_collide(trilens_ctx *c, int64_t step, double *yields) {
   const double ct = TL_C * ((double)step * c->p.dt_fs);
   const int nonempty = c->beam[0].n > 0 && c->beam[1].n > 0;

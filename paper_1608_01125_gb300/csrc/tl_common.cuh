@@ -193,7 +193,7 @@ struct TravArgs {
   unsigned long long queue_cap;  // in pairs
   int stack_depth;
   const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal
-  long long spin_limit;          // iteration limit of the wait between passes
+  long long spin_limit;          // iteration limit of a warp's wait for queued work
 };
 
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],

@@ -3,9 +3,11 @@
 //
 // The two hierarchies are traversed against each other (Sec. 2.2: depth-first
 // descent; a failed overlap test, Eq. CollDet, skips the whole subtree pair).
-// A few breadth-first expansion levels first turn the root pair into a
-// frontier of node pairs; then persistent warps take frontier pairs and
-// descend depth first with a stack of node pairs in shared memory.  Each
+// The frontier of node pairs comes from the refit's seed lists (large beams:
+// every overlapping pair of cut nodes) or from a few breadth-first expansion
+// levels of the root pair; then persistent warps take frontier pairs and
+// descend depth first with a stack of node pairs in shared memory, handing
+// large items on to a device work queue (see k_traverse).  Each
 // iteration a warp pops up to 8 pairs and tests the up-to-4 child
 // combinations of each with one lane per combination; survivors are pushed
 // (or, when both sides are leaf buckets, queued) with ballot/popc
