@@ -290,7 +290,9 @@ int trilens_mlp_grad(const float *params, const float *norm, const float *x, con
  * (trained with a Poisson-type deviance, whose minimiser is the conditional
  * mean; trilens_mlp_grad loss_kind 1), times a calibration scale fitted on
  * the training pairs; pairs whose predicted standard deviation of y
- * exceeds tau are evaluated exactly instead (the fallback). */
+ * exceeds tau are evaluated exactly instead (the fallback), and the scale is
+ * then the one fitted on the training pairs the network keeps at that tau
+ * (a table over tau = 2^(g/2 - 10), g = 0..63; the largest edge <= tau). */
 
 /* Build each listed step, collect its level-L pairs with features and exact
  * labels into the context's training set (steps are not added to the
@@ -301,7 +303,8 @@ int trilens_surrogate_collect(trilens_ctx *c, const int64_t *steps, int32_t n, i
 /* Train the network on the collected samples (feature normalisation from
  * the samples, He-initialised weights from `seed`, AdamW with cosine decay,
  * minibatches of 8192, `epochs` passes), then fit the calibration scales of
- * the network's and of the ST-form estimates on all the samples. */
+ * the network's and of the ST-form estimates on all the samples, and the
+ * network's per fallback threshold (on the samples the network keeps). */
 int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed);
 
 /* collect + fit. */
@@ -335,8 +338,10 @@ int trilens_surrogate_dataset(trilens_ctx *c, float *x, double *label, float *st
 int trilens_surrogate_add_samples(trilens_ctx *c, const float *x, const double *label,
                                   const float *st, int64_t n, int32_t level_L);
 
-/* Save / load the model (level, calibrations, feature normalisation and
- * parameters) as a little-endian binary file. */
+/* Save / load the model (level, calibrations and the table by fallback
+ * threshold, feature normalisation and parameters) as a little-endian binary
+ * file ("TRLSUR03"; an older "TRLSUR02" file without the table loads with
+ * one scale for every threshold). */
 int trilens_surrogate_save(trilens_ctx *c, const char *path);
 int trilens_surrogate_load(trilens_ctx *c, const char *path);
 

@@ -14,6 +14,9 @@
 
 
 constexpr int kBatch = 8192;
+constexpr int kTauBins = 64;
+// edges of the fallback-threshold bins of the calibration table: 2^(g/2 - 10)
+static inline double tau_edge(int g) { return std::ldexp(1.0, -10) * std::pow(2.0, 0.5 * g); }
 
 struct SurrogateState {
   // model
@@ -22,6 +25,10 @@ struct SurrogateState {
   bool trained = false;
   int level = -1;
   double calib = 1.0, st_calib = 1.0, st_only_calib = 1.0;
+  // calibration by fallback threshold: cal_tau[g] is the calibration of the
+  // training pairs whose predicted spread is at most kTauEdge(g) (the pairs the
+  // network keeps at that threshold; the others are evaluated exactly)
+  double cal_tau[64];
   int adam_step = 0;
   // per-step buffers
   double *pre[2]{}, *bsum[2]{};
@@ -471,6 +478,9 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
   // whose objective has an intercept, it stays close to 1)
   const int64_t c0 = 0;
   double lab = 0, est = 0, stsum = 0;
+  std::vector<double> bl(kTauBins + 1, 0.0), be(kTauBins + 1, 0.0);  // per spread bin
+  std::vector<float> hout;
+  std::vector<double> hpred, hlb;
   if (!rc && tl::mlp_pack(s->prm, s->work, c->stream)) rc = fail(c, TRILENS_ERR_CUDA, "pack");
   for (int64_t r0 = c0; !rc && r0 < N; r0 += s->cut_cap) {
     const int64_t m = std::min<int64_t>(s->cut_cap, N - r0);
@@ -492,6 +502,24 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
     est += a;
     lab += b;
     stsum += d;
+    // the same sums split by predicted spread (in sample order: deterministic)
+    hout.resize(2 * (size_t)m);
+    hpred.resize((size_t)m);
+    hlb.resize((size_t)m);
+    if (cudaMemcpy(hout.data(), s->out, sizeof(float) * 2 * m, cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(hpred.data(), s->pred, sizeof(double) * m, cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(hlb.data(), dlab + r0, sizeof(double) * m, cudaMemcpyDeviceToHost)) {
+      rc = fail(c, TRILENS_ERR_CUDA, "calibration copy failed");
+      break;
+    }
+    for (int64_t q = 0; q < m; ++q) {
+      const float sv = std::fmin(std::fmax(hout[2 * q + 1], -12.f), 12.f);
+      const double spread = std::sqrt(std::exp((double)sv));
+      int g = 0;
+      while (g < kTauBins && spread > tau_edge(g)) ++g;  // bin kTauBins: above every edge
+      bl[g] += hlb[q];
+      be[g] += hpred[q];
+    }
   }
   cudaFree(dx);
   cudaFree(dy);
@@ -499,6 +527,14 @@ int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed) {
   cudaFree(dlab);
   if (rc) return rc;
   s->calib = est > 0 ? lab / est : 1.0;
+  {  // the pairs with spread <= edge g: bins 0..g
+    double cl = 0, ce = 0;
+    for (int g = 0; g < kTauBins; ++g) {
+      cl += bl[g];
+      ce += be[g];
+      s->cal_tau[g] = ce > 0 ? cl / ce : s->calib;
+    }
+  }
   // the ST-form estimator alone (the network keeps the baseline scale it was
   // trained with; over all samples the two agree)
   s->st_only_calib = stsum > 0 ? lab / stsum : s->st_calib;
@@ -563,7 +599,14 @@ int trilens_surrogate_step(trilens_ctx *c, int64_t step, int32_t level_L, float 
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
   cudaEventDestroy(e3);
-  const double yield = s->calib * est + fb_exact;
+  // the calibration of the pairs the network keeps at this threshold
+  double cal = s->calib;
+  for (int g = kTauBins - 1; g >= 0; --g)
+    if (tau_edge(g) <= (double)tau) {
+      if (g < kTauBins - 1) cal = s->cal_tau[g];
+      break;
+    }
+  const double yield = cal * est + fb_exact;
   s->tot += yield;
   out[0] = yield;                 // surrogate estimate of the step's weighted yield
   out[1] = s->st_only_calib * st;  // the ST-form estimate (no network), same pairs
@@ -642,11 +685,13 @@ int trilens_surrogate_save(trilens_ctx *c, const char *path) {
   CK(cudaMemcpy(nrm.data(), s->norm, sizeof(float) * 48, cudaMemcpyDeviceToHost));
   FILE *f = fopen(path, "wb");
   if (!f) return fail(c, TRILENS_ERR_INVALID, "cannot write %s", path);
-  const char magic[8] = {'T', 'R', 'L', 'S', 'U', 'R', '0', '2'};
+  const char magic[8] = {'T', 'R', 'L', 'S', 'U', 'R', '0', '3'};
   const int32_t hdr[2] = {s->level, TRILENS_MLP_PARAMS};
   const double cal[3] = {s->calib, s->st_calib, s->st_only_calib};
   bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 2, f) == 2 &&
-            fwrite(cal, sizeof(double), 3, f) == 3 && fwrite(nrm.data(), sizeof(float), 48, f) == 48 &&
+            fwrite(cal, sizeof(double), 3, f) == 3 &&
+            fwrite(s->cal_tau, sizeof(double), kTauBins, f) == (size_t)kTauBins &&
+            fwrite(nrm.data(), sizeof(float), 48, f) == 48 &&
             fwrite(p.data(), sizeof(float), p.size(), f) == p.size();
   fclose(f);
   return ok ? TRILENS_OK : fail(c, TRILENS_ERR_INVALID, "short write to %s", path);
@@ -665,10 +710,15 @@ int trilens_surrogate_load(trilens_ctx *c, const char *path) {
   int32_t hdr[2];
   double cal[3];
   std::vector<float> p(TRILENS_MLP_PARAMS), nrm(48);
-  bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "TRLSUR02", 8) == 0 &&
+  double tab[kTauBins];
+  bool ok = fread(magic, 1, 8, f) == 8 &&
+            (memcmp(magic, "TRLSUR03", 8) == 0 || memcmp(magic, "TRLSUR02", 8) == 0) &&
             fread(hdr, sizeof(int32_t), 2, f) == 2 && hdr[1] == TRILENS_MLP_PARAMS &&
-            fread(cal, sizeof(double), 3, f) == 3 && fread(nrm.data(), sizeof(float), 48, f) == 48 &&
-            fread(p.data(), sizeof(float), p.size(), f) == p.size();
+            fread(cal, sizeof(double), 3, f) == 3;
+  const bool has_tab = ok && magic[7] == '3';
+  if (has_tab) ok = fread(tab, sizeof(double), kTauBins, f) == (size_t)kTauBins;
+  ok = ok && fread(nrm.data(), sizeof(float), 48, f) == 48 &&
+       fread(p.data(), sizeof(float), p.size(), f) == p.size();
   fclose(f);
   if (!ok) return fail(c, TRILENS_ERR_INVALID, "%s is not a surrogate model file", path);
   CK(cudaMemcpy(s->prm, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice));
@@ -677,6 +727,7 @@ int trilens_surrogate_load(trilens_ctx *c, const char *path) {
   s->calib = cal[0];
   s->st_calib = cal[1];
   s->st_only_calib = cal[2];
+  for (int g = 0; g < kTauBins; ++g) s->cal_tau[g] = has_tab ? tab[g] : cal[0];
   s->trained = true;
   return TRILENS_OK;
 }
