@@ -87,6 +87,12 @@ def lib():
             L.oracle_com_direction.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                                ctypes.POINTER(ctypes.c_double)]
             L.oracle_com_direction.restype = None
+            pd = ctypes.POINTER(ctypes.c_double)
+            L.oracle_hit_times.argtypes = [pb, pb, ctypes.c_int64, d, d, pu, ctypes.c_int64, pd]
+            L.oracle_hit_times.restype = ctypes.c_int
+            L.oracle_deplete.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), pd, pu,
+                                         pd, ctypes.c_int64, pd, ctypes.c_int64, pd]
+            L.oracle_deplete.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -182,3 +188,57 @@ def com_direction(seed: int, i: int, j: int) -> np.ndarray:
     lib().oracle_com_direction(ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), i, j, n)
     return np.array(list(n))
 
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def hit_times(a: dict, b: dict, step: int, dt: float, kappa: float, hits) -> np.ndarray:
+    """Closest-approach time t* [fs, relative to t_k] of each hit (i, j) of step k."""
+    A, ka = _beam(a)
+    B, kb = _beam(b)
+    h = np.ascontiguousarray(np.asarray(hits, dtype=np.uint32).reshape(-1, 2))
+    t = np.zeros(len(h), dtype=np.float64)
+    rc = lib().oracle_hit_times(ctypes.byref(A), ctypes.byref(B), int(step), float(dt),
+                                float(kappa), h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                len(h), _pd(t))
+    if rc != 0:
+        raise ValueError("a listed pair is not a hit of this step")
+    return t
+
+
+def deplete(steps, tstar, hits, rem_a, rem_b):
+    """Depletion in chronological order (Sec. 2.2, Sec. 3.1): the hits, each with its
+    step and t*, taken in (step, t*, i, j) order; each takes min(rem_i, rem_j) from both.
+    Returns (delta per hit, rem_a, rem_b after), leaving the inputs untouched."""
+    h = np.ascontiguousarray(np.asarray(hits, dtype=np.uint32).reshape(-1, 2))
+    n = len(h)
+    st = np.ascontiguousarray(np.broadcast_to(np.asarray(steps, dtype=np.int64), (n,)))
+    t = np.ascontiguousarray(np.asarray(tstar, dtype=np.float64).reshape(n))
+    ra = np.array(rem_a, dtype=np.float64, copy=True)
+    rb = np.array(rem_b, dtype=np.float64, copy=True)
+    delta = np.zeros(n, dtype=np.float64)
+    rc = lib().oracle_deplete(n, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _pd(t),
+                              h.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _pd(ra), len(ra),
+                              _pd(rb), len(rb), _pd(delta))
+    if rc == -1:
+        raise ValueError("hit index out of range")
+    if rc != 0:
+        raise MemoryError("oracle_deplete")
+    return delta, ra, rb
+
+
+def deplete_run(a: dict, b: dict, dt: float, kappa: float, steps, rem_a=None, rem_b=None,
+                use_tree: bool = True):
+    """The exact hits of each step (in order), then depletion in time order across
+    the steps.  Returns a list of (hits, delta) per step and the final (rem_a, rem_b);
+    rem defaults to the weights."""
+    ra = np.array(a["w"] if rem_a is None else rem_a, dtype=np.float64, copy=True)
+    rb = np.array(b["w"] if rem_b is None else rem_b, dtype=np.float64, copy=True)
+    out = []
+    for k in steps:
+        hits, _ = (tree if use_tree else bruteforce)(a, b, k, dt, kappa)
+        t = hit_times(a, b, k, dt, kappa, hits)
+        delta, ra, rb = deplete(k, t, hits, ra, rb)
+        out.append((hits, delta))
+    return out, ra, rb

@@ -600,3 +600,64 @@ int oracle_pair_products(const oracle_beam *a, const oracle_beam *b, const uint3
   }
   return rc;
 }
+
+/* ---- depletion with chronological order (Sec. 2.2, Sec. 3.1) ----------- */
+
+int oracle_hit_times(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                     double kappa, const uint32_t *hits, int64_t n_hits, double *tstar) {
+  int rc = 0;
+  for (int64_t k = 0; k < n_hits; ++k) {
+    double out[6];
+    const int hit = oracle_pair_detail(a, hits[2 * k], b, hits[2 * k + 1], step, dt, kappa, out);
+    tstar[k] = out[3];
+    if (!hit) rc = -1;
+  }
+  return rc;
+}
+
+typedef struct {
+  int64_t step;
+  double t;
+  uint32_t i, j;
+  int64_t k; /* position in the caller's list */
+} dep_item;
+
+/* (step, t*, i, j) lexicographic; equal t* (also -0 and +0) fall to i, then j */
+static int cmp_dep(const void *x, const void *y) {
+  const dep_item *p = (const dep_item *)x, *q = (const dep_item *)y;
+  if (p->step != q->step) return p->step < q->step ? -1 : 1;
+  if (p->t < q->t) return -1;
+  if (q->t < p->t) return 1;
+  if (p->i != q->i) return p->i < q->i ? -1 : 1;
+  if (p->j != q->j) return p->j < q->j ? -1 : 1;
+  return 0;
+}
+
+int oracle_deplete(int64_t n_hits, const int64_t *step, const double *tstar,
+                   const uint32_t *hits, double *rem_a, int64_t na, double *rem_b, int64_t nb,
+                   double *delta) {
+  dep_item *it = (dep_item *)malloc(sizeof(dep_item) * (size_t)(n_hits > 0 ? n_hits : 1));
+  if (!it) return -2;
+  for (int64_t k = 0; k < n_hits; ++k) {
+    it[k].step = step[k];
+    it[k].t = tstar[k];
+    it[k].i = hits[2 * k];
+    it[k].j = hits[2 * k + 1];
+    it[k].k = k;
+    if ((int64_t)it[k].i >= na || (int64_t)it[k].j >= nb) {
+      free(it);
+      return -1;
+    }
+  }
+  qsort(it, (size_t)n_hits, sizeof(dep_item), cmp_dep);
+  /* in time order: the collision takes what both photons still hold */
+  for (int64_t q = 0; q < n_hits; ++q) {
+    const uint32_t i = it[q].i, j = it[q].j;
+    const double d = rem_a[i] < rem_b[j] ? rem_a[i] : rem_b[j];
+    rem_a[i] = rem_a[i] - d;
+    rem_b[j] = rem_b[j] - d;
+    delta[it[q].k] = d;
+  }
+  free(it);
+  return 0;
+}

@@ -67,6 +67,30 @@ int oracle_pair_products(const oracle_beam *a, const oracle_beam *b, const uint3
 /* the same CoM direction draw, exposed for tests: n[3] for (seed, i, j) */
 void oracle_com_direction(uint64_t seed, uint32_t i, uint32_t j, double n[3]);
 
+/* Depletion with chronological order (Sec. 2.2, Sec. 3.1, Fig. ChronOrder).
+ * A photon annihilates when it collides, so a collision can only happen if
+ * neither photon was used up by an earlier one; the collisions of a step are
+ * therefore taken in time order.  With macro-photons of weight w (Sec. 2.2:
+ * a swarm of w photons handled individually) a collision takes
+ * delta = min(rem_i, rem_j) from both, the number of photon pairs the two
+ * swarms can still form; with unit weights that is "the earliest hit of a
+ * photon annihilates it".  Each beam then loses exactly the pairs made
+ * (Eq. for n_I(t), n_II(t): n_I(0) - n(t)).
+ *
+ * oracle_hit_times: the closest-approach time t* (relative to t_k) of each
+ * hit (i, j) of step k, by the same definition as oracle_pair_hit; returns
+ * -1 if a listed pair is not a hit of that step (its t* is still written).
+ *
+ * oracle_deplete: the hits, each with its step, taken in (step, t*, i, j)
+ * lexicographic order; rem_a[na] and rem_b[nb] hold what each photon still
+ * holds (updated in place), delta[k] receives what hit k took.  Returns 0,
+ * -1 for an index out of range (nothing changed), -2 out of memory. */
+int oracle_hit_times(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                     double kappa, const uint32_t *hits, int64_t n_hits, double *tstar);
+int oracle_deplete(int64_t n_hits, const int64_t *step, const double *tstar,
+                   const uint32_t *hits, double *rem_a, int64_t na, double *rem_b, int64_t nb,
+                   double *delta);
+
 /* All pairs.  Hits (i, j) written as uint32 pairs in lexicographic order,
  * at most cap of them; res->count is the true number. */
 int oracle_bruteforce(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
