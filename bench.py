@@ -210,6 +210,72 @@ def pair_products_timing(col, A, B, stream, step=2, seed=2024, reps=5):
                          "bytes_per_hit": 8 + 2 * 32 + 64}}
 
 
+# Algorithmic bytes per hit of a depletion call: the t* gather (hit 8, two photons'
+# p0 and direction 96, their remaining weights 16, key/state/delta written 17), one
+# round over every hit (state 1 + hit 8 + key 8 read three times, rem 16, four slot
+# reads 24 and resets 24, delta 8) and the sum (8).  Later rounds touch the open hits
+# only and are not counted.
+DEP_BYTES_PER_HIT = (8 + 96 + 16 + 17) + (3 * 17 + 16 + 24 + 24 + 8) + 8
+
+
+def depletion_timing(col, stream, steps, peak, peak_src):
+    """Depletion in time order over a whole run (trilens_deplete_step after each
+    step's collision, unit weights, what is left carried from step to step):
+    device time of the depletion calls with CUDA events (the collisions are not
+    timed).  The run is done twice; the second is reported."""
+    import torch
+
+    from paper_1608_01125_gb300 import binding
+    dev = col.a["px"].device
+    na, nb = col.a["px"].numel(), col.b["px"].numel()
+    cap = 1 << 21
+    buf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    delta = torch.empty(cap, dtype=torch.float64, device=dev)
+    for rep in range(2):
+        ra = torch.ones(na, dtype=torch.float64, device=dev)
+        rb = torch.ones(nb, dtype=torch.float64, device=dev)
+        ms = wall = made = 0.0
+        hits = acc = 0
+        rounds = []
+        for k in steps:
+            col.build(k)
+            while True:
+                try:
+                    n = col.collide(k, buf)
+                    break
+                except binding.TrilensError as e:
+                    if e.code != binding.ERR_CAPACITY:
+                        raise
+                    cap = e.needed + 1024
+                    buf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+                    delta = torch.empty(cap, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            r = col.deplete_step(k, buf, n, ra, rb, delta)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            wall += 1e3 * (time.perf_counter() - t0)
+            ms += e0.elapsed_time(e1)
+            hits += n
+            acc += r["accepted"]
+            made += r["transferred"]
+            rounds.append(r["rounds"])
+    used = int((ra == 0).sum().item())
+    achieved = DEP_BYTES_PER_HIT * hits / (ms / 1e3) / 1e9
+    return {"time_steps": len(steps), "hits": hits, "pairs_made": acc, "transferred": made,
+            "photons_used_up_a": used, "ms_per_run": ms, "wall_ms_per_run": wall,
+            "hits_per_s": hits / (ms / 1e3), "rounds_max": max(rounds),
+            "rounds_per_step": statistics.mean(rounds),
+            "steps_with_hits": sum(1 for x in rounds if x > 0),
+            "launches_per_run": sum(4 + 3 * x for x in rounds if x > 0),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_hit": DEP_BYTES_PER_HIT}}
+
+
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -347,6 +413,8 @@ def run_ours(args, wl):
     phase_ms, launches = col.phase_ms(reset=True)
     col.timing(False)
     pairs = pair_products_timing(col, A, B, stream) if rank == 0 else None
+    depl = (depletion_timing(col, stream, list(time_steps), *read_peaks())
+            if rank == 0 and not args.no_depletion else None)
     ms = slowest_rank_ms(ms, world, dev)
     K = args.steps
     units_rank = wl.a.n * wl.b.n * nsteps * K
@@ -415,6 +483,7 @@ def run_ours(args, wl):
                      "traffic": read_traffic(dom), "algorithmic_bytes_per_launch": algo,
                      "launch_ms": launch_ms},
         "pair_products": pairs,
+        "depletion": depl,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 16},
@@ -555,6 +624,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-depletion", action="store_true",
+                    help="skip the depletion leg (run-long depletion after each step)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default knobs)")
     ap.add_argument("--photons", type=int, default=1 << 20)

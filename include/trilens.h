@@ -165,6 +165,41 @@ int trilens_run(trilens_ctx *c, int64_t first_step, int64_t steps, trilens_step_
 int trilens_pair_products(const trilens_beam *a, const trilens_beam *b, const uint32_t *hits,
                           int64_t n_hits, uint64_t seed, double *out, trilens_stream_t stream);
 
+/* Depletion with chronological order (Sec. 2.2, Sec. 3.1, Fig. ChronOrder).
+ * Photons annihilate when they collide, so a hit only produces pairs if both
+ * photons still exist when it happens.  The hits of step `step` -- hits:
+ * device, n_hits distinct (i, j) uint32 pairs as trilens_collide_step wrote
+ * them -- are taken in the order of their closest-approach time t* (then i,
+ * then j); t* is computed in FP64 with the operations of the exact decision.
+ * A macro-photon of weight w stands for w photons handled one by one, so a
+ * hit takes delta = min(rem_a[i], rem_b[j]) from both photons (with unit
+ * weights: a photon's earliest remaining hit annihilates it).
+ *
+ * rem_a (n_a doubles) and rem_b (n_b doubles): device, caller-owned, what
+ * each photon of the context's beams still holds; initialise them to the
+ * weights (or 1) before the first step and pass them unchanged from step to
+ * step, calling steps in increasing order, so that hits of earlier steps come
+ * first.  They must be >= 0.  Updated in place.  delta: device, n_hits
+ * doubles, what each hit took (in the order of `hits`), or NULL.  *n_accepted
+ * (host, may be NULL): hits with delta > 0; *transferred (host, may be NULL):
+ * the sum of delta, i.e. the pairs made (summed in a fixed order, so the
+ * value is reproducible).
+ *
+ * Runs on the context's stream and returns when the step is done (the host
+ * reads a counter after every 8 rounds of 3 kernels; a step needs as many
+ * rounds as its longest chain of hits that wait on one another).  Allocates
+ * its workspace on the first call (24 bytes per photon of both beams, 17 per
+ * hit, growing with n_hits).  INVALID (nothing changed except delta, which
+ * may hold zeros) for a NULL context, a negative step, n_hits < 0 or >= 2^32,
+ * NULL hits/rem arrays with n_hits > 0, an index out of range or a negative
+ * or NaN rem of a listed photon.  A pair listed twice is not supported. */
+int trilens_deplete_step(trilens_ctx *c, int64_t step, const uint32_t *hits, int64_t n_hits,
+                         double *rem_a, double *rem_b, double *delta, int64_t *n_accepted,
+                         double *transferred);
+
+/* Rounds the last successful trilens_deplete_step call ran (a multiple of 8). */
+int trilens_deplete_rounds(trilens_ctx *c, int64_t *rounds);
+
 /* Zero the cumulative yield. */
 int trilens_reset_yield(trilens_ctx *c);
 

@@ -152,6 +152,11 @@ def lib() -> ctypes.CDLL:
             getattr(L, "trilens_surrogate_" + f).restype = ctypes.c_int
         L.trilens_yield_reduce_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.trilens_yield_reduce_noalloc.restype = ctypes.c_int
+        L.trilens_deplete_step.argtypes = [vp, i64, vp, i64, vp, vp, vp, ctypes.POINTER(i64),
+                                           ctypes.POINTER(dbl)]
+        L.trilens_deplete_step.restype = ctypes.c_int
+        L.trilens_deplete_rounds.argtypes = [vp, ctypes.POINTER(i64)]
+        L.trilens_deplete_rounds.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -357,6 +362,35 @@ class Collider:
 
     def surrogate_load(self, path: str):
         _check(lib().trilens_surrogate_load(self.ctx, path.encode()), self.ctx)
+
+    def deplete_step(self, step: int, hits, n_hits: int, rem_a, rem_b, delta=None) -> dict:
+        """Depletion in time order of step `step`'s hits (trilens_deplete_step): hits an
+        int32 CUDA tensor holding >= 2*n_hits entries ((i, j) pairs as collide wrote them),
+        rem_a / rem_b float64 CUDA tensors (one entry per photon of beam a / b, updated in
+        place), delta an optional float64 CUDA tensor of >= n_hits entries.  Returns
+        {"accepted", "transferred", "rounds"}."""
+        n_hits = int(n_hits)
+        na, nb = int(self.a["px"].numel()), int(self.b["px"].numel())
+        for name, t, n in (("rem_a", rem_a, na), ("rem_b", rem_b, nb)):
+            if not (t.is_cuda and t.dtype == self._torch.float64 and t.is_contiguous()
+                    and t.numel() == n):
+                raise TrilensError(ERR_INVALID, f"{name}: need {n} contiguous float64 on the GPU")
+        if n_hits > 0 and not (hits.is_cuda and hits.element_size() == 4 and hits.is_contiguous()
+                               and hits.numel() >= 2 * n_hits):
+            raise TrilensError(ERR_INVALID, "hits: need >= 2*n_hits contiguous 32-bit entries")
+        if delta is not None and not (delta.is_cuda and delta.dtype == self._torch.float64
+                                      and delta.is_contiguous() and delta.numel() >= n_hits):
+            raise TrilensError(ERR_INVALID, "delta: need >= n_hits contiguous float64")
+        acc = ctypes.c_int64(0)
+        tr = ctypes.c_double(0.0)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        _check(lib().trilens_deplete_step(self.ctx, int(step), ptr(hits) if n_hits else None,
+                                          n_hits, ptr(rem_a), ptr(rem_b), ptr(delta),
+                                          ctypes.byref(acc), ctypes.byref(tr)), self.ctx)
+        r = ctypes.c_int64(0)
+        _check(lib().trilens_deplete_rounds(self.ctx, ctypes.byref(r)), self.ctx)
+        return {"accepted": int(acc.value), "transferred": float(tr.value),
+                "rounds": int(r.value) if n_hits else 0}
 
     def debug_set_spin_limit(self, limit: int):
         _check(lib().trilens_debug_set_spin_limit(self.ctx, int(limit)), self.ctx)

@@ -202,6 +202,7 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFree(c->partials);
   cudaFree(c->build_status);
   surrogate_free(c);
+  deplete_free(c);
   cudaFreeHost(c->ctr_host);
   cudaFreeHost(c->build_status_host);
   for (int k = 0; k < 2; ++k) {

@@ -11,6 +11,7 @@
 #include "trilens.h"
 
 struct SurrogateState;
+struct DepState;
 
 constexpr int kMaxLevels = 24;
 
@@ -74,6 +75,8 @@ struct trilens_ctx {
   double phase_ms[9]{};
   int64_t phase_launches[9]{};
   SurrogateState *sur = nullptr;  // learned statistical regime (tl_surrogate_host.cu)
+  DepState *dep = nullptr;        // depletion workspace (tl_deplete.cu)
+  int64_t dep_rounds = 0;         // rounds the last depletion call took
   char msg[512] = {0};
 };
 
@@ -133,4 +136,5 @@ tl::TravArgs trav_args(trilens_ctx *c, double ct);
 // hierarchies from the roots) for the built step; fills c->ctr_host
 int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, int *retries);
 void surrogate_free(trilens_ctx *c);
+void deplete_free(trilens_ctx *c);
 extern "C" int surrogate_total(trilens_ctx *c, int level, double *out);

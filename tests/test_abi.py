@@ -81,4 +81,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert pp(ctypes.byref(empty), ctypes.byref(empty), None, -1, 0, None, None) == binding.ERR_INVALID
     assert pp(ctypes.byref(empty), ctypes.byref(empty), None, 0, 0, None, None) == 0
     assert pp(ctypes.byref(empty), ctypes.byref(empty), None, 3, 0, None, None) == binding.ERR_INVALID
+    # depletion: a context is required; nothing runs without one
+    n = ctypes.c_int64(-5)
+    x = ctypes.c_double(-5.0)
+    assert lib.trilens_deplete_step(None, 0, None, 0, None, None, None, ctypes.byref(n),
+                                    ctypes.byref(x)) == binding.ERR_INVALID
+    assert lib.trilens_deplete_rounds(None, ctypes.byref(n)) == binding.ERR_INVALID
     lib.trilens_destroy(None)
