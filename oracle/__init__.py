@@ -93,6 +93,11 @@ def lib():
             L.oracle_deplete.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), pd, pu,
                                          pd, ctypes.c_int64, pd, ctypes.c_int64, pd]
             L.oracle_deplete.restype = ctypes.c_int
+            L.oracle_swarm_offset.argtypes = [ctypes.c_uint64, pd]
+            L.oracle_swarm_offset.restype = None
+            L.oracle_ip_bruteforce.argtypes = [pb, pb, d, d, ctypes.c_int64, d, d, pu,
+                                               ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+            L.oracle_ip_bruteforce.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -242,3 +247,33 @@ def deplete_run(a: dict, b: dict, dt: float, kappa: float, steps, rem_a=None, re
         delta, ra, rb = deplete(k, t, hits, ra, rb)
         out.append((hits, delta))
     return out, ra, rb
+
+
+def swarm_offset(k: int) -> np.ndarray:
+    """Offset u_k (in units of the MP's cube side) of photon k of a swarm (IP regime)."""
+    u = np.zeros(3)
+    lib().oracle_swarm_offset(ctypes.c_uint64(k), _pd(u))
+    return u
+
+
+def ip_bruteforce(a: dict, b: dict, h_a: float, h_b: float, step: int, dt: float,
+                  kappa: float, cap: int = 1 << 16):
+    """IP regime (Sec. 2.2): every real-photon pair of the two beams' swarms.
+    Returns hits[n, 4] uint32 = (MP i of a, photon k, MP j of b, photon l), sorted."""
+    A, ka = _beam(a)
+    B, kb = _beam(b)
+    count = ctypes.c_int64(0)
+    for _ in range(3):
+        hits = np.zeros((max(cap, 1), 4), dtype=np.uint32)
+        rc = lib().oracle_ip_bruteforce(ctypes.byref(A), ctypes.byref(B), float(h_a),
+                                        float(h_b), int(step), float(dt), float(kappa),
+                                        hits.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                        cap, ctypes.byref(count))
+        if rc == -1:
+            raise ValueError("IP regime: weights must be integers in [1, 2^32)")
+        if rc != 0:
+            raise MemoryError("oracle_ip_bruteforce")
+        if count.value <= cap:
+            return hits[: count.value].copy()
+        cap = int(count.value)
+    raise RuntimeError("oracle capacity loop")

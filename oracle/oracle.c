@@ -661,3 +661,92 @@ int oracle_deplete(int64_t n_hits, const int64_t *step, const double *tstar,
   free(it);
   return 0;
 }
+
+/* ---- IP regime: macro-photons split into swarms of real photons (Sec. 2.2) */
+
+/* 1/g, 1/g^2, 1/g^3 with g the real root > 1 of x^4 = x + 1 (Roberts' R_3
+ * low-discrepancy sequence), as the nearest doubles */
+static const double O_R3[3] = {0.81917251339616448, 0.67104360670378926, 0.5497004779019703};
+
+void oracle_swarm_offset(uint64_t k, double u[3]) {
+  for (int d = 0; d < 3; ++d) {
+    const double x = 0.5 + (double)k * O_R3[d];
+    u[d] = (x - floor(x)) - 0.5;
+  }
+}
+
+static int weight_ok(double w) { return w >= 1.0 && w < 4294967296.0 && w == floor(w); }
+
+typedef struct {
+  uint32_t i, k, j, l;
+} ip_hit;
+
+static int cmp_ip(const void *x, const void *y) {
+  const ip_hit *p = (const ip_hit *)x, *q = (const ip_hit *)y;
+  if (p->i != q->i) return p->i < q->i ? -1 : 1;
+  if (p->k != q->k) return p->k < q->k ? -1 : 1;
+  if (p->j != q->j) return p->j < q->j ? -1 : 1;
+  if (p->l != q->l) return p->l < q->l ? -1 : 1;
+  return 0;
+}
+
+int oracle_ip_bruteforce(const oracle_beam *a, const oracle_beam *b, double h_a, double h_b,
+                         int64_t step, double dt, double kappa, uint32_t *hits, int64_t cap,
+                         int64_t *count) {
+  for (int64_t i = 0; i < a->n; ++i)
+    if (!weight_ok(a->w[i])) return -1;
+  for (int64_t j = 0; j < b->n; ++j)
+    if (!weight_ok(b->w[j])) return -1;
+  const double ct = O_C * ((double)step * dt);
+  ip_hit *hv = NULL;
+  int64_t n = 0, hcap = 0;
+  for (int64_t i = 0; i < a->n; ++i) {
+    const double di[3] = {a->dx[i], a->dy[i], a->dz[i]};
+    for (int64_t j = 0; j < b->n; ++j) {
+      const double dj[3] = {b->dx[j], b->dy[j], b->dz[j]};
+      /* every photon of a swarm has its MP's energy and direction: the same s */
+      const double cs = di[0] * dj[0] + di[1] * dj[1] + di[2] * dj[2];
+      if (!(oracle_s(a->E[i], b->E[j], cs) > 1.0)) continue;
+      for (uint64_t k = 0; k < (uint64_t)a->w[i]; ++k) {
+        double u[3], Pi[3];
+        oracle_swarm_offset(k, u);
+        Pi[0] = (a->px[i] + h_a * u[0]) + ct * di[0];
+        Pi[1] = (a->py[i] + h_a * u[1]) + ct * di[1];
+        Pi[2] = (a->pz[i] + h_a * u[2]) + ct * di[2];
+        for (uint64_t l = 0; l < (uint64_t)b->w[j]; ++l) {
+          double v[3], Pj[3];
+          oracle_swarm_offset(l, v);
+          Pj[0] = (b->px[j] + h_b * v[0]) + ct * dj[0];
+          Pj[1] = (b->py[j] + h_b * v[1]) + ct * dj[1];
+          Pj[2] = (b->pz[j] + h_b * v[2]) + ct * dj[2];
+          if (!decide(Pi, di, a->E[i], Pj, dj, b->E[j], dt, kappa, NULL)) continue;
+          if (n == hcap) {
+            int64_t nc = hcap ? 2 * hcap : 1024;
+            ip_hit *p = (ip_hit *)realloc(hv, (size_t)nc * sizeof(ip_hit));
+            if (!p) {
+              free(hv);
+              return -2;
+            }
+            hv = p;
+            hcap = nc;
+          }
+          hv[n].i = (uint32_t)i;
+          hv[n].k = (uint32_t)k;
+          hv[n].j = (uint32_t)j;
+          hv[n].l = (uint32_t)l;
+          ++n;
+        }
+      }
+    }
+  }
+  qsort(hv, (size_t)n, sizeof(ip_hit), cmp_ip);
+  for (int64_t q = 0; q < n && q < cap; ++q) {
+    hits[4 * q] = hv[q].i;
+    hits[4 * q + 1] = hv[q].k;
+    hits[4 * q + 2] = hv[q].j;
+    hits[4 * q + 3] = hv[q].l;
+  }
+  *count = n;
+  free(hv);
+  return 0;
+}

@@ -91,6 +91,25 @@ int oracle_deplete(int64_t n_hits, const int64_t *step, const double *tstar,
                    const uint32_t *hits, double *rem_a, int64_t na, double *rem_b, int64_t nb,
                    double *delta);
 
+/* IP regime (Sec. 2.2): a macro-photon of integer weight w is a swarm of w
+ * real photons with its energy and direction, "positioned as homogeneously as
+ * possible over the volume of the MP".  The volume is an axis-aligned cube of
+ * side h (one h per beam) centred on the MP; photon k of the swarm sits at
+ * p0 + h u_k, u_k,d = frac(0.5 + k alpha_d) - 0.5 with alpha = (1/g, 1/g^2,
+ * 1/g^3), g the real root > 1 of x^4 = x + 1 (Roberts' R_3 low-discrepancy
+ * sequence), so u_0 = 0 and a weight-1 MP is its own photon.
+ *
+ * oracle_swarm_offset: u_k.
+ * oracle_ip_bruteforce: every real-photon pair (photon k of MP i of a, photon
+ * l of MP j of b) decided as oracle_pair_hit decides a pair of photons, with
+ * p0 = MP position + h u; hits written as (i, k, j, l) uint32 quadruples in
+ * lexicographic order, at most cap of them; *count is the true number.
+ * Returns -1 if a weight is not an integer in [1, 2^32), -2 out of memory. */
+void oracle_swarm_offset(uint64_t k, double u[3]);
+int oracle_ip_bruteforce(const oracle_beam *a, const oracle_beam *b, double h_a, double h_b,
+                         int64_t step, double dt, double kappa, uint32_t *hits, int64_t cap,
+                         int64_t *count);
+
 /* All pairs.  Hits (i, j) written as uint32 pairs in lexicographic order,
  * at most cap of them; res->count is the true number. */
 int oracle_bruteforce(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
