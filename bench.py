@@ -276,6 +276,55 @@ def depletion_timing(col, stream, steps, peak, peak_src):
                          "bytes_per_hit": DEP_BYTES_PER_HIT}}
 
 
+def ip_regime_timing(dev, stream, reps=3):
+    """IP regime on the 2 x 16384-MP head-on workload (mean weight 100): the marking
+    of the MPs that can collide (all MP pairs: FP32 pre-test, FP64 decision), counting
+    and writing the real photons, and the exact run over the real photons (one
+    captured graph).  Device times with CUDA events; the best of `reps` repetitions
+    after one warm-up."""
+    import torch
+
+    from paper_1608_01125_gb300 import binding
+    wl = synth.ip_headon()
+    a_np, b_np = synth.beams(wl)
+    h = synth.IP_CUBE_UM
+    A, B = binding.to_device(a_np, dev), binding.to_device(b_np, dev)
+
+    def timed(fn):
+        best, out = None, None
+        for _ in range(reps + 1):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None or ms < best else best
+        return best, out
+
+    mark_ms, marks = timed(lambda: binding.swarm_mark(A, B, h, h, wl.dt, wl.kappa, 0, wl.steps,
+                                                      stream))
+    split_ms, sp = timed(lambda: binding.swarm_split(A, B, h, h, wl.dt, wl.kappa, 0, wl.steps,
+                                                     stream))
+    na, nb = int(sp["a"]["px"].numel()), int(sp["b"]["px"].numel())
+    col = binding.Collider(sp["a"], sp["b"], wl.dt, wl.kappa, precision=binding.FP32_BAND,
+                           stream=stream)
+    run_ms, r = timed(lambda: col.run(0, wl.steps))
+    col.close()
+    pairs = wl.a.n * wl.b.n
+    return {"workload": wl.name, "macro_photons_per_beam": wl.a.n, "cube_um": h,
+            "time_steps": wl.steps, "real_photons": [na, nb],
+            "marked": [int(marks[0].sum().item()), int(marks[1].sum().item())],
+            "mark_ms": mark_ms, "split_ms": split_ms, "run_ms": run_ms,
+            "total_ms": split_ms + run_ms, "hits_per_run": r["count"],
+            "real_pair_tests_per_s": na * nb * wl.steps / ((split_ms + run_ms) / 1e3),
+            # all MP pairs are covered; most are skipped (both MPs already marked) or
+            # rejected by the FP32 pre-test, so no single arithmetic roofline applies
+            "mark_mp_pairs_per_s": pairs / (mark_ms / 1e3)}
+
+
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -415,6 +464,7 @@ def run_ours(args, wl):
     pairs = pair_products_timing(col, A, B, stream) if rank == 0 else None
     depl = (depletion_timing(col, stream, list(time_steps), *read_peaks())
             if rank == 0 and not args.no_depletion else None)
+    ipr = ip_regime_timing(dev, stream) if rank == 0 and not args.no_ip else None
     ms = slowest_rank_ms(ms, world, dev)
     K = args.steps
     units_rank = wl.a.n * wl.b.n * nsteps * K
@@ -484,6 +534,7 @@ def run_ours(args, wl):
                      "launch_ms": launch_ms},
         "pair_products": pairs,
         "depletion": depl,
+        "ip_regime": ipr,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 16},
@@ -626,6 +677,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depletion", action="store_true",
                     help="skip the depletion leg (run-long depletion after each step)")
+    ap.add_argument("--no-ip", action="store_true",
+                    help="skip the IP-regime leg (swarm split + exact run of real photons)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default knobs)")
     ap.add_argument("--photons", type=int, default=1 << 20)

@@ -200,6 +200,50 @@ int trilens_deplete_step(trilens_ctx *c, int64_t step, const uint32_t *hits, int
 /* Rounds the last successful trilens_deplete_step call ran (a multiple of 8). */
 int trilens_deplete_rounds(trilens_ctx *c, int64_t *rounds);
 
+/* IP regime (Sec. 2.2): macro-photons (MPs) of integer weight w split into
+ * swarms of w real photons when they collide.  A swarm has its MP's energy
+ * and direction; its photons are spread over the MP's volume, taken as an
+ * axis-aligned cube of side h (one h per beam, um) centred on the MP: photon
+ * k sits at p0 + h u_k, u_k,d = frac(0.5 + k alpha_d) - 0.5 with alpha =
+ * (1/g, 1/g^2, 1/g^3), g^4 = g + 1 (Roberts' R_3 low-discrepancy sequence;
+ * u_0 = 0, so a weight-1 MP is its own photon).  Every real-photon pair is
+ * then decided like a pair of single photons.  Three calls write the real
+ * photons of the MPs that can collide; the caller then runs the exact path
+ * (trilens_create on the expanded beams, trilens_run / trilens_collide_step,
+ * and trilens_deplete_step for annihilation of individual photons) and maps
+ * each hit back to (MP, photon in swarm) with the owner / index arrays.
+ *
+ * trilens_swarm_mark: mark_a (n_a bytes) and mark_b (n_b bytes), device,
+ * receive 1 for every MP that belongs to a pair which can collide in steps
+ * [first_step, first_step + steps) of dt = p->dt_fs (with kappa = p->kappa),
+ * else 0.  The test is conservative (s > 1 up to a relative 1e-9; the MP
+ * centres' closest approach within the window at most the largest collision
+ * radius plus both cubes' half-diagonals, with margins for rounding), so the
+ * marked MPs hold every real-photon hit of the run.  FP64, all MP pairs,
+ * asynchronous on `stream`.  INVALID for bad beams, h < 0, dt or kappa <= 0,
+ * first_step < 0, steps < 1, or NULL marks of non-empty beams. */
+int trilens_swarm_mark(const trilens_beam *a, const trilens_beam *b, double h_a, double h_b,
+                       const trilens_params *p, int64_t first_step, int64_t steps,
+                       uint8_t *mark_a, uint8_t *mark_b, trilens_stream_t stream);
+
+/* offsets (device, n + 1 int64): offsets[i] = the sum of the weights of the
+ * marked MPs before i, offsets[n] = *total (host) = the real photons of the
+ * marked swarms.  Weights (mp->w, NULL = all 1) must be integers in
+ * [1, 2^32): INVALID otherwise (offsets then undefined).  Returns after the
+ * stream has done it; uses stream-ordered scratch (cudaMallocAsync). */
+int trilens_swarm_count(const trilens_beam *mp, const uint8_t *mark, int64_t *offsets,
+                        int64_t *total, trilens_stream_t stream);
+
+/* Write the `total` real photons: out (host array of 8 device pointers, each
+ * `total` doubles: px py pz dx dy dz E w; out[7] may be NULL, else all 1),
+ * owner[q] = the MP of photon q and index_in_swarm[q] = its k (device uint32,
+ * `total` each).  Photons come grouped by MP in MP order, k ascending.
+ * Positions p0 + h u_k in FP64 (each product and sum rounded to nearest).
+ * Asynchronous on `stream`; allocates nothing. */
+int trilens_swarm_expand(const trilens_beam *mp, double h, const int64_t *offsets,
+                         int64_t total, double *const *out, uint32_t *owner,
+                         uint32_t *index_in_swarm, trilens_stream_t stream);
+
 /* Zero the cumulative yield. */
 int trilens_reset_yield(trilens_ctx *c);
 

@@ -157,6 +157,14 @@ def lib() -> ctypes.CDLL:
         L.trilens_deplete_step.restype = ctypes.c_int
         L.trilens_deplete_rounds.argtypes = [vp, ctypes.POINTER(i64)]
         L.trilens_deplete_rounds.restype = ctypes.c_int
+        L.trilens_swarm_mark.argtypes = [ctypes.POINTER(Beam), ctypes.POINTER(Beam), dbl, dbl,
+                                         ctypes.POINTER(Params), i64, i64, vp, vp, vp]
+        L.trilens_swarm_mark.restype = ctypes.c_int
+        L.trilens_swarm_count.argtypes = [ctypes.POINTER(Beam), vp, vp, ctypes.POINTER(i64), vp]
+        L.trilens_swarm_count.restype = ctypes.c_int
+        L.trilens_swarm_expand.argtypes = [ctypes.POINTER(Beam), dbl, vp, i64,
+                                           ctypes.POINTER(vp), vp, vp, vp]
+        L.trilens_swarm_expand.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -476,6 +484,62 @@ def pair_products(beam_a: dict, beam_b: dict, hits, seed: int, out=None, stream=
                                        ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF),
                                        ctypes.c_void_p(out.data_ptr()),
                                        ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
+def swarm_mark(mp_a: dict, mp_b: dict, h_a: float, h_b: float, dt_fs: float, kappa: float,
+               first_step: int, steps: int, stream=None):
+    """trilens_swarm_mark: uint8 CUDA tensors (mark_a, mark_b), 1 for the
+    macro-photons of pairs that can collide in the given steps."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ba, bb = beam_struct(mp_a), beam_struct(mp_b)
+    dev = mp_a["px"].device
+    na, nb = int(mp_a["px"].numel()), int(mp_b["px"].numel())
+    mark_a = torch.zeros(max(na, 1), dtype=torch.uint8, device=dev)
+    mark_b = torch.zeros(max(nb, 1), dtype=torch.uint8, device=dev)
+    params = Params(float(dt_fs), float(kappa), FP32_BAND, 0, 0, 0, 0)
+    _check(lib().trilens_swarm_mark(ctypes.byref(ba), ctypes.byref(bb), float(h_a), float(h_b),
+                                    ctypes.byref(params), int(first_step), int(steps),
+                                    ctypes.c_void_p(mark_a.data_ptr()),
+                                    ctypes.c_void_p(mark_b.data_ptr()),
+                                    ctypes.c_void_p(st.cuda_stream)))
+    return mark_a[:na], mark_b[:nb]
+
+
+def swarm_split(mp_a: dict, mp_b: dict, h_a: float, h_b: float, dt_fs: float, kappa: float,
+                first_step: int, steps: int, stream=None) -> dict:
+    """IP regime (trilens_swarm_mark / _count / _expand): the real photons of the
+    macro-photons that can collide in the given steps.  mp_a / mp_b: beams of MPs
+    (device tensors, integer weights); h_a / h_b: the MPs' cube sides [um].
+    Returns {"a", "b": the real-photon beams (device tensors, weight 1),
+    "owner_a", "k_a", "owner_b", "k_b": int32 tensors mapping each real photon to
+    its MP and its index in the swarm, "mark_a", "mark_b": uint8 tensors}."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    sp = ctypes.c_void_p(st.cuda_stream)
+    ba, bb = beam_struct(mp_a), beam_struct(mp_b)
+    dev = mp_a["px"].device
+    mark_a, mark_b = swarm_mark(mp_a, mp_b, h_a, h_b, dt_fs, kappa, first_step, steps, st)
+    out = {"mark_a": mark_a, "mark_b": mark_b}
+    for side, mp, bs, mark, h in (("a", mp_a, ba, mark_a, h_a), ("b", mp_b, bb, mark_b, h_b)):
+        n = int(mp["px"].numel())
+        off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        total = ctypes.c_int64(0)
+        _check(lib().trilens_swarm_count(ctypes.byref(bs), ctypes.c_void_p(mark.data_ptr()),
+                                         ctypes.c_void_p(off.data_ptr()), ctypes.byref(total), sp))
+        m = int(total.value)
+        beam = {k: torch.empty(m, dtype=torch.float64, device=dev) for k in BEAM_KEYS}
+        owner = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        kof = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+        ptrs = (ctypes.c_void_p * 8)(*[ctypes.c_void_p(beam[k].data_ptr() if m else None)
+                                       for k in BEAM_KEYS])
+        _check(lib().trilens_swarm_expand(ctypes.byref(bs), float(h), ctypes.c_void_p(off.data_ptr()),
+                                          m, ptrs, ctypes.c_void_p(owner.data_ptr()),
+                                          ctypes.c_void_p(kof.data_ptr()), sp))
+        out[side] = beam
+        out["owner_" + side] = owner[:m]
+        out["k_" + side] = kof[:m]
     return out
 
 

@@ -79,6 +79,9 @@ static double host_sigma_max() {
   return host_sigma(0.5 * (lo + hi));
 }
 
+// an upper bound of Eq. BWcross over s (for conservative tests elsewhere)
+double tl_sigma_max_bound() { return host_sigma_max() * (1.0 + 1e-6); }
+
 static float round_up(double x) {
   float f = (float)x;
   if ((double)f < x) f = nextafterf(f, INFINITY);

@@ -137,4 +137,5 @@ tl::TravArgs trav_args(trilens_ctx *c, double ct);
 int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, int *retries);
 void surrogate_free(trilens_ctx *c);
 void deplete_free(trilens_ctx *c);
+double tl_sigma_max_bound();
 extern "C" int surrogate_total(trilens_ctx *c, int level, double *out);

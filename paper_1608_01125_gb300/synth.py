@@ -32,7 +32,7 @@ class BeamSpec:
     sigma_l: float  # longitudinal sigma in the beam frame [um]
     divergence: float  # rms angle per transverse axis [rad]
     energy: tuple  # ("lognormal", median, sigma_ln) | ("gamma", shape, scale)
-    weight: tuple = ("const", 1.0)  # ("const", w) | ("uniform", lo, hi)
+    weight: tuple = ("const", 1.0)  # ("const", w) | ("uniform", lo, hi) | ("integers", lo, hi)
 
 
 @dataclasses.dataclass(frozen=True)
@@ -90,6 +90,8 @@ def _draw_beam(rng: np.random.Generator, spec: BeamSpec, crossing: float,
         raise ValueError(kind)
     if spec.weight[0] == "const":
         w = np.full(n, float(spec.weight[1]))
+    elif spec.weight[0] == "integers":  # macro-photons of the IP regime: lo..hi photons
+        w = rng.integers(int(spec.weight[1]), int(spec.weight[2]) + 1, n).astype(np.float64)
     else:
         w = rng.uniform(spec.weight[1], spec.weight[2], n)
     out = {}
@@ -181,6 +183,20 @@ def fixed_energy_headon(n: int, energy: float, seed: int, sigma_t: float = 1.0,
     """Zero divergence, one fixed energy: the case with a closed-form yield."""
     s = _spec(n, (sigma_t, sigma_t), sigma_l, 0.0, ("const", energy))
     return Workload("fixed_energy_headon", s, s, 0.0, offset, dt, 1, kappa, seed)
+
+
+#: side of a macro-photon's cube [um] in the IP-regime workload
+IP_CUBE_UM = 0.5
+
+
+def ip_headon(n_mp: int = 16384, w_lo: int = 1, w_hi: int = 199, seed: int = 0) -> Workload:
+    """IP regime: 2 x 16384 macro-photons of 1..199 photons each (mean 100, so
+    about 1.64e6 real photons per beam), each spread over a cube of side
+    IP_CUBE_UM; otherwise the 2 x 1M head-on beams (sigma = (1, 1, 10) um,
+    5 mrad, log-normal energies with median 5 MeV, 64 steps of 5 fs, kappa 1e14).
+    """
+    s = _spec(n_mp, (1.0, 1.0), 10.0, 5e-3, ("lognormal", 5.0, 0.5), ("integers", w_lo, w_hi))
+    return Workload(f"ip_headon_2x{n_mp}", s, s, 0.0, 3.0, 5.0, 64, 1e14, seed)
 
 
 WORKLOADS = {

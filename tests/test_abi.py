@@ -87,4 +87,23 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.trilens_deplete_step(None, 0, None, 0, None, None, None, ctypes.byref(n),
                                     ctypes.byref(x)) == binding.ERR_INVALID
     assert lib.trilens_deplete_rounds(None, ctypes.byref(n)) == binding.ERR_INVALID
+    # swarm split (IP regime): bad beams, sizes or parameters never reach the device
+    P = binding.Params(10.0, 1e16, 0, 0, 0, 0, 0)
+    sm = lib.trilens_swarm_mark
+    assert sm(None, ctypes.byref(empty), 0.1, 0.1, ctypes.byref(P), 0, 1, None, None,
+              None) == binding.ERR_INVALID
+    assert sm(ctypes.byref(empty), ctypes.byref(empty), -0.1, 0.1, ctypes.byref(P), 0, 1, None,
+              None, None) == binding.ERR_INVALID
+    assert sm(ctypes.byref(empty), ctypes.byref(empty), 0.1, 0.1, ctypes.byref(P), 0, 0, None,
+              None, None) == binding.ERR_INVALID
+    assert sm(ctypes.byref(missing), ctypes.byref(empty), 0.1, 0.1, ctypes.byref(P), 0, 1, None,
+              None, None) == binding.ERR_INVALID
+    assert lib.trilens_swarm_count(ctypes.byref(bad_n), None, None, ctypes.byref(n),
+                                   None) == binding.ERR_INVALID
+    assert lib.trilens_swarm_count(ctypes.byref(empty), None, None, ctypes.byref(n),
+                                   None) == binding.ERR_INVALID
+    assert lib.trilens_swarm_expand(ctypes.byref(empty), -1.0, None, 0, None, None, None,
+                                    None) == binding.ERR_INVALID
+    assert lib.trilens_swarm_expand(ctypes.byref(empty), 0.5, None, 0, None, None, None,
+                                    None) == binding.ERR_INVALID
     lib.trilens_destroy(None)
