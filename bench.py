@@ -218,11 +218,13 @@ def pair_products_timing(col, A, B, stream, step=2, seed=2024, reps=5):
 DEP_BYTES_PER_HIT = (8 + 96 + 16 + 17) + (3 * 17 + 16 + 24 + 24 + 8) + 8
 
 
-def depletion_timing(col, stream, steps, peak, peak_src):
+def depletion_timing(col, stream, steps, peak, peak_src, host=None):
     """Depletion in time order over a whole run (trilens_deplete_step after each
     step's collision, unit weights, what is left carried from step to step):
     device time of the depletion calls with CUDA events (the collisions are not
-    timed).  The run is done twice; the second is reported."""
+    timed).  The run is done twice; the second is reported.  With host = (beam a,
+    beam b, dt, kappa) as numpy, the oracle then depletes the same hit lists on the
+    host cores (timed, and its pairs compared with the GPU's)."""
     import torch
 
     from paper_1608_01125_gb300 import binding
@@ -237,6 +239,7 @@ def depletion_timing(col, stream, steps, peak, peak_src):
         ms = wall = made = 0.0
         hits = acc = 0
         rounds = []
+        lists = []
         for k in steps:
             col.build(k)
             while True:
@@ -263,25 +266,47 @@ def depletion_timing(col, stream, steps, peak, peak_src):
             acc += r["accepted"]
             made += r["transferred"]
             rounds.append(r["rounds"])
+            if rep == 1 and host is not None:
+                lists.append(buf[:n].cpu().numpy().view(np.uint32).copy())
     used = int((ra == 0).sum().item())
+    cpu = None
+    if host is not None:
+        import oracle
+        a_np, b_np, dt, kappa = host
+        o_ra, o_rb = np.ones(na), np.ones(nb)
+        o_made = 0
+        t0 = time.perf_counter()
+        for k, h in zip(steps, lists):
+            t = oracle.hit_times(a_np, b_np, k, dt, kappa, h)
+            d, o_ra, o_rb = oracle.deplete(k, t, h, o_ra, o_rb)
+            o_made += int((d > 0).sum())
+        cpu_s = time.perf_counter() - t0
+        cpu = {"kind": "oracle", "cores": 1, "ms_per_run": 1e3 * cpu_s,
+               "hits_per_s": hits / cpu_s, "pairs_made": o_made, "equal_to_gpu": o_made == acc,
+               "sample": "the same run's hit lists, every step (t* of every hit, then the "
+                         "time-ordered sweep)"}
     achieved = DEP_BYTES_PER_HIT * hits / (ms / 1e3) / 1e9
     return {"time_steps": len(steps), "hits": hits, "pairs_made": acc, "transferred": made,
             "photons_used_up_a": used, "ms_per_run": ms, "wall_ms_per_run": wall,
             "hits_per_s": hits / (ms / 1e3), "rounds_max": max(rounds),
-            "rounds_per_step": statistics.mean(rounds),
+            "rounds_per_step_with_hits": statistics.mean([x for x in rounds if x > 0] or [0]),
             "steps_with_hits": sum(1 for x in rounds if x > 0),
-            "launches_per_run": sum(4 + 3 * x for x in rounds if x > 0),
+            # init, clear, two sums, and batches of 8 rounds of 3 kernels
+            "launches_per_run": sum(4 + 24 * math.ceil(x / 8) for x in rounds if x > 0),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                         "bytes_per_hit": DEP_BYTES_PER_HIT}}
+                         "bytes_per_hit": DEP_BYTES_PER_HIT},
+            "cpu_baseline": cpu}
 
 
-def ip_regime_timing(dev, stream, reps=3):
+def ip_regime_timing(dev, stream, reps=3, cpu=True):
     """IP regime on the 2 x 16384-MP head-on workload (mean weight 100): the marking
     of the MPs that can collide (all MP pairs: FP32 pre-test, FP64 decision), counting
     and writing the real photons, and the exact run over the real photons (one
     captured graph).  Device times with CUDA events; the best of `reps` repetitions
-    after one warm-up."""
+    after one warm-up.  With cpu, the oracle decides every real-photon pair of 64 MP
+    pairs sampled from the marked ones at the collision-peak step (timed on one host
+    core)."""
     import torch
 
     from paper_1608_01125_gb300 import binding
@@ -314,6 +339,22 @@ def ip_regime_timing(dev, stream, reps=3):
     run_ms, r = timed(lambda: col.run(0, wl.steps))
     col.close()
     pairs = wl.a.n * wl.b.n
+    cpu_line = None
+    if cpu:
+        import oracle
+        ma = np.nonzero(marks[0].cpu().numpy())[0]
+        mb = np.nonzero(marks[1].cpu().numpy())[0]
+        rng = np.random.default_rng(7)
+        ia, jb = rng.choice(ma, 64), rng.choice(mb, 64)
+        sub = lambda beam, i: {k: v[i:i + 1].copy() for k, v in beam.items()}  # noqa: E731
+        tests = 0
+        t0 = time.perf_counter()
+        for i, j in zip(ia, jb):
+            oracle.ip_bruteforce(sub(a_np, i), sub(b_np, j), h, h, 2, wl.dt, wl.kappa)
+            tests += int(a_np["w"][i]) * int(b_np["w"][j])
+        cpu_s = time.perf_counter() - t0
+        cpu_line = {"kind": "oracle", "cores": 1, "real_pair_tests_per_s": tests / cpu_s,
+                    "sample": f"64 marked MP pairs at step 2, {tests} real-photon pairs"}
     return {"workload": wl.name, "macro_photons_per_beam": wl.a.n, "cube_um": h,
             "time_steps": wl.steps, "real_photons": [na, nb],
             "marked": [int(marks[0].sum().item()), int(marks[1].sum().item())],
@@ -322,7 +363,8 @@ def ip_regime_timing(dev, stream, reps=3):
             "real_pair_tests_per_s": na * nb * wl.steps / ((split_ms + run_ms) / 1e3),
             # all MP pairs are covered; most are skipped (both MPs already marked) or
             # rejected by the FP32 pre-test, so no single arithmetic roofline applies
-            "mark_mp_pairs_per_s": pairs / (mark_ms / 1e3)}
+            "mark_mp_pairs_per_s": pairs / (mark_ms / 1e3),
+            "cpu_baseline": cpu_line}
 
 
 def run_reference(args, wl):
@@ -462,9 +504,11 @@ def run_ours(args, wl):
     phase_ms, launches = col.phase_ms(reset=True)
     col.timing(False)
     pairs = pair_products_timing(col, A, B, stream) if rank == 0 else None
-    depl = (depletion_timing(col, stream, list(time_steps), *read_peaks())
+    depl = (depletion_timing(col, stream, list(time_steps), *read_peaks(),
+                             host=None if args.no_cpu_baseline else (a_np, b_np, wl.dt, wl.kappa))
             if rank == 0 and not args.no_depletion else None)
-    ipr = ip_regime_timing(dev, stream) if rank == 0 and not args.no_ip else None
+    ipr = (ip_regime_timing(dev, stream, cpu=not args.no_cpu_baseline)
+           if rank == 0 and not args.no_ip else None)
     ms = slowest_rank_ms(ms, world, dev)
     K = args.steps
     units_rank = wl.a.n * wl.b.n * nsteps * K

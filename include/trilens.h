@@ -197,7 +197,9 @@ int trilens_deplete_step(trilens_ctx *c, int64_t step, const uint32_t *hits, int
                          double *rem_a, double *rem_b, double *delta, int64_t *n_accepted,
                          double *transferred);
 
-/* Rounds the last successful trilens_deplete_step call ran (a multiple of 8). */
+/* Rounds that had open hits in the last successful trilens_deplete_step call
+ * (the longest chain of hits waiting on one another; the kernels run in
+ * batches of 8 rounds). */
 int trilens_deplete_rounds(trilens_ctx *c, int64_t *rounds);
 
 /* IP regime (Sec. 2.2): macro-photons (MPs) of integer weight w split into

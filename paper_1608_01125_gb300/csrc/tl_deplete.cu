@@ -20,8 +20,9 @@
 //   R3  a hit holding both minima at both photons is resolved; the others
 //       clear the other round's slots of their photons and are counted.
 // The globally earliest unresolved hit is always resolved, so a step of n
-// hits needs at most n rounds; the host runs rounds in batches and reads the
-// count after each batch.  No kernel waits on another block.
+// hits needs at most n rounds; the host runs rounds in batches of 8 and reads
+// the count after each batch (rounds after the last one with open hits return
+// at once).  No kernel waits on another block.
 //
 // t* is computed with the operations of the exact decision (FP64, explicit
 // round-to-nearest), so the order is the one the FP64 definition gives.
@@ -47,7 +48,8 @@ struct DepArgs {
   double *rem_a, *rem_b;
   unsigned long long *tA[2], *tB[2];
   unsigned *pA[2], *pB[2];
-  int *ctr;  // [0], [1]: hits left open after a round (by round parity); [2]: bad input
+  int *ctr;  // [0], [1]: hits left open after a round (by round parity); [2]: bad input;
+             // [3]: rounds that had open hits
 };
 
 // t* of input photons i of A and j of B at c t_k = ct: the operations of the
@@ -96,9 +98,13 @@ __global__ void __launch_bounds__(kThreads) k_dep_init(DepArgs g) {
 }
 
 // R1: used-up photons; minimum time key at both photons
-__global__ void __launch_bounds__(kThreads) k_dep_min_time(DepArgs g, int r) {
+__global__ void __launch_bounds__(kThreads) k_dep_min_time(DepArgs g, int r, int round) {
+  if (g.ctr[2]) return;  // bad input: no round changes anything
   const int prev = g.ctr[(r + 1) & 1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) g.ctr[r & 1] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    g.ctr[r & 1] = 0;
+    if (prev) g.ctr[3] = round + 1;
+  }
   if (prev == 0) return;
   const int b = r & 1;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n;
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_dep_min_time(DepArgs g, int r) {
 
 // R2: among the hits at the minimum time of a photon, the smallest partner
 __global__ void __launch_bounds__(kThreads) k_dep_min_partner(DepArgs g, int r) {
-  if (g.ctr[(r + 1) & 1] == 0) return;
+  if (g.ctr[2] || g.ctr[(r + 1) & 1] == 0) return;
   const int b = r & 1;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n;
        e += (long long)gridDim.x * blockDim.x) {
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_dep_min_partner(DepArgs g, int r) 
 
 // R3: resolve the hits that are earliest at both photons
 __global__ void __launch_bounds__(kThreads) k_dep_resolve(DepArgs g, int r) {
-  if (g.ctr[(r + 1) & 1] == 0) return;
+  if (g.ctr[2] || g.ctr[(r + 1) & 1] == 0) return;
   const int b = r & 1, nb = b ^ 1;
   int open = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.n;
@@ -363,23 +369,22 @@ static int dep_run(trilens_ctx *c, int64_t step, const uint32_t *hits, int64_t n
   CK(cudaMemsetAsync(d.ctr, 0, 4 * sizeof(int), s));
   k_dep_init<<<blocks, kThreads, 0, s>>>(g);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(d.ctr_host, d.ctr, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  if (d.ctr_host[2])
-    return fail(c, TRILENS_ERR_INVALID,
-                "deplete: a hit index is out of range or a remaining weight is negative or NaN");
-  // rounds, in batches; at most n_hits rounds have work
+  // rounds, in batches; at most n_hits rounds have work.  Bad input (found by
+  // the init) stops every round kernel, and is reported after the first batch.
   int64_t r = 0;
   const int64_t max_rounds = n_hits + kRoundsPerBatch;
   for (;;) {
     for (int q = 0; q < kRoundsPerBatch; ++q, ++r) {
-      k_dep_min_time<<<blocks, kThreads, 0, s>>>(g, (int)(r & 1));
+      k_dep_min_time<<<blocks, kThreads, 0, s>>>(g, (int)(r & 1), (int)std::min<int64_t>(r, 1 << 30));
       k_dep_min_partner<<<blocks, kThreads, 0, s>>>(g, (int)(r & 1));
       k_dep_resolve<<<blocks, kThreads, 0, s>>>(g, (int)(r & 1));
     }
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(d.ctr_host, d.ctr, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(d.ctr_host, d.ctr, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (d.ctr_host[2])
+      return fail(c, TRILENS_ERR_INVALID,
+                  "deplete: a hit index is out of range or a remaining weight is negative or NaN");
     if (d.ctr_host[(r - 1) & 1] == 0) break;
     if (r >= max_rounds) {
       d.dirty = true;
@@ -402,7 +407,7 @@ static int dep_run(trilens_ctx *c, int64_t step, const uint32_t *hits, int64_t n
     memcpy(&cnt, &d.res_host[1], sizeof cnt);
     *n_accepted = (int64_t)cnt;
   }
-  if (rounds_out) *rounds_out = r;
+  if (rounds_out) *rounds_out = d.ctr_host[3];
   return TRILENS_OK;
 }
 

@@ -106,7 +106,7 @@ def test_small_headon_run(weights):
         wa, wb = rng.lognormal(0, 1, len(a["E"])), rng.lognormal(0, 1, len(b["E"]))
     info, ra, rb = run_both(a, b, wl.dt, wl.kappa, [0, 1, 2], wa, wb)
     assert sum(x["hits"] for x in info) > 10000
-    assert max(x["rounds"] for x in info) >= 8
+    assert max(x["rounds"] for x in info) >= 2  # hits that wait on earlier ones
     if weights == "unit":  # every photon at most once
         assert ((ra == 0) | (ra == 1)).all()
         assert (ra == 0).sum() == sum(x["accepted"] for x in info) == (rb == 0).sum()
@@ -198,5 +198,5 @@ def test_edges():
         assert np.array_equal(ra.cpu().numpy(), ra_ref)
         # every photon used up: the same hits again take nothing
         r = col.deplete_step(0, hits, len(h), torch.zeros_like(ra), torch.zeros_like(rb), delta)
-        assert r["accepted"] == 0 and r["transferred"] == 0.0 and r["rounds"] == 8
+        assert r["accepted"] == 0 and r["transferred"] == 0.0 and r["rounds"] == 1
         assert (delta == 0).all()
