@@ -436,10 +436,14 @@ int trilens_surrogate_load(trilens_ctx *c, const char *path);
  *
  * Reduces a hit list -- hits: device, 2 * n_hits uint32 (i_A, j_B) pairs as
  * written by trilens_collide_step -- with the weights w_a, w_b (device FP64
- * arrays indexed by i_A and j_B; NULL means weight 1) to the same four values
+ * arrays indexed by i_A and j_B; NULL means weight 1) to the four values
  * trilens_collide_step reports for a step: out_result (device, 32 bytes) =
  * { uint64 count, double sum of w_i w_j, uint64 checksum sum, uint64
- * checksum xor } (see trilens_step_stats).  Asynchronous on `stream`.
+ * checksum xor } (see trilens_step_stats).  Count and checksums are
+ * bit-identical to the step's; the weighted sum equals it up to rounding
+ * (the terms are added in another order).  Asynchronous on `stream`.
+ * hits and out_result must be 8-byte aligned (TRILENS_ERR_INVALID
+ * otherwise, before anything is launched).
  *
  * Scratch lives in a fixed 128 KiB device array inside the library (held on
  * every GPU that loads it until the process exits), so n_hits is limited to

@@ -15,82 +15,46 @@
 // library holds this array until the process exits.  Every call shares it:
 // calls that overlap on the GPU race with each other.  The completion
 // counter is cleared at the start of every call.
+#include <stdint.h>
+
 #include <mutex>
 
-#include "tl_common.cuh"
+#include "tl_yield.cuh"
 #include "trilens.h"
 
 namespace {
 
-constexpr int kChunk = 65536;
-constexpr int kMaxChunks = 4096;  // TRILENS_NOALLOC_MAX_HITS / kChunk
-constexpr int kThreads = 256;
+using tl::YieldPartial;
 
-struct NaPartial {
-  unsigned long long count;
-  double weighted;
-  unsigned long long hsum, hxor;
-};
+constexpr int kChunk = 65536;
+constexpr int kMaxChunks = 4096;
+constexpr int kThreads = 256;
+static_assert((long long)kMaxChunks * kChunk == TRILENS_NOALLOC_MAX_HITS,
+              "the scratch array must hold one partial per chunk of the largest list");
 
 struct NaScratch {
-  NaPartial part[kMaxChunks];
+  YieldPartial part[kMaxChunks];
   unsigned int done;
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NaScratch)];
 
-__device__ __forceinline__ unsigned long long na_mix(unsigned long long x) {
-  // splitmix64 finaliser (Steele, Lea & Flood 2014; Vigna's constants)
-  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ void na_add(NaPartial &a, const NaPartial &b) {
-  a.count += b.count;
-  a.weighted += b.weighted;
-  a.hsum += b.hsum;
-  a.hxor ^= b.hxor;
-}
-
-__device__ NaPartial na_block_reduce(NaPartial p, NaPartial *sp) {
-  for (int off = 16; off; off >>= 1) {
-    NaPartial o;
-    o.count = __shfl_xor_sync(0xffffffffu, p.count, off);
-    o.weighted = __shfl_xor_sync(0xffffffffu, p.weighted, off);
-    o.hsum = __shfl_xor_sync(0xffffffffu, p.hsum, off);
-    o.hxor = __shfl_xor_sync(0xffffffffu, p.hxor, off);
-    na_add(p, o);
-  }
-  if ((threadIdx.x & 31) == 0) sp[threadIdx.x >> 5] = p;
-  __syncthreads();
-  NaPartial b = sp[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) na_add(b, sp[w]);
-  __syncthreads();
-  return b;
-}
-
 // One block per chunk of hits; the last block to finish adds the chunk
-// partials in chunk order and writes the result.
+// partials in a fixed order (strided over its threads, then the block's
+// fixed-order reduction) and writes the result.
 __global__ void __launch_bounds__(kThreads) k_yield_noalloc(NaScratch *sc, const uint2 *hits,
                                                             int64_t n, const double *wA,
-                                                            const double *wB, NaPartial *out) {
-  __shared__ NaPartial sp[kThreads / 32];
+                                                            const double *wB, YieldPartial *out) {
+  __shared__ YieldPartial sp[kThreads / 32];
   __shared__ bool last;
   const int64_t lo = (int64_t)blockIdx.x * kChunk;
   const int64_t hi = lo + kChunk < n ? lo + kChunk : n;
-  NaPartial p = {0ull, 0.0, 0ull, 0ull};
+  YieldPartial p = tl::yield_zero();
   for (int64_t i = lo + threadIdx.x; i < hi; i += kThreads) {
     const uint2 h = hits[i];
-    const double wi = wA ? wA[h.x] : 1.0, wj = wB ? wB[h.y] : 1.0;
-    p.count += 1ull;
-    p.weighted += wi * wj;
-    const unsigned long long m = na_mix(((unsigned long long)h.x << 32) | h.y);
-    p.hsum += m;
-    p.hxor ^= m;
+    tl::yield_hit(p, h.x, h.y, wA ? wA[h.x] : 1.0, wB ? wB[h.y] : 1.0);
   }
-  const NaPartial b = na_block_reduce(p, sp);
+  const YieldPartial b = tl::yield_block_reduce(p, sp);
   if (threadIdx.x == 0) {
     sc->part[blockIdx.x] = b;
     __threadfence();
@@ -99,17 +63,10 @@ __global__ void __launch_bounds__(kThreads) k_yield_noalloc(NaScratch *sc, const
   __syncthreads();
   if (!last) return;
   __threadfence();
-  NaPartial t = {0ull, 0.0, 0ull, 0ull};
-  for (unsigned q = threadIdx.x; q < gridDim.x; q += kThreads) {
-    const volatile NaPartial *v = sc->part + q;
-    NaPartial o;
-    o.count = v->count;
-    o.weighted = v->weighted;
-    o.hsum = v->hsum;
-    o.hxor = v->hxor;
-    na_add(t, o);
-  }
-  const NaPartial tot = na_block_reduce(t, sp);
+  YieldPartial t = tl::yield_zero();
+  for (unsigned q = threadIdx.x; q < gridDim.x; q += kThreads)
+    tl::yield_add(t, tl::yield_load_volatile(sc->part + q));
+  const YieldPartial tot = tl::yield_block_reduce(t, sp);
   if (threadIdx.x == 0) *out = tot;
 }
 
@@ -141,6 +98,9 @@ extern "C" int trilens_yield_reduce_noalloc(const uint32_t *hits, int64_t n_hits
                                             void *out_result, trilens_stream_t stream) {
   if (n_hits < 0 || n_hits > (int64_t)TRILENS_NOALLOC_MAX_HITS) return TRILENS_ERR_INVALID;
   if (!out_result || (n_hits > 0 && !hits)) return TRILENS_ERR_INVALID;
+  // the kernel reads hits as 8-byte pairs and writes one 32-byte result of
+  // 8-byte fields: a misaligned pointer would fault in the caller's context
+  if (((uintptr_t)hits & 7u) || ((uintptr_t)out_result & 7u)) return TRILENS_ERR_INVALID;
   NaScratch *sc = nullptr;
   if (scratch_for_current_device(&sc) != cudaSuccess) return TRILENS_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -149,6 +109,6 @@ extern "C" int trilens_yield_reduce_noalloc(const uint32_t *hits, int64_t n_hits
   const int64_t blocks = n_hits > 0 ? (n_hits + kChunk - 1) / kChunk : 1;
   k_yield_noalloc<<<(unsigned)blocks, kThreads, 0, s>>>(
       sc, reinterpret_cast<const uint2 *>(hits), n_hits, w_a, w_b,
-      reinterpret_cast<NaPartial *>(out_result));
+      reinterpret_cast<YieldPartial *>(out_result));
   return cudaGetLastError() == cudaSuccess ? TRILENS_OK : TRILENS_ERR_CUDA;
 }

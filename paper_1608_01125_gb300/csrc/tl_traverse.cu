@@ -17,6 +17,7 @@
 #include "tl_common.cuh"
 #include "tl_exact.cuh"
 #include "tl_narrow.cuh"
+#include "tl_yield.cuh"
 
 namespace tl {
 
@@ -548,59 +549,20 @@ __global__ void __launch_bounds__(256) k_band(TravArgs a) {
 
 // ------------------------------------------------------------ yield
 
-// splitmix64 (Steele, Lea & Flood 2014; Vigna's constants)
-
-struct Partial {
-  unsigned long long count;
-  double weighted;
-  unsigned long long hsum, hxor;
-};
-
-__device__ __forceinline__ void padd(Partial &a, const Partial &b) {
-  a.count += b.count;
-  a.weighted += b.weighted;
-  a.hsum += b.hsum;
-  a.hxor ^= b.hxor;
-}
-
-// fixed-order block reduction (warp xor-tree, then warps in order)
-__device__ __forceinline__ Partial block_reduce(Partial p, Partial *sp) {
-  for (int off = 16; off; off >>= 1) {
-    Partial o;
-    o.count = __shfl_xor_sync(0xffffffffu, p.count, off);
-    o.weighted = __shfl_xor_sync(0xffffffffu, p.weighted, off);
-    o.hsum = __shfl_xor_sync(0xffffffffu, p.hsum, off);
-    o.hxor = __shfl_xor_sync(0xffffffffu, p.hxor, off);
-    padd(p, o);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sp[warp] = p;
-  __syncthreads();
-  Partial b = sp[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) padd(b, sp[w]);
-  __syncthreads();
-  return b;
-}
-
 // Sum over the step's hits of w_i w_j (FP64), the count and the order-free
 // checksums.  Per-block partials are combined by the last block to finish,
 // in a fixed order.
-__global__ void __launch_bounds__(256) k_yield(TravArgs a, Partial *partials) {
-  __shared__ Partial sp[8];
+__global__ void __launch_bounds__(256) k_yield(TravArgs a, YieldPartial *partials) {
+  __shared__ YieldPartial sp[8];
   __shared__ bool last;
   const unsigned long long n = min(a.ctr->hits, a.hit_cap);
-  Partial p = {0ull, 0.0, 0ull, 0ull};
+  YieldPartial p = yield_zero();
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const uint2 h = a.hits[i];
-    const double wi = a.mA.w ? a.mA.w[h.x] : 1.0, wj = a.mB.w ? a.mB.w[h.y] : 1.0;
-    p.count += 1ull;
-    p.weighted += wi * wj;
-    const unsigned long long hm = smix64(((unsigned long long)h.x << 32) | h.y);
-    p.hsum += hm;
-    p.hxor ^= hm;
+    yield_hit(p, h.x, h.y, a.mA.w ? a.mA.w[h.x] : 1.0, a.mB.w ? a.mB.w[h.y] : 1.0);
   }
-  const Partial b = block_reduce(p, sp);
+  const YieldPartial b = yield_block_reduce(p, sp);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = b;
     __threadfence();
@@ -609,17 +571,9 @@ __global__ void __launch_bounds__(256) k_yield(TravArgs a, Partial *partials) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  Partial t = {0ull, 0.0, 0ull, 0ull};
-  for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) {
-    const volatile Partial *v = partials + q;
-    Partial o;
-    o.count = v->count;
-    o.weighted = v->weighted;
-    o.hsum = v->hsum;
-    o.hxor = v->hxor;
-    padd(t, o);
-  }
-  const Partial tot = block_reduce(t, sp);
+  YieldPartial t = yield_zero();
+  for (unsigned q = threadIdx.x; q < gridDim.x; q += blockDim.x) yield_add(t, yield_load_volatile(partials + q));
+  const YieldPartial tot = yield_block_reduce(t, sp);
   if (threadIdx.x == 0) {
     a.ctr->count = tot.count;
     a.ctr->weighted = tot.weighted;
@@ -726,11 +680,11 @@ cudaError_t launch_band(const TravArgs &a, int blocks, cudaStream_t s) {
 }
 
 cudaError_t launch_yield(const TravArgs &a, void *partials, int blocks, cudaStream_t s) {
-  k_yield<<<blocks, 256, 0, s>>>(a, reinterpret_cast<Partial *>(partials));
+  k_yield<<<blocks, 256, 0, s>>>(a, reinterpret_cast<YieldPartial *>(partials));
   return cudaGetLastError();
 }
 
-size_t partial_bytes() { return sizeof(Partial); }
+size_t partial_bytes() { return sizeof(YieldPartial); }
 
 cudaError_t launch_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *rootA,
                                   const uint32_t *rootB, int n_inst, cudaStream_t s) {

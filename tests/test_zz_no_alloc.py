@@ -48,3 +48,6 @@ def test_noalloc_rejects_oversized_input():
                                           None) == binding.ERR_INVALID
     assert L.trilens_yield_reduce_noalloc(dummy, -1, None, None, dummy, None) == binding.ERR_INVALID
     assert L.trilens_yield_reduce_noalloc(None, 5, None, None, dummy, None) == binding.ERR_INVALID
+    odd = ctypes.c_void_p(20)  # 4-byte but not 8-byte aligned
+    assert L.trilens_yield_reduce_noalloc(odd, 5, None, None, dummy, None) == binding.ERR_INVALID
+    assert L.trilens_yield_reduce_noalloc(dummy, 5, None, None, odd, None) == binding.ERR_INVALID
