@@ -98,6 +98,12 @@ def lib():
             L.oracle_ip_bruteforce.argtypes = [pb, pb, d, d, ctypes.c_int64, d, d, pu,
                                                ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
             L.oracle_ip_bruteforce.restype = ctypes.c_int
+            pu32 = ctypes.POINTER(ctypes.c_uint32)
+            L.oracle_cloud_pairs.argtypes = [pb, pb, ctypes.c_int64, d, d, pu32, ctypes.c_int64,
+                                             pu32, ctypes.c_int64, pu32, ctypes.c_int64, pd, pd]
+            L.oracle_cloud_pairs.restype = ctypes.c_int
+            L.oracle_overlap_integral.argtypes = [pd] * 6 + [d]
+            L.oracle_overlap_integral.restype = d
             _lib = L
     return _lib
 
@@ -277,3 +283,61 @@ def ip_bruteforce(a: dict, b: dict, h_a: float, h_b: float, step: int, dt: float
             return hits[: count.value].copy()
         cap = int(count.value)
     raise RuntimeError("oracle capacity loop")
+
+
+def _pu32(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+
+
+def cloud_pairs(a: dict, b: dict, step: int, dt: float, kappa: float, cloud_a, cloud_b, pairs):
+    """Statistical regime at a cut (Sec. 2.2, Eq. rate, Eq. reactivity): clouds
+    are given by photon -> cloud memberships; for every listed cloud pair
+    (cloud of a, cloud of b) the 24 node-pair features and the ST rate (the
+    expected number of pairs in step k).  Returns (feat[m, 24], st[m])."""
+    A, ka = _beam(a)
+    B, kb = _beam(b)
+    ca = np.ascontiguousarray(cloud_a, dtype=np.uint32)
+    cb = np.ascontiguousarray(cloud_b, dtype=np.uint32)
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.uint32).reshape(-1, 2))
+    m = len(pr)
+    assert len(ca) == len(a["px"]) and len(cb) == len(b["px"])
+    nca = int(ca.max()) + 1 if len(ca) else 0
+    ncb = int(cb.max()) + 1 if len(cb) else 0
+    feat = np.zeros((m, 24))
+    st = np.zeros(m)
+    rc = lib().oracle_cloud_pairs(ctypes.byref(A), ctypes.byref(B), int(step), float(dt),
+                                  float(kappa), _pu32(ca), nca, _pu32(cb), ncb, _pu32(pr), m,
+                                  _pd(feat), _pd(st))
+    if rc == -1:
+        raise ValueError("cloud membership or pair out of range, or an empty cloud")
+    if rc != 0:
+        raise MemoryError("oracle_cloud_pairs")
+    return feat, st
+
+
+def overlap_integral(la, ua, va, lb, ub, vb, T: float) -> float:
+    """Exact integral over [0, T] of the overlap volume of two moving boxes."""
+    arr = [np.ascontiguousarray(x, dtype=np.float64) for x in (la, ua, va, lb, ub, vb)]
+    return lib().oracle_overlap_integral(*[_pd(x) for x in arr], float(T))
+
+
+def cloud_labels(a: dict, b: dict, hits, cloud_a, cloud_b, pairs):
+    """Exact yield of every listed cloud pair: the sum of w_i w_j over the
+    hits (i, j) whose photons lie in the pair's clouds, added in hit order.
+    Returns (label[m], hits that fall in no listed pair)."""
+    h = np.asarray(hits, dtype=np.int64).reshape(-1, 2)
+    pr = np.asarray(pairs, dtype=np.uint64).reshape(-1, 2)
+    ca = np.asarray(cloud_a, dtype=np.uint64)
+    cb = np.asarray(cloud_b, dtype=np.uint64)
+    key = (ca[h[:, 0]] << np.uint64(32)) | cb[h[:, 1]]
+    pk = (pr[:, 0] << np.uint64(32)) | pr[:, 1]
+    order = np.argsort(pk, kind="stable")
+    spk = pk[order]
+    pos = np.searchsorted(spk, key)
+    pos_c = np.minimum(pos, max(len(spk) - 1, 0))
+    found = (pos < len(spk)) & (spk[pos_c] == key) if len(spk) else np.zeros(len(key), bool)
+    wa = np.asarray(a["w"], dtype=np.float64)
+    wb = np.asarray(b["w"], dtype=np.float64)
+    label = np.zeros(len(pr))
+    np.add.at(label, order[pos_c[found]], wa[h[found, 0]] * wb[h[found, 1]])
+    return label, int((~found).sum())

@@ -750,3 +750,192 @@ int oracle_ip_bruteforce(const oracle_beam *a, const oracle_beam *b, double h_a,
   free(hv);
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Statistical (ST) regime at a cut of the hierarchy (Sec. 2.2, Eq. rate and
+ * Eq. reactivity).  A cloud is a set of photons (a node of the cut, given as
+ * a photon -> cloud membership).  Per cloud X at step k:
+ *   W_X = sum w;  mean and spread of ln E with weights w;  mean direction
+ *   dbar_X = sum w d / W_X (not renormalised);  swept box S_X = the AABB of
+ *   the photons' segments from P(t_k) to P(t_k) + c dt d, each widened by
+ *   h = r_max / 2 (half the largest collision radius) on every side.
+ * The cloud is read as a box of uniform density moving rigidly with c dbar:
+ * its box at t_k is S_X with the step's travel c dt dbar taken off (per axis
+ * [lo - min(0, D), hi - max(0, D)], D = c dt dbar_a), volume V_X, so that the
+ * box swept by it over the step is S_X again.  Eq. rate, n_I n_II <sigma v>
+ * per unit volume with n = W / V, integrated over the clouds' overlap and the
+ * step, gives the expected number of pairs
+ *   N = W_A W_B (1e12 kappa sigma(sbar)) |v_rel| int_0^dt V_ov(t) dt / (V_A V_B)
+ * with the collision area pi r^2 = 1e12 kappa sigma [um^2] of the collision
+ * criterion, the reactivity taken at the clouds' mean momenta: sbar from the
+ * geometric-mean energies exp(<ln E>) and 1 - dbar_A . dbar_B, and
+ * v_rel = c |dbar_A - dbar_B| the speed at which the criterion's cylinder
+ * sweeps (the printed <sigma v> = 2 pi sigma c is garbled; for head-on clouds
+ * c(1 - cos) and |v_A - v_B| are both 2c).  V_ov(t) is a product of three
+ * piecewise-linear overlap lengths, so its integral is taken exactly: split
+ * [0, dt] where an overlap length changes form, Simpson's rule on each piece
+ * (exact for the cubic there).
+ * ------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t count;
+  double W, wl, wl2, wd[3];
+  double lo[3], hi[3];
+} o_cloud;
+
+static int o_clouds(const oracle_beam *bm, int64_t step, double dt, double kappa,
+                    const uint32_t *cloud, int64_t n_cloud, o_cloud *out) {
+  const double h = 0.5 * 1e6 * sqrt(kappa * oracle_sigma_max() / O_PI);
+  const double ct = O_C * ((double)step * dt), L = O_C * dt;
+  for (int64_t c = 0; c < n_cloud; ++c) {
+    memset(&out[c], 0, sizeof(o_cloud));
+    for (int a = 0; a < 3; ++a) {
+      out[c].lo[a] = INFINITY;
+      out[c].hi[a] = -INFINITY;
+    }
+  }
+  for (int64_t i = 0; i < bm->n; ++i) {
+    const uint32_t c = cloud[i];
+    if ((int64_t)c >= n_cloud) return -1;
+    o_cloud *q = &out[c];
+    const double w = bm->w ? bm->w[i] : 1.0;
+    const double le = log(bm->E[i]);
+    const double p0[3] = {bm->px[i], bm->py[i], bm->pz[i]};
+    const double d[3] = {bm->dx[i], bm->dy[i], bm->dz[i]};
+    q->count += 1;
+    q->W += w;
+    q->wl += w * le;
+    q->wl2 += w * le * le;
+    for (int a = 0; a < 3; ++a) {
+      q->wd[a] += w * d[a];
+      const double P = p0[a] + ct * d[a];   /* position at t_k */
+      const double Q = P + L * d[a];        /* and at t_k + dt */
+      const double lo = (P < Q ? P : Q) - h, hi = (P < Q ? Q : P) + h;
+      if (lo < q->lo[a]) q->lo[a] = lo;
+      if (hi > q->hi[a]) q->hi[a] = hi;
+    }
+  }
+  return 0;
+}
+
+/* overlap length at time t of [la + va t, ua + va t] and [lb + vb t, ub + vb t] */
+static double o_olap(double la, double ua, double va, double lb, double ub, double vb, double t) {
+  const double hi = fmin(ua + va * t, ub + vb * t), lo = fmax(la + va * t, lb + vb * t);
+  return hi > lo ? hi - lo : 0.0;
+}
+
+static double o_vol_ov(const double la[3], const double ua[3], const double va[3],
+                       const double lb[3], const double ub[3], const double vb[3], double t) {
+  double v = 1.0;
+  for (int a = 0; a < 3; ++a) v *= o_olap(la[a], ua[a], va[a], lb[a], ub[a], vb[a], t);
+  return v;
+}
+
+static int o_cmp_double(const void *x, const void *y) {
+  const double a = *(const double *)x, b = *(const double *)y;
+  return (a > b) - (a < b);
+}
+
+/* exact integral over [0, T] of the overlap volume of two moving boxes */
+double oracle_overlap_integral(const double la[3], const double ua[3], const double va[3],
+                               const double lb[3], const double ub[3], const double vb[3],
+                               double T) {
+  double br[14];
+  int nb = 0;
+  br[nb++] = 0.0;
+  br[nb++] = T;
+  for (int a = 0; a < 3; ++a) {
+    const double w = vb[a] - va[a];
+    if (w == 0.0) continue;
+    /* times where an end of B passes an end of A */
+    const double cand[4] = {(ua[a] - ub[a]) / w, (la[a] - lb[a]) / w, (ua[a] - lb[a]) / w,
+                            (la[a] - ub[a]) / w};
+    for (int q = 0; q < 4; ++q)
+      if (cand[q] > 0.0 && cand[q] < T) br[nb++] = cand[q];
+  }
+  qsort(br, (size_t)nb, sizeof(double), o_cmp_double);
+  double I = 0.0;
+  for (int q = 0; q + 1 < nb; ++q) {
+    const double t0 = br[q], t1 = br[q + 1];
+    if (!(t1 > t0)) continue;
+    const double f0 = o_vol_ov(la, ua, va, lb, ub, vb, t0);
+    const double fm = o_vol_ov(la, ua, va, lb, ub, vb, 0.5 * (t0 + t1));
+    const double f1 = o_vol_ov(la, ua, va, lb, ub, vb, t1);
+    I += (t1 - t0) * (f0 + 4.0 * fm + f1) / 6.0;
+  }
+  return I;
+}
+
+int oracle_cloud_pairs(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                       double kappa, const uint32_t *cloud_a, int64_t n_cloud_a,
+                       const uint32_t *cloud_b, int64_t n_cloud_b, const uint32_t *pairs,
+                       int64_t n_pairs, double *feat, double *st) {
+  o_cloud *ca = (o_cloud *)malloc(sizeof(o_cloud) * (size_t)(n_cloud_a > 0 ? n_cloud_a : 1));
+  o_cloud *cb = (o_cloud *)malloc(sizeof(o_cloud) * (size_t)(n_cloud_b > 0 ? n_cloud_b : 1));
+  if (!ca || !cb) {
+    free(ca);
+    free(cb);
+    return -2;
+  }
+  int rc = 0;
+  if (o_clouds(a, step, dt, kappa, cloud_a, n_cloud_a, ca) ||
+      o_clouds(b, step, dt, kappa, cloud_b, n_cloud_b, cb))
+    rc = -1;
+  const double L = O_C * dt;
+  for (int64_t p = 0; p < n_pairs && !rc; ++p) {
+    const uint32_t ia = pairs[2 * p], ib = pairs[2 * p + 1];
+    if ((int64_t)ia >= n_cloud_a || (int64_t)ib >= n_cloud_b || ca[ia].count == 0 ||
+        cb[ib].count == 0) {
+      rc = -1;
+      break;
+    }
+    const o_cloud *A = &ca[ia], *B = &cb[ib];
+    double *f = feat + 24 * p;
+    for (int q = 0; q < 3; ++q) {
+      f[q] = 0.5 * (B->lo[q] + B->hi[q]) - 0.5 * (A->lo[q] + A->hi[q]);
+      f[3 + q] = 0.5 * (A->hi[q] - A->lo[q]);
+      f[6 + q] = 0.5 * (B->hi[q] - B->lo[q]);
+    }
+    f[9] = log((double)A->count);
+    f[10] = log((double)B->count);
+    f[11] = log(A->W);
+    f[12] = log(B->W);
+    const double mla = A->wl / A->W, mlb = B->wl / B->W;
+    f[13] = mla;
+    f[14] = mlb;
+    f[15] = sqrt(fmax(A->wl2 / A->W - mla * mla, 0.0));
+    f[16] = sqrt(fmax(B->wl2 / B->W - mlb * mlb, 0.0));
+    double da[3], db[3];
+    for (int q = 0; q < 3; ++q) {
+      da[q] = A->wd[q] / A->W;
+      db[q] = B->wd[q] / B->W;
+      f[17 + q] = da[q];
+      f[20 + q] = db[q];
+    }
+    const double omc = 1.0 - (da[0] * db[0] + da[1] * db[1] + da[2] * db[2]);
+    f[23] = omc;
+    /* the ST rate */
+    const double sbar = exp(mla + mlb) * omc / (2.0 * O_MEC2 * O_MEC2);
+    const double sig = oracle_sigma(sbar);
+    double la[3], ua[3], va[3], lb[3], ub[3], vb[3], VA = 1.0, VB = 1.0, dv2 = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double DA = L * da[q], DB = L * db[q];
+      la[q] = A->lo[q] - fmin(0.0, DA);
+      ua[q] = A->hi[q] - fmax(0.0, DA);
+      lb[q] = B->lo[q] - fmin(0.0, DB);
+      ub[q] = B->hi[q] - fmax(0.0, DB);
+      va[q] = O_C * da[q];
+      vb[q] = O_C * db[q];
+      VA *= ua[q] - la[q];
+      VB *= ub[q] - lb[q];
+      dv2 += (va[q] - vb[q]) * (va[q] - vb[q]);
+    }
+    const double I = oracle_overlap_integral(la, ua, va, lb, ub, vb, dt);
+    st[p] = (sig > 0.0 && I > 0.0)
+                ? A->W * B->W * (1e12 * kappa * sig) * sqrt(dv2) * I / (VA * VB)
+                : 0.0;
+  }
+  free(ca);
+  free(cb);
+  return rc;
+}

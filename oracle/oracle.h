@@ -110,6 +110,29 @@ int oracle_ip_bruteforce(const oracle_beam *a, const oracle_beam *b, double h_a,
                          int64_t step, double dt, double kappa, uint32_t *hits, int64_t cap,
                          int64_t *count);
 
+/* Statistical (ST) regime at a cut of the hierarchy (Sec. 2.2, Eq. rate,
+ * Eq. reactivity).  Clouds are sets of photons: cloud_a[i] is the cloud
+ * (0 .. n_cloud_a - 1) of photon i of a, likewise for b.  For each pair p of
+ * clouds (pairs[2p] of a, pairs[2p + 1] of b) at step k: the 24 node-pair
+ * features feat[24p .. 24p + 23] -- centre of B's swept box minus A's (3),
+ * half-extents of A's (3) and B's (3) swept boxes, ln count of A and B, ln of
+ * the weight sums, weighted mean of ln E of A and B, weighted spread of ln E
+ * of A and B, weighted mean direction of A (3) and B (3), 1 - dbar_A . dbar_B
+ * -- with the swept box of a cloud the AABB of its photons' segments over
+ * the step, each widened by half the largest collision radius; and st[p], the
+ * expected number of pairs of Eq. rate for the two clouds as uniform boxes
+ * moving with their mean velocities (details in oracle.c).  Returns 0, -1
+ * for a membership or pair out of range or an empty cloud, -2 out of memory. */
+int oracle_cloud_pairs(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
+                       double kappa, const uint32_t *cloud_a, int64_t n_cloud_a,
+                       const uint32_t *cloud_b, int64_t n_cloud_b, const uint32_t *pairs,
+                       int64_t n_pairs, double *feat, double *st);
+/* the exact integral over [0, T] of the overlap volume of box A ([la, ua]
+ * moving with va) and box B ([lb, ub] moving with vb) */
+double oracle_overlap_integral(const double la[3], const double ua[3], const double va[3],
+                               const double lb[3], const double ub[3], const double vb[3],
+                               double T);
+
 /* All pairs.  Hits (i, j) written as uint32 pairs in lexicographic order,
  * at most cap of them; res->count is the true number. */
 int oracle_bruteforce(const oracle_beam *a, const oracle_beam *b, int64_t step, double dt,
