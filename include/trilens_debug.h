@@ -71,6 +71,35 @@ int trilens_debug_timing(trilens_ctx *c, int on);
  * synchronises). */
 int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int reset);
 
+/* Random stress of the FP32 narrow phase's error band (the precision
+ * pattern's guarantee that the FP32 path returns exactly the FP64 hit set of
+ * Eq. BWcross / Eq. eq.Cond and the closest-approach test).  Draws n_pairs
+ * seeded photon pairs near a boundary of the decision and decides each with
+ * the FP32 narrow phase and with the FP64 definition.  Pair q belongs to
+ * category q mod 8:
+ *   0-3  distance at closest approach d^2 = r^2 (1 +- 2^-e), e in 1..50
+ *   4    closest-approach time t* = +-2^-e dt (the window's start)
+ *   5    t* = dt (1 +- 2^-e) (the window's end)
+ *   6    invariant s = 1 +- 2^-e (the threshold), e in 1..52
+ *   7    d^2 uniform in [0, 4 r_max^2), t* in [-0.1 dt, 1.1 dt) (quick miss)
+ * with a random time step 0..63, beam axes at a random angle, 5 mrad spread,
+ * and the meeting point anywhere within +-100 um.  counts (device,
+ * TRILENS_STRESS_CATEGORIES x TRILENS_STRESS_FIELDS uint64, accumulated: zero
+ * it first) receives per category: pairs, FP64 hits, FP32 sure hits, FP32
+ * sure misses, FP32 band, sure hits FP64 rejects, sure misses FP64 accepts.
+ * The first n_sample pairs (<= n_pairs) are written to sample (device,
+ * n_sample x TRILENS_STRESS_SAMPLE doubles: p0 (3), direction (3) and energy
+ * of photon i, the same of photon j, the step k, the FP64 decision (0/1) and
+ * the FP32 outcome (0 miss, 1 hit, 2 band)).  Asynchronous on `stream`.
+ * INVALID for negative sizes, dt_fs or kappa not positive, NULL counts, or
+ * n_sample > n_pairs. */
+#define TRILENS_STRESS_CATEGORIES 8
+#define TRILENS_STRESS_FIELDS 7
+#define TRILENS_STRESS_SAMPLE 17
+int trilens_debug_band_stress(uint64_t seed, int64_t n_pairs, double dt_fs, double kappa,
+                              unsigned long long *counts, double *sample, int64_t n_sample,
+                              trilens_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,9 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_set_key_bits.restype = ctypes.c_int
         L.trilens_debug_eval64.argtypes = [vp, vp, i64, i32, vp]
         L.trilens_debug_eval64.restype = ctypes.c_int
+        L.trilens_debug_band_stress.argtypes = [ctypes.c_uint64, i64, ctypes.c_double,
+                                                ctypes.c_double, vp, vp, i64, vp]
+        L.trilens_debug_band_stress.restype = ctypes.c_int
         L.trilens_debug_timing.argtypes = [vp, ctypes.c_int]
         L.trilens_debug_timing.restype = ctypes.c_int
         L.trilens_debug_phase_ms.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.c_int]
@@ -446,6 +449,32 @@ def eval64(x, which: str = "sigma", stream=None):
                                       x.numel(), 0 if which == "sigma" else 1,
                                       ctypes.c_void_p(st.cuda_stream)))
     return out
+
+
+STRESS_CATEGORIES, STRESS_FIELDS, STRESS_SAMPLE = 8, 7, 17
+STRESS_FIELD_NAMES = ("pairs", "fp64_hits", "fp32_sure_hits", "fp32_sure_misses", "fp32_band",
+                      "wrong_sure_hits", "wrong_sure_misses")
+
+
+def band_stress(seed: int, n_pairs: int, dt_fs: float, kappa: float, n_sample: int = 0,
+                stream=None):
+    """Seeded near-boundary photon pairs decided by the FP32 narrow phase and
+    the FP64 definition on the device (trilens_debug_band_stress).  Returns
+    (counts[8 categories, 7 fields] as numpy uint64, sample[n_sample, 17] as
+    numpy float64 or None)."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    counts = torch.zeros(STRESS_CATEGORIES * STRESS_FIELDS, dtype=torch.int64, device="cuda")
+    sample = (torch.empty((n_sample, STRESS_SAMPLE), dtype=torch.float64, device="cuda")
+              if n_sample > 0 else None)
+    _check(lib().trilens_debug_band_stress(
+        ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(n_pairs), float(dt_fs), float(kappa),
+        ctypes.c_void_p(counts.data_ptr()),
+        ctypes.c_void_p(sample.data_ptr()) if sample is not None else None, int(n_sample),
+        ctypes.c_void_p(st.cuda_stream)))
+    torch.cuda.synchronize()
+    c = counts.cpu().numpy().view(np.uint64).reshape(STRESS_CATEGORIES, STRESS_FIELDS)
+    return c, (sample.cpu().numpy() if sample is not None else None)
 
 
 NOALLOC_MAX_HITS = 1 << 28

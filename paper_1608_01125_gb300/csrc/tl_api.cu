@@ -93,6 +93,21 @@ static float round_down(double x) {
   return f;
 }
 
+// constants of the FP32 narrow phase for a step of dt_fs and amplification kappa
+TLNarrowConst tl_narrow_const(double dt_fs, double kappa) {
+  const double u = ldexp(1.0, -24);
+  const double sigma_max = host_sigma_max() * (1.0 + 1e-6);
+  TLNarrowConst nk;
+  nk.L = (float)(TL_C * dt_fs);
+  nk.L_in = round_down((double)nk.L * (1.0 - 8.0 * u));
+  nk.L_out = round_up((double)nk.L * (1.0 + 8.0 * u));
+  nk.r2max = round_up(1e12 * kappa * sigma_max * (1.0 + 1e-5) / TL_PI);
+  nk.kr = (float)(1e12 * kappa / TL_PI);
+  nk.inv2mc4 = (float)(1.0 / (2.0 * TL_MEC2 * TL_MEC2));
+  nk.pref = (float)(0.5 * TL_PI * TL_RE * TL_RE);
+  return nk;
+}
+
 static void free_beam(tl::BuildBufs &w) {
   cudaFree(w.pos_u);
   cudaFree(w.dir_u);
@@ -265,17 +280,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   c->L_lo = round_down(c->L64);
   c->L_hi = round_up(c->L64);
   c->half = round_up(0.5 * c->rmax * (1.0 + 1e-6) + 1e-9);
-  {
-    const double u = ldexp(1.0, -24);
-    TLNarrowConst &nk = c->nk;
-    nk.L = (float)c->L64;
-    nk.L_in = round_down((double)nk.L * (1.0 - 8.0 * u));
-    nk.L_out = round_up((double)nk.L * (1.0 + 8.0 * u));
-    nk.r2max = round_up(1e12 * c->p.kappa * c->sigma_max * (1.0 + 1e-5) / TL_PI);
-    nk.kr = (float)(1e12 * c->p.kappa / TL_PI);
-    nk.inv2mc4 = (float)(1.0 / (2.0 * TL_MEC2 * TL_MEC2));
-    nk.pref = (float)(0.5 * TL_PI * TL_RE * TL_RE);
-  }
+  c->nk = tl_narrow_const(c->p.dt_fs, c->p.kappa);
   // workspace
   CK(dalloc(&c->build_status, 1));
   CK(cudaMallocHost((void **)&c->build_status_host, sizeof(unsigned)));

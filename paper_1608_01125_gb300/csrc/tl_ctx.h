@@ -138,4 +138,5 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
 void surrogate_free(trilens_ctx *c);
 void deplete_free(trilens_ctx *c);
 double tl_sigma_max_bound();
+TLNarrowConst tl_narrow_const(double dt_fs, double kappa);
 extern "C" int surrogate_total(trilens_ctx *c, int level, double *out);

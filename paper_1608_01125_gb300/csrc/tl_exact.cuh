@@ -65,23 +65,25 @@ __device__ __forceinline__ double tl_s64(double Ei, double Ej, double cs) {
   return __ddiv_rn(__dmul_rn(__dmul_rn(Ei, Ej), __dsub_rn(1.0, cs)), (2.0 * TL_MEC2) * TL_MEC2);
 }
 
-// The decision for input photons i of A and j of B at the step with
-// ct = c * (k * dt).
-__device__ __forceinline__ bool tl_exact_hit(const TLBeam &A, uint32_t i, const TLBeam &B,
-                                             uint32_t j, double ct, double dt, double kappa) {
-  const double dxi = A.dx[i], dyi = A.dy[i], dzi = A.dz[i];
-  const double dxj = B.dx[j], dyj = B.dy[j], dzj = B.dz[j];
+// The decision for one photon pair given by value: positions at t = 0,
+// unit directions and energies of photon i (beam A) and photon j (beam B),
+// at the step with ct = c * (k * dt).
+__device__ __forceinline__ bool tl_exact_decide(double p0xi, double p0yi, double p0zi, double dxi,
+                                                double dyi, double dzi, double Ei, double p0xj,
+                                                double p0yj, double p0zj, double dxj, double dyj,
+                                                double dzj, double Ej, double ct, double dt,
+                                                double kappa) {
   double cs = __dadd_rn(__dadd_rn(__dmul_rn(dxi, dxj), __dmul_rn(dyi, dyj)), __dmul_rn(dzi, dzj));
-  double s = tl_s64(A.E[i], B.E[j], cs);
+  double s = tl_s64(Ei, Ej, cs);
   if (!(s > 1.0)) return false;
   double vx = __dmul_rn(TL_C, __dsub_rn(dxi, dxj));
   double vy = __dmul_rn(TL_C, __dsub_rn(dyi, dyj));
   double vz = __dmul_rn(TL_C, __dsub_rn(dzi, dzj));
   double vv = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
   if (vv == 0.0) return false;
-  double px = __dsub_rn(__dadd_rn(A.px[i], __dmul_rn(ct, dxi)), __dadd_rn(B.px[j], __dmul_rn(ct, dxj)));
-  double py = __dsub_rn(__dadd_rn(A.py[i], __dmul_rn(ct, dyi)), __dadd_rn(B.py[j], __dmul_rn(ct, dyj)));
-  double pz = __dsub_rn(__dadd_rn(A.pz[i], __dmul_rn(ct, dzi)), __dadd_rn(B.pz[j], __dmul_rn(ct, dzj)));
+  double px = __dsub_rn(__dadd_rn(p0xi, __dmul_rn(ct, dxi)), __dadd_rn(p0xj, __dmul_rn(ct, dxj)));
+  double py = __dsub_rn(__dadd_rn(p0yi, __dmul_rn(ct, dyi)), __dadd_rn(p0yj, __dmul_rn(ct, dyj)));
+  double pz = __dsub_rn(__dadd_rn(p0zi, __dmul_rn(ct, dzi)), __dadd_rn(p0zj, __dmul_rn(ct, dzj)));
   double pv = __dadd_rn(__dadd_rn(__dmul_rn(px, vx), __dmul_rn(py, vy)), __dmul_rn(pz, vz));
   double ts = __ddiv_rn(-pv, vv);
   if (!(ts >= 0.0) || !(ts < dt)) return false;  // half-open window [0, dt)
@@ -91,4 +93,12 @@ __device__ __forceinline__ bool tl_exact_hit(const TLBeam &A, uint32_t i, const 
   double d2 = __dadd_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(qz, qz));
   double r2 = __ddiv_rn(__dmul_rn(__dmul_rn(1e12, kappa), tl_sigma64(s)), TL_PI);
   return d2 < r2;
+}
+
+// The decision for input photons i of A and j of B at the step with
+// ct = c * (k * dt).
+__device__ __forceinline__ bool tl_exact_hit(const TLBeam &A, uint32_t i, const TLBeam &B,
+                                             uint32_t j, double ct, double dt, double kappa) {
+  return tl_exact_decide(A.px[i], A.py[i], A.pz[i], A.dx[i], A.dy[i], A.dz[i], A.E[i], B.px[j],
+                         B.py[j], B.pz[j], B.dx[j], B.dy[j], B.dz[j], B.E[j], ct, dt, kappa);
 }

@@ -65,9 +65,34 @@ def crossing90(out_path=None):
     print(path)
 
 
+def headon_run(out_path=None):
+    """Stored oracle values of every time step of the 2 x 1,048,576 head-on run
+    (64 steps of 5 fs): the per-step count, weighted yield and checksums whose
+    sums over the run the captured run (trilens_run) must reproduce.  Slow: run
+    by hand (python tests/golden/make_golden.py headon_run)."""
+    wl = synth.headon_1m()
+    a, b = synth.beams(wl)
+    out = {"_about": "FP64 oracle (k-d tree) results of every time step; written by "
+                     "tests/golden/make_golden.py", "workload": wl.name, "n": wl.a.n,
+           "seed": wl.seed, "steps": []}
+    for step in range(wl.steps):
+        _, r = oracle.tree(a, b, step, wl.dt, wl.kappa, nthreads=os.cpu_count() or 1,
+                           cap=1 << 22)
+        out["steps"].append({"step": step, "count": r["count"], "weighted": r["weighted"],
+                             "hsum": str(r["hsum"]), "hxor": str(r["hxor"])})
+        print(out["steps"][-1], flush=True)
+    path = out_path or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                    "oracle_values_headon_run.json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(path)
+
+
 if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "crossing90":
         crossing90()
+    elif len(sys.argv) > 1 and sys.argv[1] == "headon_run":
+        headon_run()
     else:
         main()
 

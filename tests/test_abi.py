@@ -106,4 +106,13 @@ def test_invalid_arguments_rejected_on_host(lib):
                                     None) == binding.ERR_INVALID
     assert lib.trilens_swarm_expand(ctypes.byref(empty), 0.5, None, 0, None, None, None,
                                     None) == binding.ERR_INVALID
+    # band stress: sizes and constants are checked before anything is launched
+    bs = lib.trilens_debug_band_stress
+    dummy = ctypes.c_void_p(256)
+    assert bs(1, -1, 5.0, 1e14, dummy, None, 0, None) == binding.ERR_INVALID
+    assert bs(1, 10, 5.0, 1e14, None, None, 0, None) == binding.ERR_INVALID
+    assert bs(1, 10, 0.0, 1e14, dummy, None, 0, None) == binding.ERR_INVALID
+    assert bs(1, 10, 5.0, -1.0, dummy, None, 0, None) == binding.ERR_INVALID
+    assert bs(1, 10, 5.0, 1e14, dummy, None, 4, None) == binding.ERR_INVALID
+    assert bs(1, 10, 5.0, 1e14, dummy, dummy, 11, None) == binding.ERR_INVALID
     lib.trilens_destroy(None)

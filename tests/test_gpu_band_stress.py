@@ -1,0 +1,67 @@
+"""Random stress of the precision pattern: 10^9 seeded photon pairs placed on
+the decision's boundaries (distance at closest approach against the collision
+radius, the closest-approach time against both ends of the window, the
+invariant s against the threshold, the quick miss's margin) are decided by
+the FP32 narrow phase and by the FP64 definition on the device.  No FP32
+"sure" decision may disagree with FP64; the device FP64 decision itself
+equals the CPU oracle's on a sample of the same pairs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_01125_gb300 import binding
+
+pytestmark = pytest.mark.gpu
+
+# (dt [fs], kappa) of the workloads: 2x1M head-on, the small head-on case,
+# the statistical and the crossing workloads
+SETTINGS = [(5.0, 1e14), (10.0, 1e16), (20.0, 1e12), (2.0, 1e12)]
+PAIRS = 250_000_000  # per setting: 10^9 in total
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("dt,kappa", SETTINGS)
+def test_no_fp32_sure_decision_disagrees_with_fp64(dt, kappa):
+    seed = int(dt * 1000) ^ int(np.log10(kappa))
+    c, _ = binding.band_stress(seed, PAIRS, dt, kappa)
+    f = {k: c[:, i].astype(np.int64) for i, k in enumerate(binding.STRESS_FIELD_NAMES)}
+    print(dt, kappa, {k: v.tolist() for k, v in f.items()})
+    assert int(f["pairs"].sum()) == PAIRS
+    assert int(f["wrong_sure_hits"].sum()) == 0
+    assert int(f["wrong_sure_misses"].sum()) == 0
+    # each boundary is met from both sides
+    for cat in range(7):
+        assert 0 < f["fp64_hits"][cat] < f["pairs"][cat], cat
+    # the FP32 path still decides most pairs away from the boundaries
+    assert f["fp32_band"][7] < 0.01 * f["pairs"][7]
+    # and sure decisions happen in every category (the band is not everything)
+    assert (f["fp32_sure_hits"][:6] + f["fp32_sure_misses"][:6] > 0).all()
+
+
+def test_device_fp64_decision_equals_oracle_on_stress_pairs():
+    dt, kappa = 5.0, 1e14
+    _, smp = binding.band_stress(77, 1 << 16, dt, kappa, n_sample=1 << 16)
+    n = len(smp)
+    a = {k: np.ascontiguousarray(smp[:, c]) for c, k in enumerate(("px", "py", "pz", "dx", "dy",
+                                                                   "dz", "E"))}
+    b = {k: np.ascontiguousarray(smp[:, 7 + c]) for c, k in enumerate(("px", "py", "pz", "dx",
+                                                                       "dy", "dz", "E"))}
+    a["w"] = np.ones(n)
+    b["w"] = np.ones(n)
+    A, ka = oracle._beam(a)
+    B, kb = oracle._beam(b)
+    L = oracle.lib()
+    import ctypes
+    got = np.array([L.oracle_pair_hit(ctypes.byref(A), q, ctypes.byref(B), q, int(smp[q, 14]),
+                                      dt, kappa) for q in range(n)], dtype=bool)
+    dev = smp[:, 15] > 0.5
+    assert np.array_equal(got, dev), int((got != dev).sum())
+    assert 0.2 * n < dev.sum() < 0.8 * n
+    # FP32 sure outcomes in the sample agree as well
+    r32 = smp[:, 16].astype(int)
+    assert not np.any((r32 == 1) & ~dev) and not np.any((r32 == 0) & dev)

@@ -58,3 +58,35 @@ def test_run_regrows_small_buffers():
         col.debug_shrink_buffers()
         r = col.run(0, 2)
     assert r["count"] == ref["count"] and r["hsum"] == ref["hsum"]
+
+
+def test_benchmarked_run_equals_oracle_every_step():
+    """What bench.py times, as it times it: 2 x 1,048,576 photons, FP32 + FP64
+    band, all 64 steps as one captured run with the autotuner's knobs.  The
+    run's totals equal the sums of the oracle's per-step values
+    (tests/golden/oracle_values_headon_run.json, written from the oracle
+    only); one-step captured runs at sampled steps equal that step's values."""
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    g = json.load(open(os.path.join(here, "golden", "oracle_values_headon_run.json")))
+    per = {s["step"]: s for s in g["steps"]}
+    wl = synth.headon_1m()
+    assert g["n"] == wl.a.n and g["seed"] == wl.seed and len(per) == wl.steps
+    a, b = synth.beams(wl)
+    cache = os.path.join(os.path.dirname(here), "paper_1608_01125_gb300", "_tuning_cache.json")
+    with binding.Collider(a, b, wl.dt, wl.kappa, precision=binding.FP32_BAND) as col:
+        tuned = col.autotune([2, 4, 40], cache)  # the bench's call
+        print("knobs", tuned)
+        r = col.run(0, wl.steps)
+        assert r["count"] == sum(s["count"] for s in g["steps"])
+        assert r["hsum"] == sum(int(s["hsum"]) for s in g["steps"]) % (1 << 64)
+        hx = 0
+        for s in g["steps"]:
+            hx ^= int(s["hxor"])
+        assert r["hxor"] == hx
+        assert r["weighted"] == float(r["count"])  # unit weights: exact
+        for k in (0, 1, 2, 7, 9, 40):
+            r1 = col.run(k, 1)
+            assert r1["count"] == per[k]["count"], k
+            assert r1["hsum"] == int(per[k]["hsum"]) and r1["hxor"] == int(per[k]["hxor"]), k
