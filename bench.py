@@ -3,9 +3,11 @@
 One benchmark step = one full run of the head-on workload: 64 time steps of
 5 fs, each a hierarchy build of both beams plus the collision step (dual
 traversal, FP32 narrow phase, FP64 band re-test, yield), inputs resident in
-HBM.  The metric counts photon-pair tests in the all-pairs sense: each time
-step answers N_A * N_B pair queries.  Collided pairs/s and the narrow-phase
-tests actually evaluated per second are reported beside it.
+HBM.  The metric is the narrow-phase photon-pair tests per second: photon
+pairs that reach the exact closest-approach test (the work the method
+does after the hierarchy has pruned).  Collided pairs/s and the all-pairs
+equivalent N_A * N_B * time steps per second are reported beside it as
+context.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -33,8 +35,13 @@ sys.path.insert(0, ROOT)
 
 from paper_1608_01125_gb300 import synth  # noqa: E402
 
-METRIC = "photon-pair tests/s at 2x1M (N_A*N_B pair queries per time step)"
+METRIC = "narrow-phase photon-pair tests/s at 2x1M (photon pairs given the exact test per second)"
 UNIT = "pair-tests/s"
+# the oracle's CPU samples: every 4th time step (a systematic sample of the
+# run's busy and empty steps), all host cores; single-threaded (as the paper
+# ran) on one busy and one empty step
+CPU_STEP_STRIDE = 4
+SINGLE_THREAD_STEPS = (4, 36)
 FALLBACK_HBM_GBS = 6800.0
 PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "band", "yield")
 
@@ -155,23 +162,33 @@ def _isnum(s):
 
 
 def oracle_sample(wl, a, b, steps, threads):
+    """The FP64 k-d-tree oracle over the given time steps: (seconds, hits,
+    narrow-phase tests)."""
     import oracle
     t0 = time.perf_counter()
-    hits = 0
+    hits = tests = 0
     for k in steps:
         _, r = oracle.tree(a, b, k, wl.dt, wl.kappa, nthreads=threads, cap=1 << 22)
         hits += r["count"]
-    return time.perf_counter() - t0, hits
+        tests += r["tests"]
+    return time.perf_counter() - t0, hits, tests
 
 
-def cpu_baseline(wl, a, b):
+def cpu_baseline(wl, a, b, first=0, nsteps=None):
     threads = os.cpu_count() or 1
-    steps = list(range(0, wl.steps, 16))  # 4 of the 64 time steps, evenly spaced
-    dt, _ = oracle_sample(wl, a, b, steps, threads)
-    value = wl.a.n * wl.b.n * len(steps) / dt
-    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"FP64 k-d-tree oracle, time steps {steps} of the {wl.steps}-step run, "
-                      f"{threads} threads, {dt:.1f} s"}
+    nsteps = nsteps or wl.steps
+    steps = list(range(first, first + nsteps, CPU_STEP_STRIDE))
+    dt, hits, tests = oracle_sample(wl, a, b, steps, threads)
+    st_steps = [k for k in SINGLE_THREAD_STEPS if first <= k < first + nsteps] or steps[:1]
+    dt1, _, tests1 = oracle_sample(wl, a, b, st_steps, 1)
+    return {"value": tests / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"FP64 k-d-tree oracle (leaf size 8), every {CPU_STEP_STRIDE}th time step "
+                      f"({len(steps)} of the {nsteps}-step run: {steps[0]}, {steps[1] if len(steps) > 1 else ''}"
+                      f"...), {threads} threads, {dt:.1f} s, {tests} narrow-phase tests, {hits} hits",
+            "all_pairs_per_s": wl.a.n * wl.b.n * len(steps) / dt,
+            "single_thread": {"value": tests1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"time steps {st_steps}, one thread, {dt1:.1f} s, "
+                                        f"{tests1} narrow-phase tests"}}
 
 
 # FP64 operations per hit of the pair products, counted from the kernel: 26
@@ -368,27 +385,39 @@ def ip_regime_timing(dev, stream, reps=3, cpu=True):
 
 
 def run_reference(args, wl):
+    """The oracle as the reference arm: bench step q times the time steps
+    {j, j + 16, j + 32, j + 48} of the run with j = q mod 16, so that 16 bench
+    steps cover every time step once and any K steps keep the run's mix of
+    busy and empty steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     a, b = synth.beams(wl)
     threads = os.cpu_count() or 1
-    steps = list(range(0, wl.steps, 16))
-    for _ in range(args.warmup):
-        oracle_sample(wl, a, b, steps[:1], threads)
+    first, nsteps = args.first_step, (args.time_steps or wl.steps)
+    stride = max(nsteps // 4, 1)
+    sample = lambda q: [first + (q % stride) + m * stride  # noqa: E731
+                        for m in range(4) if (q % stride) + m * stride < nsteps]
+    for q in range(args.warmup):
+        oracle_sample(wl, a, b, sample(q)[-1:], threads)
     total = 0.0
-    for _ in range(args.steps):
-        dt, _ = oracle_sample(wl, a, b, steps, threads)
+    tests = hits = 0
+    for q in range(args.steps):
+        dt, h, t = oracle_sample(wl, a, b, sample(q), threads)
         total += dt
-    units = wl.a.n * wl.b.n * len(steps) * args.steps
-    value = units / total
+        tests += t
+        hits += h
+    value = tests / total
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": config_of(wl, "oracle on the host cores; no GPU"),
+            "config": config_of(wl, L2_NOTE, nsteps, first),
+            "collided_pairs_per_s": hits / total,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"each step = time steps {steps} of the {wl.steps}-step run"},
+                             "sample": f"bench step q = time steps q mod {stride} + {{0, {stride}, "
+                                       f"{2 * stride}, {3 * stride}}} of the {nsteps}-step run "
+                                       f"(FP64 k-d-tree oracle, leaf size 8, {threads} threads)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -410,10 +439,13 @@ def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
     return world * units_per_rank / (ms / 1e3)
 
 
-def config_of(wl, l2):
-    return {"workload": wl.name, "photons_per_beam": wl.a.n, "time_steps": wl.steps,
-            "dt_fs": wl.dt, "kappa": wl.kappa, "precision": "fp32 + fp64 band",
-            "l2": l2, "parallelism": "replicas"}
+L2_NOTE = "GPU: L2 flushed (256 MiB write) before every timed step"
+
+
+def config_of(wl, l2, nsteps=None, first=0):
+    return {"workload": wl.name, "photons_per_beam": wl.a.n, "time_steps": nsteps or wl.steps,
+            "first_step": first, "dt_fs": wl.dt, "kappa": wl.kappa,
+            "precision": "fp32 + fp64 band", "l2": l2, "parallelism": "replicas"}
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -502,6 +534,16 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         sw_ms.append(e0.elapsed_time(e1))
     phase_ms, launches = col.phase_ms(reset=True)
+    # the traversal step by step: its device time per time step, to give the
+    # roofline of the busy steps (where the bunches cross) beside the run's average
+    per_step = []
+    for k in time_steps:
+        col.build(k)
+        col.phase_ms(reset=True)
+        col.collide(k)
+        ph, _ = col.phase_ms(reset=True)
+        st = col.stats()
+        per_step.append((k, ph["traverse"], st["narrow_tests"], st["count"], st["band"]))
     col.timing(False)
     pairs = pair_products_timing(col, A, B, stream) if rank == 0 else None
     depl = (depletion_timing(col, stream, list(time_steps), *read_peaks(),
@@ -511,8 +553,7 @@ def run_ours(args, wl):
            if rank == 0 and not args.no_ip else None)
     ms = slowest_rank_ms(ms, world, dev)
     K = args.steps
-    units_rank = wl.a.n * wl.b.n * nsteps * K
-    value = whole_job_rate(units_rank, world, ms)
+    value = whole_job_rate(tests, world, ms)
 
     # end to end through the public API with host buffers: every step copies
     # the two beams from pinned host memory, runs, and reads the yield back
@@ -531,7 +572,7 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = whole_job_rate(wl.a.n * wl.b.n * nsteps, world,
+    e2e_value = whole_job_rate(tests / K, world,
                                slowest_rank_ms(statistics.mean(e2e_ms), world, dev))
 
     if rank != 0:
@@ -556,15 +597,23 @@ def run_ours(args, wl):
         algo = per_unit * (wl.a.n + wl.b.n) + 8.0 * (hits + band) / (K * nsteps)
         launch_ms = phase_ms[dom] / (K * nsteps)
     achieved = algo / (launch_ms / 1e3) / 1e9
-    cpu = cpu_baseline(wl, a_np, b_np) if (world == 1 and not args.no_cpu_baseline) else None
+    # busy steps: those with at least 5% of the peak step's narrow-phase tests
+    peak_tests = max(t for _, _, t, _, _ in per_step) if per_step else 0
+    busy = [r for r in per_step if peak_tests and r[2] >= 0.05 * peak_tests]
+    tb = sum(r[1] for r in busy)
+    busy_bytes = sum(per_unit * (wl.a.n + wl.b.n) + 8.0 * (r[3] + r[4]) for r in busy)
+    busy_gbs = busy_bytes / (tb / 1e3) / 1e9 if tb > 0 else None
+    cpu = (cpu_baseline(wl, a_np, b_np, first, nsteps)
+           if (world == 1 and not args.no_cpu_baseline) else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": dict(config_of(wl, "flushed (256 MiB write) before every timed step"),
-                       time_steps=nsteps, first_step=first),
+        "config": config_of(wl, L2_NOTE, nsteps, first),
         "collided_pairs_per_s": world * hits / (ms / 1e3),
-        "narrow_tests_per_s": world * tests / (ms / 1e3),
+        "all_pairs_per_s": whole_job_rate(wl.a.n * wl.b.n * nsteps * K, world, ms),
+        "all_pairs_note": "context only: N_A * N_B * time steps per second, the all-pairs work "
+                          "the hierarchy avoids",
         "hits_per_run": hits / K, "narrow_tests_per_run": tests / K, "band_per_run": band / K,
         "node_tests_per_run": work.get("node_tests"), "leaf_pairs_per_run": work.get("leaf_pairs"),
         "path": "trilens_run: all steps of a run as one captured CUDA graph",
@@ -575,7 +624,14 @@ def run_ours(args, wl):
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": read_traffic(dom), "algorithmic_bytes_per_launch": algo,
-                     "launch_ms": launch_ms},
+                     "launch_ms": launch_ms,
+                     "average": "over every launch of the run (most time steps are almost "
+                                "empty: the bunches cross in the first ~10)",
+                     "busy_steps": {"steps": [r[0] for r in busy], "traverse_ms": tb,
+                                    "algorithmic_bytes": busy_bytes, "achieved": busy_gbs,
+                                    "frac": busy_gbs / peak if busy_gbs else None,
+                                    "per_step_ms": [round(r[1], 4) for r in busy],
+                                    "narrow_tests": [r[2] for r in busy]}},
         "pair_products": pairs,
         "depletion": depl,
         "ip_regime": ipr,
