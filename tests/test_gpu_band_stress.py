@@ -37,8 +37,10 @@ def test_no_fp32_sure_decision_disagrees_with_fp64(dt, kappa):
     # each boundary is met from both sides
     for cat in range(7):
         assert 0 < f["fp64_hits"][cat] < f["pairs"][cat], cat
-    # the FP32 path still decides most pairs away from the boundaries
-    assert f["fp32_band"][7] < 0.01 * f["pairs"][7]
+    # the FP32 path still decides most pairs away from the boundaries (at
+    # kappa = 1e12 the radius, ~2e-3 um, is within a few hundred FP32 ulps of
+    # positions near 100 um, so about 1% of these pairs are banded there)
+    assert f["fp32_band"][7] < 0.05 * f["pairs"][7]
     # and sure decisions happen in every category (the band is not everything)
     assert (f["fp32_sure_hits"][:6] + f["fp32_sure_misses"][:6] > 0).all()
 
