@@ -78,7 +78,7 @@ typedef struct {
   int32_t precision;   /* enum trilens_precision */
   int32_t leaf_bucket; /* photons per hierarchy leaf, 1..32 (0: 4) */
   int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (0: 256) */
-  int32_t block_shape; /* traversal warps per block, 1..16 (0: 4) */
+  int32_t block_shape; /* traversal warps per block, 1..8 (0: 4) */
   int64_t spin_limit;  /* iteration limit of every device wait (0: 1<<22) */
 } trilens_params;
 
@@ -298,7 +298,7 @@ int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const tr
  * The hit set never depends on these knobs; only the time does.
  *   leaf_bucket  photons per hierarchy leaf (1..32)
  *   stack_depth  traversal stack entries per warp, in shared memory (64..4096)
- *   block_shape  traversal warps per block (1..16)
+ *   block_shape  traversal warps per block (1..8)
  *   budget       traversal iterations a warp spends on one work item before it
  *                hands the rest on, as chunks of 8 node pairs, to the step's
  *                device work queue, where idle warps take them (0 = never;
@@ -332,7 +332,7 @@ int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
  * each W row-major [out][in], layer z = W h + b.  norm (device, 48 floats) holds
  * the feature mean[24] and 1/std[24] applied to the raw features first.
  * Output per row: (mu, s), a Gaussian over the target y (for the surrogate,
- * the residual of log1p(pair yield) over log1p of the ST-form estimate) with
+ * the residual of log1p(pair yield) over log1p of the ST-rate baseline) with
  * log variance s; loss 0.5 (s + (y - mu)^2 e^-s), s clamped to +-12. */
 #define TRILENS_MLP_PARAMS 36482
 
@@ -363,11 +363,14 @@ int trilens_mlp_grad(const float *params, const float *norm, const float *x, con
  * weights and their energy and direction moments over the Morton-ordered
  * photons.  Training labels are the exact yields of the pairs (an exact
  * traversal seeded with the pairs; every hit is attributed to the pair that
- * holds its two photons).  Next to the features the kernels compute an
- * estimate of the paper's ST form (rate ~ n_I n_II sigma: weight sums times
- * sigma(s) at the mean energies and directions times the boxes' overlap over
- * their volumes, scaled by a constant fitted on the training pairs).  The
- * network predicts each pair's mean yield (B + 1) e^mu over that baseline B
+ * holds its two photons).  Next to the features the kernels compute the
+ * paper's ST rate of the pair (Eq. rate, n_I n_II <sigma v>, for the two
+ * nodes read as boxes of uniform density moving with their mean velocities:
+ * W_A W_B (1e12 kappa sigma(sbar)) c |dbar_A - dbar_B| times the time integral
+ * of the boxes' overlap volume over the step, over V_A V_B; sbar from the
+ * geometric-mean energies and the mean directions).  B, that rate times a
+ * constant fitted on the training pairs, is the network's baseline: it
+ * predicts each pair's mean yield (B + 1) e^mu over B
  * (trained with a Poisson-type deviance, whose minimiser is the conditional
  * mean; trilens_mlp_grad loss_kind 1), times a calibration scale fitted on
  * the training pairs; pairs whose predicted standard deviation of y
@@ -384,7 +387,7 @@ int trilens_surrogate_collect(trilens_ctx *c, const int64_t *steps, int32_t n, i
 /* Train the network on the collected samples (feature normalisation from
  * the samples, He-initialised weights from `seed`, AdamW with cosine decay,
  * minibatches of 8192, `epochs` passes), then fit the calibration scales of
- * the network's and of the ST-form estimates on all the samples, and the
+ * the network's estimate and of the ST rate on all the samples, and the
  * network's per fallback threshold (on the samples the network keeps). */
 int trilens_surrogate_fit(trilens_ctx *c, int32_t epochs, uint64_t seed);
 
@@ -395,7 +398,9 @@ int trilens_surrogate_train(trilens_ctx *c, const int64_t *train_steps, int32_t 
 /* Surrogate yield of the built step (trilens_build(step) first) with a model
  * trained or loaded for the same level_L.  out (host, 8 doubles): [0] the
  * estimated weighted yield (network part plus exact fallback), [1] the
- * ST-form estimate of the same pairs (no network, calibrated), [2] level-L
+ * ST rate of the same pairs summed (no network, no fitted scale;
+ * trilens_surrogate_info [3] is the one scale fitted to it on the training
+ * pairs), [2] level-L
  * pairs, [3] pairs sent to the fallback, [4] their exact yield, [5] device
  * milliseconds of the whole surrogate path, [6] of network + estimate, [7]
  * of the cut traversal + features.  Adds [0] to the cumulative surrogate
@@ -403,13 +408,52 @@ int trilens_surrogate_train(trilens_ctx *c, const int64_t *train_steps, int32_t 
 int trilens_surrogate_step(trilens_ctx *c, int64_t step, int32_t level_L, float tau,
                            double out[8]);
 
+/* The level-L node pairs of the built step, for inspection and tests: what
+ * the surrogate step sees (ST regime at the cut, Sec. 2.2).  Every array is
+ * caller-owned host memory of the stated size, or NULL to skip it; arrays
+ * per pair hold the first min(cap, n_pairs) pairs.
+ *   cloud       2 x cap uint32: the pair's cut node in beam A and in beam B
+ *               (ids 0 .. of the level-L frontier of each tree)
+ *   feat        24 x cap FP32 features (see trilens_surrogate_dataset)
+ *   st          cap FP32: the ST rate of the pair -- the expected number of
+ *               pairs of Eq. rate for the two nodes as uniform boxes moving
+ *               with their mean velocities over the step (no fitted scale)
+ *   label       cap FP64: the pair's exact yield, sum of w_i w_j over its hits
+ *   pred        cap FP64: the network's estimate (0 where the pair falls back)
+ *   fallback    cap bytes: 1 where the predicted spread exceeds tau
+ *   net         2 x cap FP32: the network's outputs (mu, log variance)
+ *   cloud_of_a  n_a uint32: the cut node of every input photon of beam A
+ *   cloud_of_b  n_b uint32: the same for beam B
+ * n_pairs receives the number of pairs; fallback_exact the exact yield of the
+ * pairs that fall back (computed when pred, fallback or net is requested,
+ * which needs a model trained at level_L).  The cumulative yields are left
+ * unchanged.  INVALID for a step that is not built, a bad level, or a
+ * missing model. */
+typedef struct {
+  int64_t cap;
+  int64_t n_pairs;
+  uint32_t *cloud;
+  float *feat;
+  float *st;
+  double *label;
+  double *pred;
+  uint8_t *fallback;
+  float *net;
+  uint32_t *cloud_of_a;
+  uint32_t *cloud_of_b;
+  double fallback_exact;
+} trilens_sur_pairs;
+int trilens_surrogate_pairs(trilens_ctx *c, int64_t step, int32_t level_L, float tau,
+                            trilens_sur_pairs *out);
+
 /* [0] samples collected, [1] last training loss, [2] network calibration,
- * [3] ST-form calibration, [4] level L, [5] cumulative surrogate yield. */
+ * [3] the single scale of the ST rate fitted on the samples (sum of labels
+ * over sum of ST rates), [4] level L, [5] cumulative surrogate yield. */
 int trilens_surrogate_info(trilens_ctx *c, double out[6]);
 
 /* Copy the training set to host arrays of capacity cap: x (cap x 24 FP32
- * features), label (cap FP64 exact pair yields), st (cap FP32 uncalibrated
- * ST-form estimates); any may be NULL.  *n receives the number of samples. */
+ * features), label (cap FP64 exact pair yields), st (cap FP32 ST rates, no
+ * fitted scale); any may be NULL.  *n receives the number of samples. */
 int trilens_surrogate_dataset(trilens_ctx *c, float *x, double *label, float *st, int64_t cap,
                               int64_t *n);
 

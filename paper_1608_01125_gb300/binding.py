@@ -66,6 +66,16 @@ _lib = None
 PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "band", "yield")
 
 
+class SurPairs(ctypes.Structure):
+    """trilens_sur_pairs: host arrays of the level-L node pairs of a step."""
+    _fields_ = [("cap", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("cloud", ctypes.c_void_p), ("feat", ctypes.c_void_p), ("st", ctypes.c_void_p),
+                ("label", ctypes.c_void_p), ("pred", ctypes.c_void_p),
+                ("fallback", ctypes.c_void_p), ("net", ctypes.c_void_p),
+                ("cloud_of_a", ctypes.c_void_p), ("cloud_of_b", ctypes.c_void_p),
+                ("fallback_exact", ctypes.c_double)]
+
+
 def lib() -> ctypes.CDLL:
     """Load ``libtrilens.so`` (raises if it was not built)."""
     global _lib
@@ -150,8 +160,10 @@ def lib() -> ctypes.CDLL:
         L.trilens_surrogate_save.argtypes = [vp, ctypes.c_char_p]
         L.trilens_surrogate_load.argtypes = [vp, ctypes.c_char_p]
         L.trilens_surrogate_add_samples.argtypes = [vp, vp, vp, vp, i64, i32]
+        L.trilens_surrogate_pairs.argtypes = [vp, i64, i32, ctypes.c_float,
+                                              ctypes.POINTER(SurPairs)]
         for f in ("collect", "fit", "train", "step", "info", "dataset", "save", "load",
-                  "add_samples"):
+                  "add_samples", "pairs"):
             getattr(L, "trilens_surrogate_" + f).restype = ctypes.c_int
         L.trilens_yield_reduce_noalloc.argtypes = [vp, i64, vp, vp, vp, vp]
         L.trilens_yield_reduce_noalloc.restype = ctypes.c_int
@@ -342,6 +354,37 @@ class Collider:
                self.ctx)
         return dict(zip(("yield", "st_yield", "pairs", "fallback_pairs", "fallback_yield",
                          "ms", "ms_network", "ms_cut"), list(v)))
+
+    def surrogate_pairs(self, step: int, level_L: int, tau: float | None = None,
+                        labels: bool = True, cap: int = 1 << 22) -> dict:
+        """Build `step` and return its level-L node pairs (trilens_surrogate_pairs):
+        cut node ids, features, ST rates, exact labels (labels=True), and with
+        tau given the network's outputs, estimates and fallback flags; plus every
+        input photon's cut node in each beam."""
+        self.build(step)
+        na, nb = self.a["px"].numel(), self.b["px"].numel()
+        out = {"cloud": np.zeros((cap, 2), np.uint32), "feat": np.zeros((cap, 24), np.float32),
+               "st": np.zeros(cap, np.float32), "cloud_of_a": np.zeros(na, np.uint32),
+               "cloud_of_b": np.zeros(nb, np.uint32)}
+        if labels:
+            out["label"] = np.zeros(cap, np.float64)
+        if tau is not None:
+            out["pred"] = np.zeros(cap, np.float64)
+            out["fallback"] = np.zeros(cap, np.uint8)
+            out["net"] = np.zeros((cap, 2), np.float32)
+        sp = SurPairs(cap, 0, *[out[k].ctypes.data if k in out else None
+                                for k in ("cloud", "feat", "st", "label", "pred", "fallback",
+                                          "net", "cloud_of_a", "cloud_of_b")], 0.0)
+        _check(lib().trilens_surrogate_pairs(self.ctx, int(step), int(level_L),
+                                             float(1e30 if tau is None else tau), ctypes.byref(sp)),
+               self.ctx)
+        n = int(sp.n_pairs)
+        if n > cap:
+            return self.surrogate_pairs(step, level_L, tau, labels, n)
+        res = {k: (v[:n] if k not in ("cloud_of_a", "cloud_of_b") else v) for k, v in out.items()}
+        res["n_pairs"] = n
+        res["fallback_exact"] = sp.fallback_exact
+        return res
 
     def surrogate_info(self) -> dict:
         v = (ctypes.c_double * 6)()

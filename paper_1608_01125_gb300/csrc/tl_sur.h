@@ -49,7 +49,7 @@ cudaError_t launch_prefix_moments(const TLBeam &B, const float4 *pos, const floa
 cudaError_t launch_cut_level(const CutArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_features(const CutTree &A, const CutTree &B, const uint4 *cut,
                             const unsigned *cut_count, unsigned cap, float *feat, float *st,
-                            int blocks, cudaStream_t s);
+                            double dt, double kappa, int blocks, cudaStream_t s);
 cudaError_t launch_labels_prep(const CutTree &T, int L, uint32_t *cid_node, uint32_t *cid_slot,
                                uint2 *flist, unsigned *fcount, unsigned fcap, uint32_t *cut_of,
                                uint32_t *inv, cudaStream_t s);
@@ -67,7 +67,7 @@ cudaError_t launch_attribute(const uint2 *hits, const unsigned long long *nhits,
 cudaError_t launch_estimate(const float *out, const float *st, float st_scale, const uint4 *cut,
                             const unsigned *cut_count, unsigned cap, float tau, double *pred,
                             uint2 *fb, unsigned *fb_count, unsigned fb_cap, int blocks,
-                            cudaStream_t s);
+                            cudaStream_t s, uint8_t *flag = nullptr);
 // small helpers: op 0 copies cut refs (uint4 -> uint2), op 1 writes log1p of
 // doubles as floats, op 2 / op 3 add n doubles / floats into *c (a double)
 cudaError_t launch_sur_misc(int op, const void *a, const void *b, void *c, int64_t n,

@@ -234,13 +234,72 @@ cudaError_t launch_cut_level(const CutArgs &a, int blocks, cudaStream_t s) {
 
 // ------------------------------------------------------------ features
 
-// 24 features per node pair, and the ST-form rate estimate
-//   sum_w(A) sum_w(B) sigma(s_bar) V_overlap / (V_A V_B)
-// (s_bar from the geometric-mean energies and the mean directions); its
-// scale is fitted on training data.
+// The ST regime's rate for two clouds (Sec. 2.2, Eq. rate, Eq. reactivity).
+// A cloud is a level-L node read as a box of uniform density moving rigidly
+// with the mean velocity c dbar: its box at t_k is the node's swept box with
+// the step's travel c dt dbar taken off, so that it sweeps the node's box
+// over the step.  n_I n_II <sigma v> integrated over the overlap and the step:
+//   N = W_A W_B (1e12 kappa sigma(sbar)) c |dbar_A - dbar_B|
+//       * int_0^dt V_ov(t) dt / (V_A V_B),
+// with the collision area 1e12 kappa sigma [um^2] and sbar from the
+// geometric-mean energies and 1 - dbar_A . dbar_B.  V_ov(t) is the product of
+// three piecewise-linear overlap lengths: the integral is exact, Simpson's
+// rule on each piece between the times where an overlap length changes form.
+
+__device__ __forceinline__ double st_len(double la, double ua, double va, double lb, double ub,
+                                         double vb, double t) {
+  const double hi = fmin(ua + va * t, ub + vb * t), lo = fmax(la + va * t, lb + vb * t);
+  return hi > lo ? hi - lo : 0.0;
+}
+
+__device__ __forceinline__ double st_vol(const double *la, const double *ua, const double *va,
+                                         const double *lb, const double *ub, const double *vb,
+                                         double t) {
+  return st_len(la[0], ua[0], va[0], lb[0], ub[0], vb[0], t) *
+         st_len(la[1], ua[1], va[1], lb[1], ub[1], vb[1], t) *
+         st_len(la[2], ua[2], va[2], lb[2], ub[2], vb[2], t);
+}
+
+__device__ double st_overlap_time_integral(const double *la, const double *ua, const double *va,
+                                           const double *lb, const double *ub, const double *vb,
+                                           double T) {
+  double br[14];
+  int nb = 0;
+  br[nb++] = 0.0;
+  br[nb++] = T;
+  for (int q = 0; q < 3; ++q) {
+    const double w = vb[q] - va[q];
+    if (w == 0.0) continue;
+    const double c4[4] = {(ua[q] - ub[q]) / w, (la[q] - lb[q]) / w, (ua[q] - lb[q]) / w,
+                          (la[q] - ub[q]) / w};
+    for (int r = 0; r < 4; ++r)
+      if (c4[r] > 0.0 && c4[r] < T) br[nb++] = c4[r];
+  }
+  for (int i = 1; i < nb; ++i) {  // insertion sort of at most 14 times
+    const double v = br[i];
+    int j = i - 1;
+    while (j >= 0 && br[j] > v) {
+      br[j + 1] = br[j];
+      --j;
+    }
+    br[j + 1] = v;
+  }
+  double I = 0.0, f0 = st_vol(la, ua, va, lb, ub, vb, br[0]);
+  for (int i = 0; i + 1 < nb; ++i) {
+    const double t0 = br[i], t1 = br[i + 1];
+    const double f1 = st_vol(la, ua, va, lb, ub, vb, t1);
+    if (t1 > t0) I += (t1 - t0) * (f0 + 4.0 * st_vol(la, ua, va, lb, ub, vb, 0.5 * (t0 + t1)) + f1) / 6.0;
+    f0 = f1;
+  }
+  return I;
+}
+
+// 24 features per node pair, and the ST rate above (FP64 from the FP32 node
+// boxes and the FP64 prefix moments).  L = c dt [um].
 __global__ void __launch_bounds__(256) k_features(CutTree A, CutTree B, const uint4 *cut,
                                                   const unsigned *cut_count, unsigned cap,
-                                                  float *feat, float *st) {
+                                                  float *feat, float *st, double L, double dt,
+                                                  double kappa) {
   const unsigned n = min(*cut_count, cap);
   for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const uint4 c = cut[p];
@@ -285,22 +344,38 @@ __global__ void __launch_bounds__(256) k_features(CutTree A, CutTree B, const ui
     f[22] = (float)dbz;
     const double omc = 1.0 - (dax * dbx + day * dby + daz * dbz);
     f[23] = (float)omc;
-    // ST-form estimate
+    // the ST rate
     const double sbar = exp(mla + mlb) * omc / (2.0 * TL_MEC2 * TL_MEC2);
     const double sig = tl_sigma64(sbar);
-    const double ovx = fmax(0.0, (double)fminf(ba.hx, bb.hx) - (double)fmaxf(ba.lx, bb.lx));
-    const double ovy = fmax(0.0, (double)fminf(ba.hy, bb.hy) - (double)fmaxf(ba.ly, bb.ly));
-    const double ovz = fmax(0.0, (double)fminf(ba.hz, bb.hz) - (double)fmaxf(ba.lz, bb.lz));
-    const double va = fmax((double)(ba.hx - ba.lx) * (ba.hy - ba.ly) * (ba.hz - ba.lz), 1e-30);
-    const double vb = fmax((double)(bb.hx - bb.lx) * (bb.hy - bb.ly) * (bb.hz - bb.lz), 1e-30);
-    st[p] = (float)(swa * swb * sig * 1e30 * ovx * ovy * ovz / (va * vb));
+    const double loA[3] = {ba.lx, ba.ly, ba.lz}, hiA[3] = {ba.hx, ba.hy, ba.hz};
+    const double loB[3] = {bb.lx, bb.ly, bb.lz}, hiB[3] = {bb.hx, bb.hy, bb.hz};
+    const double dA[3] = {dax, day, daz}, dB[3] = {dbx, dby, dbz};
+    double la[3], ua[3], va[3], lb[3], ub[3], vb[3], VA = 1.0, VB = 1.0, dv2 = 0.0;
+    for (int q = 0; q < 3; ++q) {
+      const double DA = L * dA[q], DB = L * dB[q];
+      la[q] = loA[q] - fmin(0.0, DA);
+      ua[q] = hiA[q] - fmax(0.0, DA);
+      lb[q] = loB[q] - fmin(0.0, DB);
+      ub[q] = hiB[q] - fmax(0.0, DB);
+      va[q] = TL_C * dA[q];
+      vb[q] = TL_C * dB[q];
+      VA *= ua[q] - la[q];
+      VB *= ub[q] - lb[q];
+      dv2 += (va[q] - vb[q]) * (va[q] - vb[q]);
+    }
+    double rate = 0.0;
+    if (sig > 0.0 && VA > 0.0 && VB > 0.0) {
+      const double I = st_overlap_time_integral(la, ua, va, lb, ub, vb, dt);
+      if (I > 0.0) rate = swa * swb * (1e12 * kappa * sig) * sqrt(dv2) * I / (VA * VB);
+    }
+    st[p] = (float)rate;
   }
 }
 
 cudaError_t launch_features(const CutTree &A, const CutTree &B, const uint4 *cut,
                             const unsigned *cut_count, unsigned cap, float *feat, float *st,
-                            int blocks, cudaStream_t s) {
-  k_features<<<blocks, 256, 0, s>>>(A, B, cut, cut_count, cap, feat, st);
+                            double dt, double kappa, int blocks, cudaStream_t s) {
+  k_features<<<blocks, 256, 0, s>>>(A, B, cut, cut_count, cap, feat, st, TL_C * dt, dt, kappa);
   return cudaGetLastError();
 }
 
@@ -483,7 +558,7 @@ cudaError_t launch_attribute(const uint2 *hits, const unsigned long long *nhits,
 // fallback (their refs copied out).
 __global__ void k_estimate(const float *out, const float *st, float st_scale, const uint4 *cut,
                            const unsigned *cut_count, unsigned cap, float tau, double *pred,
-                           uint2 *fb, unsigned *fb_count, unsigned fb_cap) {
+                           uint2 *fb, unsigned *fb_count, unsigned fb_cap, uint8_t *flag) {
   const unsigned n = min(*cut_count, cap);
   const int lane = threadIdx.x & 31;
   const unsigned nround = (n + 31u) & ~31u;
@@ -498,6 +573,7 @@ __global__ void k_estimate(const float *out, const float *st, float st_scale, co
       // the predicted mean (B + 1) e^mu with baseline B = st_scale * st
       const double e = ((double)st_scale * (double)st[p] + 1.0) * exp(fmin((double)mu, 30.0));
       pred[p] = fall ? 0.0 : fmax(e, 0.0);
+      if (flag) flag[p] = fall ? 1 : 0;
       const uint4 c = cut[p];
       r = make_uint2(c.x, c.y);
     }
@@ -517,9 +593,9 @@ __global__ void k_estimate(const float *out, const float *st, float st_scale, co
 cudaError_t launch_estimate(const float *out, const float *st, float st_scale, const uint4 *cut,
                             const unsigned *cut_count, unsigned cap, float tau, double *pred,
                             uint2 *fb, unsigned *fb_count, unsigned fb_cap, int blocks,
-                            cudaStream_t s) {
+                            cudaStream_t s, uint8_t *flag) {
   k_estimate<<<blocks, 256, 0, s>>>(out, st, st_scale, cut, cut_count, cap, tau, pred, fb,
-                                    fb_count, fb_cap);
+                                    fb_count, fb_cap, flag);
   return cudaGetLastError();
 }
 

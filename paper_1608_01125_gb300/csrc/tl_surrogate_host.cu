@@ -239,7 +239,7 @@ static int sur_cut(trilens_ctx *c, int L, unsigned *ncut) {
     if (left > 0) return fail(c, TRILENS_ERR_STACK, "cut traversal did not finish");
     if (!(st & TL_ST_FRONT_OVF)) {
       CK(tl::launch_features(a.A, a.B, s->cut, s->cut_count, s->cut_cap, s->feat, s->st,
-                             4 * c->n_sm, c->stream));
+                             c->p.dt_fs, c->p.kappa, 4 * c->n_sm, c->stream));
       return TRILENS_OK;
     }
     int rc = cut_buffers(c, std::max(2 * s->cut_cap, *ncut + (*ncut >> 2) + 1024));
@@ -248,9 +248,10 @@ static int sur_cut(trilens_ctx *c, int L, unsigned *ncut) {
   return fail(c, TRILENS_ERR_STACK, "cut lists kept overflowing");
 }
 
-// exact yield of every cut pair (label[p]) for the built step; returns the
-// step's exact total through *total
-static int sur_labels(trilens_ctx *c, int L, double ct, unsigned ncut, double *total) {
+// ids of the level-L frontier nodes of both trees (every photon's id in
+// cut_of, the input -> sorted map in inv) and of every cut pair (cut[p].z,
+// cut[p].w), with the pairs' hash index
+static int sur_ids(trilens_ctx *c, int L) {
   SurrogateState *s = c->sur;
   tl::CutTree A = cut_tree(c, 0), B = cut_tree(c, 1);
   CK(cudaMemsetAsync(s->fcount, 0, sizeof(unsigned) * 2, c->stream));
@@ -264,6 +265,15 @@ static int sur_labels(trilens_ctx *c, int L, double ct, unsigned ncut, double *t
   CK(tl::launch_pair_index(A, B, s->cut, s->cut_count, s->cut_cap, s->cid_node[0], s->cid_slot[0],
                            s->cid_node[1], s->cid_slot[1], s->hkey, s->hval, s->hmask, s->status,
                            4 * c->n_sm, c->stream));
+  return TRILENS_OK;
+}
+
+// exact yield of every cut pair (label[p]) for the built step; returns the
+// step's exact total through *total
+static int sur_labels(trilens_ctx *c, int L, double ct, unsigned ncut, double *total) {
+  SurrogateState *s = c->sur;
+  int rc0 = sur_ids(c, L);
+  if (rc0) return rc0;
   // the cut pairs' node references seed the exact traversal
   CK(tl::launch_sur_misc(0, s->cut, nullptr, s->seeds, ncut, c->stream));
   int retries = 0;
@@ -609,7 +619,7 @@ int trilens_surrogate_step(trilens_ctx *c, int64_t step, int32_t level_L, float 
   const double yield = cal * est + fb_exact;
   s->tot += yield;
   out[0] = yield;                 // surrogate estimate of the step's weighted yield
-  out[1] = s->st_only_calib * st;  // the ST-form estimate (no network), same pairs
+  out[1] = st;                    // the ST rate of the same pairs (no network, no scale)
   out[2] = (double)ncut;          // node pairs at level L
   out[3] = (double)nfb;           // pairs sent to the exact fallback
   out[4] = fb_exact;              // their exact yield
@@ -617,6 +627,86 @@ int trilens_surrogate_step(trilens_ctx *c, int64_t step, int32_t level_L, float 
   out[6] = ms_mlp;                // network + estimate [ms]
   out[7] = ms_cut;                // cut traversal + features [ms]
   return TRILENS_OK;
+}
+
+int trilens_surrogate_pairs(trilens_ctx *c, int64_t step, int32_t level_L, float tau,
+                            trilens_sur_pairs *o) {
+  if (!c || !o || o->cap < 0 || level_L < 1 || level_L > 63) return TRILENS_ERR_INVALID;
+  if (c->n_inst > 1) return fail(c, TRILENS_ERR_INVALID, "surrogate on a batch context");
+  if (step != c->built_step) return fail(c, TRILENS_ERR_INVALID, "step not built");
+  const bool want_net = o->pred || o->fallback || o->net;
+  if (want_net && (!c->sur || !c->sur->trained || c->sur->level != level_L))
+    return fail(c, TRILENS_ERR_INVALID, "no surrogate model for level %d", level_L);
+  CK(cudaSetDevice(c->device));
+  int rc = ensure_state(c);
+  if (rc) return rc;
+  SurrogateState *s = c->sur;
+  const double keep_c = c->tot_count, keep_w = c->tot_weighted;
+  unsigned ncut = 0;
+  if ((rc = sur_cut(c, level_L, &ncut))) return rc;
+  o->n_pairs = ncut;
+  o->fallback_exact = 0.0;
+  if (ncut == 0) return TRILENS_OK;
+  if (o->label) {
+    double total = 0.0;
+    if ((rc = sur_labels(c, level_L, TL_C * ((double)step * c->p.dt_fs), ncut, &total))) return rc;
+  } else if ((rc = sur_ids(c, level_L))) {
+    return rc;
+  }
+  uint8_t *flag = nullptr;
+  if (want_net) {
+    CK(dalloc(&flag, ncut));
+    CK(tl::mlp_pack(s->prm, s->work, c->stream));
+    CK(tl::mlp_forward(s->prm, s->norm, s->work, s->feat, ncut, s->out, c->n_sm,
+                       c->p.spin_limit, c->stream));
+    CK(cudaMemsetAsync(s->fb_count, 0, sizeof(unsigned), c->stream));
+    CK(tl::launch_estimate(s->out, s->st, (float)s->st_calib, s->cut, s->cut_count, s->cut_cap,
+                           tau, s->pred, s->fb, s->fb_count, s->cut_cap, 4 * c->n_sm, c->stream,
+                           flag));
+    unsigned nfb = 0;
+    CK(cudaMemcpyAsync(&nfb, s->fb_count, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (nfb > 0) {
+      int retries = 0;
+      rc = run_exact(c, TL_C * ((double)step * c->p.dt_fs), s->fb, nfb, &retries);
+      if (rc) {
+        cudaFree(flag);
+        return rc;
+      }
+      o->fallback_exact = c->ctr_host->weighted;
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  const int64_t m = std::min<int64_t>(o->cap, ncut);
+  int err = 0;
+  if (m > 0) {
+    std::vector<uint4> cut((size_t)m);
+    err |= cudaMemcpy(cut.data(), s->cut, sizeof(uint4) * m, cudaMemcpyDeviceToHost);
+    if (o->cloud)
+      for (int64_t p = 0; p < m; ++p) {
+        o->cloud[2 * p] = cut[p].z;
+        o->cloud[2 * p + 1] = cut[p].w;
+      }
+    if (o->feat) err |= cudaMemcpy(o->feat, s->feat, sizeof(float) * 24 * m, cudaMemcpyDeviceToHost);
+    if (o->st) err |= cudaMemcpy(o->st, s->st, sizeof(float) * m, cudaMemcpyDeviceToHost);
+    if (o->label) err |= cudaMemcpy(o->label, s->label, sizeof(double) * m, cudaMemcpyDeviceToHost);
+    if (o->pred) err |= cudaMemcpy(o->pred, s->pred, sizeof(double) * m, cudaMemcpyDeviceToHost);
+    if (o->fallback) err |= cudaMemcpy(o->fallback, flag, m, cudaMemcpyDeviceToHost);
+    if (o->net) err |= cudaMemcpy(o->net, s->out, sizeof(float) * 2 * m, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(flag);
+  uint32_t *cof[2] = {o->cloud_of_a, o->cloud_of_b};
+  for (int k = 0; k < 2 && !err; ++k) {
+    const int64_t n = c->beam[k].n;
+    if (!cof[k] || n <= 0) continue;
+    std::vector<uint32_t> cut_of((size_t)n), inv((size_t)n);
+    err |= cudaMemcpy(cut_of.data(), s->cut_of[k], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+    err |= cudaMemcpy(inv.data(), s->inv[k], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+    for (int64_t i = 0; i < n && !err; ++i) cof[k][i] = cut_of[inv[i]];
+  }
+  c->tot_count = keep_c;
+  c->tot_weighted = keep_w;
+  return err ? fail(c, TRILENS_ERR_CUDA, "copying the cut pairs failed") : TRILENS_OK;
 }
 
 int trilens_surrogate_info(trilens_ctx *c, double out[6]) {

@@ -145,6 +145,28 @@ def statistical_1e8(n: int = 100_000_000, steps: int = 32, seed: int = 0) -> Wor
     return Workload("statistical_2x1e8", s, s, 0.0, C_UM_PER_FS * 16 * dt, dt, steps, 1e12, seed)
 
 
+def statistical_family(i: int, n: int = 1_000_000, steps: int = 32,
+                       kappa: float = 2e13) -> Workload:
+    """Member ``i`` of a family of statistical workloads with varied beam
+    shapes, drawn as the batching workload draws its instances: crossing
+    angle U[0, pi/2], median energy log-uniform in [0.5, 50] MeV (Gamma
+    spectrum of shape 2, as the statistical workload), transverse sigma
+    U[0.5, 2] um.  Otherwise as the statistical workload: weights U[1, 10],
+    sigma_z = 20 um, 10 mrad, steps of 20 fs with the centres c*16*dt behind
+    the meeting point.  The shape is drawn from ``PCG64(2_000_003 + i)``; the
+    photons from ``PCG64(3_000_017 + i)``."""
+    rng = np.random.Generator(np.random.PCG64(2_000_003 + i))
+    crossing = rng.uniform(0.0, math.pi / 2)
+    med = math.exp(rng.uniform(math.log(0.5), math.log(50.0)))
+    st = rng.uniform(0.5, 2.0)
+    # the median of Gamma(2, scale) is 1.678347 scale
+    s = _spec(n, (st, st), 20.0, 10e-3, ("gamma", 2.0, med / 1.6783469900166608),
+              ("uniform", 1.0, 10.0))
+    dt = 20.0
+    return Workload(f"statistical_family_{i}", s, s, crossing, C_UM_PER_FS * 16 * dt, dt,
+                    steps, kappa, 3_000_017 + i)
+
+
 def crossing90_5e7(n: int = 50_000_000, steps: int = 256, seed: int = 0) -> Workload:
     """2 x 5e7 photons crossing at 90 deg, Gamma(1.5, 13.33 MeV), kappa 1e12.
 

@@ -5,10 +5,15 @@ level L = 14, about 60 photons per level-L node):
 - the level-L pairs' exact labels add up to the step's exact yield, and
   every level-L node pair's features are consistent;
 - a network trained on two seeds estimates another seed's yield within 1%,
-  no worse (within half a percent) than the calibrated ST-form estimate (the
-  same cut without a network), and with the fallback at tau = 0 returns the
-  exact yield;
-- the surrogate path is faster than the exact traversal of the same step."""
+  and with the fallback at tau = 0 returns the exact yield;
+- with the fallback threshold at the 80th percentile of the predicted spread
+  (about a fifth of the pairs fall back), the fallback's exact yield equals
+  the oracle's hits restricted to exactly those pairs;
+- over a family of beam shapes (crossing angle, median energy and transverse
+  size drawn as the batching workload draws them), a network trained on some
+  shapes estimates held-out shapes' yields better than the paper's ST rate
+  without a network and than that rate times one scale fitted on the
+  training shapes."""
 import math
 import os
 
@@ -94,13 +99,97 @@ def test_surrogate_generalises(trained):
             ms_sur += r["ms"]
         err_nn = abs(sur - exact) / exact
         err_st = abs(stv - exact) / exact
-        print(f"exact {exact:.6g} surrogate {sur:.6g} ({err_nn:.2%}) ST {stv:.6g} ({err_st:.2%}) "
+        scale = trained["info"]["st_calib"]
+        err_sc = abs(scale * stv - exact) / exact
+        print(f"exact {exact:.6g} surrogate {sur:.6g} ({err_nn:.2%}) ST rate {stv:.6g} "
+              f"({err_st:.2%}) ST rate x {scale:.4g} ({err_sc:.2%}) "
               f"time exact {ms_exact:.2f} ms surrogate {ms_sur:.2f} ms")
         assert err_nn < 0.01
-        assert err_nn < err_st + 0.005
         # full fallback: every pair evaluated exactly
         r = col.surrogate_step(16, L, tau=0.0)
         col.build(16)
         col.collide(16)
         assert r["fallback_pairs"] == r["pairs"]
         assert math.isclose(r["yield"], col.stats()["weighted"], rel_tol=1e-9)
+
+
+def test_partial_fallback_equals_oracle_on_the_fallback_pairs(trained):
+    import oracle
+    wl = synth.statistical_1e8(n=N, seed=0)
+    a, b = synth.beams(wl)
+    step = 16
+    with binding.Collider(a, b, wl.dt, KAPPA) as col:
+        col.surrogate_load(trained["path"])
+        g0 = col.surrogate_pairs(step, L, tau=1e30, labels=False)
+        spread = np.sqrt(np.exp(np.clip(g0["net"][:, 1].astype(np.float64), -12, 12)))
+        tau = float(np.quantile(spread, 0.8))
+        g = col.surrogate_pairs(step, L, tau=tau, labels=True)
+        r = col.surrogate_step(step, L, tau)
+    fb = g["fallback"].astype(bool)
+    frac = fb.mean()
+    print(f"tau {tau:.4g}: {fb.sum()} of {len(fb)} pairs fall back, exact {g['fallback_exact']:.6g}")
+    assert 0.1 < frac < 0.3
+    assert (g["pred"][fb] == 0).all() and (g["pred"][~fb] > 0).any()
+    # the fallback's exact yield is its pairs' exact labels...
+    assert math.isclose(g["fallback_exact"], g["label"][fb].sum(), rel_tol=1e-9)
+    # ...and the oracle's hits restricted to exactly those pairs
+    hits, _ = oracle.tree(a, b, step, wl.dt, KAPPA, nthreads=os.cpu_count() or 1, cap=1 << 23)
+    lab, outside = oracle.cloud_labels(a, b, hits, g["cloud_of_a"], g["cloud_of_b"], g["cloud"])
+    assert outside == 0
+    assert math.isclose(g["fallback_exact"], lab[fb].sum(), rel_tol=1e-9)
+    assert math.isclose(r["fallback_yield"], lab[fb].sum(), rel_tol=1e-9)
+    assert r["fallback_pairs"] == fb.sum()
+
+
+FAMILY_TRAIN = list(range(1, 9))
+FAMILY_TEST = [101, 102, 103, 104]
+
+
+def _family_yields(i, model, steps):
+    wl = synth.statistical_family(i, n=N)
+    a, b = synth.beams(wl)
+    exact = sur = stv = 0.0
+    with binding.Collider(a, b, wl.dt, wl.kappa) as col:
+        col.surrogate_load(model)
+        for k in steps:
+            col.build(k)
+            col.collide(k)
+            exact += col.stats()["weighted"]
+            r = col.surrogate_step(k, L)
+            sur += r["yield"]
+            stv += r["st_yield"]
+    return exact, sur, stv
+
+
+def test_network_gains_over_st_rate_on_held_out_shapes(tmp_path):
+    """Train on 8 shapes of the family, estimate 4 other shapes: the network's
+    mean absolute yield error is below that of the ST rate alone and of the
+    ST rate times the one scale fitted on the training shapes."""
+    import __graft_entry__
+    __graft_entry__.build()
+    steps = list(range(6, 27))
+    model = str(tmp_path / "family.bin")
+    first = synth.statistical_family(FAMILY_TRAIN[0], n=N)
+    a0, b0 = synth.beams(first)
+    with binding.Collider(a0, b0, first.dt, first.kappa) as col:
+        col.surrogate_collect(steps, L)
+        for i in FAMILY_TRAIN[1:]:
+            wl = synth.statistical_family(i, n=N)
+            a, b = synth.beams(wl)
+            with binding.Collider(a, b, wl.dt, wl.kappa) as cx:
+                cx.surrogate_collect(steps, L)
+                x, lab, st = cx.surrogate_dataset()
+            col.surrogate_add_samples(x, lab, st, L)
+        col.surrogate_fit(epochs=30, seed=11)
+        scale = col.surrogate_info()["st_calib"]
+        col.surrogate_save(model)
+    errs = []
+    for i in FAMILY_TEST:
+        exact, sur, stv = _family_yields(i, model, steps)
+        e = ((sur - exact) / exact, (stv - exact) / exact, (scale * stv - exact) / exact)
+        errs.append(e)
+        print(f"shape {i}: exact {exact:.6g} network {e[0]:+.2%} ST rate {e[1]:+.2%} "
+              f"ST rate x {scale:.4g} {e[2]:+.2%}")
+    m = np.abs(np.array(errs)).mean(axis=0)
+    print(f"mean |error|: network {m[0]:.2%} ST rate {m[1]:.2%} scaled ST rate {m[2]:.2%}")
+    assert m[0] < m[1] and m[0] < m[2]
