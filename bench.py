@@ -492,8 +492,14 @@ def run_ours(args, wl):
         work.update(node_tests=r["node_tests"], leaf_pairs=r["leaf_pairs"])
         return r["count"], r["narrow_tests"], r["band"]
 
-    tuned = col.autotune([2, 4, 40], os.path.join(ROOT, "paper_1608_01125_gb300",
-                                                   "_tuning_cache.json")) if args.tune else col.tuning()
+    if args.knobs:  # fixed knobs (profiling): bucket, stack depth, warps per block, budget
+        col.set_tuning(*[int(x) for x in args.knobs.split(",")])
+        tuned = col.tuning()
+    elif args.tune:
+        tuned = col.autotune([2, 4, 40], os.path.join(ROOT, "paper_1608_01125_gb300",
+                                                      "_tuning_cache.json"))
+    else:
+        tuned = col.tuning()
     for _ in range(max(args.warmup, 0)):
         graph_run()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -781,6 +787,9 @@ def main():
                     help="skip the IP-regime leg (swarm split + exact run of real photons)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the autotuner (default knobs)")
+    ap.add_argument("--knobs", default="",
+                    help="fixed traversal knobs instead of the autotuner: leaf bucket, stack "
+                         "depth, warps per block, budget (comma-separated)")
     ap.add_argument("--photons", type=int, default=1 << 20)
     ap.add_argument("--workload", default="headon_2x1M",
                     choices=("headon_2x1M", "batch256", "statistical"))

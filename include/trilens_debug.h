@@ -44,7 +44,7 @@ int trilens_debug_set_key_bits(trilens_ctx *c, int32_t bits);
  * INVALID for a NULL context. */
 int trilens_debug_set_cut_cap(trilens_ctx *c, int32_t cap);
 
-/* Replace the internal hit, band and hand-on buffers with buffers of cap
+/* Replace the internal hit, band, leaf-pair and hand-on buffers with buffers of cap
  * pairs each (>= 1), so that the next collisions overflow them and exercise
  * the regrow-and-repeat path.  Synchronises the stream.  INVALID for a NULL
  * context or cap < 1. */
@@ -61,12 +61,13 @@ int trilens_debug_eval64(const double *x, double *out, int64_t n, int32_t which,
 /* Per-phase device time.  on != 0 records CUDA events around every kernel
  * phase on the context's stream (cheap, but adds event records).  The
  * phases, in order: 0 propagate+Morton, 1 radix sort, 2 gather, 3 hierarchy
- * emit, 4 refit, 5 frontier expansion, 6 traversal+narrow phase, 7 FP64 band
- * re-test, 8 yield reduction. */
+ * emit, 4 refit, 5 frontier (seeds, expansion, widening), 6 dual traversal
+ * (listing the overlapping leaf-bucket pairs), 7 FP64 band re-test, 8 yield
+ * reduction, 9 FP32 narrow phase of the listed leaf pairs. */
 int trilens_debug_timing(trilens_ctx *c, int on);
 
-/* Copy the accumulated milliseconds of the 9 phases into out[0..8], the
- * launches of each phase into launches[0..8] (either may be NULL), then zero
+/* Copy the accumulated milliseconds of the 10 phases into out[0..9], the
+ * launches of each phase into launches[0..9] (either may be NULL), then zero
  * them if reset != 0.  Accumulated at each trilens_collide_step (which
  * synchronises). */
 int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int reset);

@@ -63,7 +63,8 @@ _lock = threading.Lock()
 _lib = None
 
 #: kernel phases reported by Collider.phase_ms (trilens_debug_phase_ms order)
-PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "band", "yield")
+PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "band", "yield",
+          "narrow")
 
 
 class SurPairs(ctypes.Structure):
@@ -313,8 +314,8 @@ class Collider:
         _check(lib().trilens_debug_timing(self.ctx, int(bool(on))), self.ctx)
 
     def phase_ms(self, reset: bool = False) -> tuple[dict, dict]:
-        ms = (ctypes.c_double * 9)()
-        ln = (ctypes.c_int64 * 9)()
+        ms = (ctypes.c_double * len(PHASES))()
+        ln = (ctypes.c_int64 * len(PHASES))()
         _check(lib().trilens_debug_phase_ms(self.ctx, ms, ln, int(bool(reset))), self.ctx)
         return dict(zip(PHASES, list(ms))), dict(zip(PHASES, list(ln)))
 

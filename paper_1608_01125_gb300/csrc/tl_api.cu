@@ -23,6 +23,9 @@ cudaError_t launch_seed_cut(const TravArgs &a, const uint32_t *cutA, const unsig
                             uint32_t capA, const uint32_t *cutB, const unsigned *cntB,
                             uint32_t capB, uint2 *F0, unsigned cap, int blocks, cudaStream_t s);
 cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm);
+cudaError_t launch_widen(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
+                         int levels, int blocks, cudaStream_t s);
+cudaError_t launch_narrow(const TravArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
                             unsigned long long list_n, int from_frontier, int budget, int blocks,
                             int warps, cudaStream_t s);
@@ -40,7 +43,28 @@ cudaError_t launch_step_finish(const TLCounters *ctr, unsigned *run_status, TLRu
                                cudaStream_t s);
 }  // namespace tl
 
-enum { PH_PROP = 0, PH_SORT, PH_GATHER, PH_EMIT, PH_REFIT, PH_EXPAND, PH_TRAV, PH_BAND, PH_YIELD };
+enum {
+  PH_PROP = 0, PH_SORT, PH_GATHER, PH_EMIT, PH_REFIT, PH_EXPAND, PH_TRAV, PH_BAND, PH_YIELD,
+  PH_NARROW, PH_COUNT
+};
+
+// breadth-first levels that may widen the seed frontier of a large problem
+// (each a launch that does nothing once the frontier holds widen_target pairs)
+constexpr int kWidenLevels = 5;
+// node pairs per traversal queue chunk and frontier item (tl_traverse.cu)
+constexpr unsigned long long kQueueChunk = 32;
+
+// the frontier widening target: 64 pairs per resident traversal warp, two
+// full items each; and the frontier buffers' capacity for every start
+static void frontier_sizes(trilens_ctx *c, unsigned *target, unsigned *cap) {
+  const long long warps = (long long)c->trav_blocks * c->trav_warps;
+  *target = (unsigned)std::min<long long>(64ll * warps, 1 << 22);
+  const unsigned long long need =
+      std::max({(unsigned long long)c->n_inst + 4ull * c->front_target + 64,
+                (unsigned long long)c->w[0].cut_cap * c->w[1].cut_cap + 64,
+                4ull * *target + 64});
+  *cap = (unsigned)std::min<unsigned long long>(need, 0xFFFFFFF0ull);
+}
 
 static void tmark(trilens_ctx *c, int ph, int k, int end) {
   if (!c->timing) return;
@@ -50,7 +74,7 @@ static void tmark(trilens_ctx *c, int ph, int k, int end) {
 
 // add the elapsed time of every recorded phase (the stream is synchronised)
 static void tcollect(trilens_ctx *c) {
-  for (int ph = 0; ph < 9; ++ph)
+  for (int ph = 0; ph < PH_COUNT; ++ph)
     for (int k = 0; k < 2; ++k)
       if (c->ev_pending[ph][k]) {
         float ms = 0.f;
@@ -216,6 +240,7 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFree(c->run_acc);
   cudaFree(c->hits);
   cudaFree(c->band);
+  cudaFree(c->leaves);
   cudaFree(c->ctr);
   cudaFree(c->partials);
   cudaFree(c->build_status);
@@ -235,7 +260,10 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFreeHost(c->run_status_host);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  for (int ph = 0; ph < 9; ++ph)
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  for (int ph = 0; ph < PH_COUNT; ++ph)
     for (int k = 0; k < 2; ++k)
       for (int e = 0; e < 2; ++e)
         if (c->ev[ph][k][e]) cudaEventDestroy(c->ev[ph][k][e]);
@@ -253,7 +281,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   if (p->leaf_bucket < 0 || p->leaf_bucket > 32) return TRILENS_ERR_INVALID;
   if (p->stack_depth != 0 && (p->stack_depth < 64 || p->stack_depth > 4096))
     return TRILENS_ERR_INVALID;
-  if (p->block_shape < 0 || p->block_shape > 16) return TRILENS_ERR_INVALID;
+  if (p->block_shape < 0 || p->block_shape > TL_TRAV_MAX_WARPS) return TRILENS_ERR_INVALID;
   if (p->spin_limit < 0) return TRILENS_ERR_INVALID;
 
   trilens_ctx *c = new trilens_ctx();
@@ -326,7 +354,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   c->trav_blocks = bps * c->n_sm;
   c->expand_blocks = 2 * c->n_sm;
   c->front_target = (unsigned)std::min<long long>(2ll * c->trav_blocks * c->trav_warps, 1 << 16);
-  c->front_cap = std::max(4 * c->front_target + 64, c->w[0].cut_cap * c->w[1].cut_cap + 64);
+  frontier_sizes(c, &c->widen_target, &c->front_cap);
   CK(dalloc(&c->front[0], c->front_cap));
   CK(dalloc(&c->front[1], c->front_cap));
   {
@@ -342,6 +370,12 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   CK(dalloc(&c->hits, c->hit_cap));
   c->band_cap = std::max<unsigned long long>(1 << 16, (c->beam[0].n + c->beam[1].n) / 4);
   CK(dalloc(&c->band, c->band_cap));
+  // leaf pairs: 16 per photon to start (a busy step of 2 x 1M head-on lists
+  // ~2.6e7 with single-photon buckets), at most 2^27 (1 GiB) before a step
+  // asks for more
+  c->leaf_cap = std::min<unsigned long long>(
+      std::max<unsigned long long>(1 << 20, 16ull * (c->beam[0].n + c->beam[1].n)), 1ull << 27);
+  CK(dalloc(&c->leaves, c->leaf_cap));
   CK(dalloc(&c->ctr, 1));
   CK(cudaMallocHost((void **)&c->ctr_host, sizeof(TLCounters)));
   c->yield_blocks = 4 * c->n_sm;
@@ -357,9 +391,23 @@ int trilens_build(trilens_ctx *c, int64_t step) {
   CK(cudaSetDevice(c->device));
   const double ct = TL_C * ((double)step * c->p.dt_fs);
   const double T = ct + 0.5 * c->L64;
+  // the two beams' builds share nothing but the status word (set with
+  // atomic OR): beam B's runs on a side stream, forked from the context's
+  // stream and joined back before anything that reads the hierarchies (in a
+  // captured run this is a fork and a join in the graph).  Per-phase timing
+  // keeps them on one stream, one after the other.
+  const bool fork = !c->timing && c->beam[0].n > 0 && c->beam[1].n > 0;
+  if (fork) {
+    if (!c->side_stream) CK(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+    if (!c->fork_ev) CK(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    if (!c->join_ev) CK(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(c->fork_ev, c->stream));
+    CK(cudaStreamWaitEvent(c->side_stream, c->fork_ev, 0));
+  }
   for (int k = 0; k < 2; ++k) {
     const int64_t n = c->beam[k].n;
     if (n <= 0) continue;
+    cudaStream_t st = (fork && k == 1) ? c->side_stream : c->stream;
     // Morton box of the step: per axis the mean of the swept boxes' centres
     // c = p0 + T d +- 5 standard deviations, in closed form from the beam's
     // moments (centres outside are clamped to the edge cells).  Unlike the
@@ -381,33 +429,37 @@ int trilens_build(trilens_ctx *c, int64_t step) {
     tmark(c, PH_PROP, k, 0);
     if (c->n_inst > 1) {
       CK(tl::launch_inst_box(c->inst_bounds[k], c->n_inst, T, c->bits[k], c->inst_box[k],
-                             c->stream));
-      CK(cudaMemsetAsync(c->inst_root[k], 0xff, sizeof(uint32_t) * c->n_inst, c->stream));
+                             st));
+      CK(cudaMemsetAsync(c->inst_root[k], 0xff, sizeof(uint32_t) * c->n_inst, st));
     }
     CK(tl::launch_propagate(c->beam[k], ct, (float)c->L64, lo, scale, c->bits[k], w,
                             c->n_inst > 1 ? c->inst_box[k] : nullptr,
-                            n > 1 ? (c->key_bits[k] + 7) / 8 : 0, c->stream));
+                            n > 1 ? (c->key_bits[k] + 7) / 8 : 0, st));
     tmark(c, PH_PROP, k, 1);
     tmark(c, PH_SORT, k, 0);
     CK(tl::launch_sort(w, n, c->key_bits[k], c->p.spin_limit, c->debug_stall_sort,
-                       c->build_status, &c->sel[k], c->stream));
+                       c->build_status, &c->sel[k], st));
     tmark(c, PH_SORT, k, 1);
     if (n <= 1) {  // no sort: copy the one photon (a longer beam is gathered by the sort)
       tmark(c, PH_GATHER, k, 0);
-      CK(tl::launch_gather(w, n, c->sel[k], c->stream));
+      CK(tl::launch_gather(w, n, c->sel[k], st));
       tmark(c, PH_GATHER, k, 1);
       c->phase_launches[PH_GATHER] += 1;
     }
     tmark(c, PH_EMIT, k, 0);
-    CK(tl::launch_karras(w, n, c->sel[k], c->p.leaf_bucket, c->stream));
+    CK(tl::launch_karras(w, n, c->sel[k], c->p.leaf_bucket, st));
     tmark(c, PH_EMIT, k, 1);
     tmark(c, PH_REFIT, k, 0);
-    CK(tl::launch_refit(w, n, c->L_lo, c->L_hi, c->half, c->n_sm, c->stream));
+    CK(tl::launch_refit(w, n, c->L_lo, c->L_hi, c->half, c->n_sm, st));
     tmark(c, PH_REFIT, k, 1);
     c->phase_launches[PH_PROP] += 1;
     c->phase_launches[PH_SORT] += n > 1 ? 1 + (c->key_bits[k] + 7) / 8 : 0;
     c->phase_launches[PH_EMIT] += 1;
     c->phase_launches[PH_REFIT] += tl::refit_tiles(n) > 1 ? 3 : 1;
+  }
+  if (fork) {
+    CK(cudaEventRecord(c->join_ev, c->side_stream));
+    CK(cudaStreamWaitEvent(c->stream, c->join_ev, 0));
   }
   c->built_step = step;
   return TRILENS_OK;
@@ -438,10 +490,13 @@ tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   a.hit_cap = c->hit_cap;
   a.band = c->band;
   a.band_cap = c->band_cap;
+  a.leaves = c->leaves;
+  a.leaf_cap = c->leaf_cap;
   a.queue = reinterpret_cast<unsigned long long *>(c->queue);
   a.queue_cap = c->queue_cap;
   a.spin_limit = c->p.spin_limit;
   a.stack_depth = c->p.stack_depth;
+  a.leaf_bucket = c->p.leaf_bucket;
   a.build_status = c->build_status;
   return a;
 }
@@ -463,6 +518,9 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
       CK(tl::launch_seed_cut(a, c->w[0].cut, c->w[0].cut_n, c->w[0].cut_cap, c->w[1].cut,
                              c->w[1].cut_n, c->w[1].cut_cap, c->front[0], c->front_cap,
                              2 * c->n_sm, c->stream));
+      CK(tl::launch_widen(a, c->front[0], c->front[1], c->front_cap, c->widen_target,
+                          kWidenLevels, 4 * c->n_sm, c->stream));
+      c->phase_launches[PH_EXPAND] += kWidenLevels;
     } else if (!seeds) {
       if (c->n_inst > 1)
         CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
@@ -481,6 +539,10 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
                              c->trav_warps, c->stream));
     tmark(c, PH_TRAV, 0, 1);
     c->phase_launches[PH_TRAV] += 1;
+    tmark(c, PH_NARROW, 0, 0);
+    CK(tl::launch_narrow(a, 8 * c->n_sm, c->stream));
+    tmark(c, PH_NARROW, 0, 1);
+    c->phase_launches[PH_NARROW] += 1;
     if (!a.fp64) {
       tmark(c, PH_BAND, 0, 0);
       CK(tl::launch_band(a, c->n_sm * 4, c->stream));
@@ -516,8 +578,12 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
       if ((rc = grow(c, &c->hits, &c->hit_cap, h.hits + (again ? h.band : 0)))) return rc;
       again = true;
     }
+    if (st & TL_ST_LEAFQ) {
+      if ((rc = grow(c, &c->leaves, &c->leaf_cap, h.leaf_pairs))) return rc;
+      again = true;
+    }
     if (st & TL_ST_SPILL_OVF) {  // the queue: larger, and every slot the sentinel again
-      const unsigned long long need = 8 * (h.q_tail + h.q_tail / 4 + 1024);  // 8 per chunk
+      const unsigned long long need = kQueueChunk * (h.q_tail + h.q_tail / 4 + 1024);
       if ((rc = alloc_queue(c, std::max(need, 2 * c->queue_cap)))) return rc;
       again = true;
     }
@@ -700,6 +766,8 @@ static int graph_collide(trilens_ctx *c, int64_t step, double *yields) {
     CK(tl::launch_seed_cut(a, c->w[0].cut, c->w[0].cut_n, c->w[0].cut_cap, c->w[1].cut,
                            c->w[1].cut_n, c->w[1].cut_cap, c->front[0], c->front_cap,
                            2 * c->n_sm, c->stream));
+    CK(tl::launch_widen(a, c->front[0], c->front[1], c->front_cap, c->widen_target, kWidenLevels,
+                        4 * c->n_sm, c->stream));
   } else {
     if (c->n_inst > 1)
       CK(tl::launch_seed_instances(c->ctr, c->front[0], c->inst_root[0], c->inst_root[1],
@@ -709,6 +777,7 @@ static int graph_collide(trilens_ctx *c, int64_t step, double *yields) {
   }
   CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->budget, c->trav_blocks,
                          c->trav_warps, c->stream));
+  CK(tl::launch_narrow(a, 8 * c->n_sm, c->stream));
   if (!a.fp64) CK(tl::launch_band(a, c->n_sm * 4, c->stream));
   CK(tl::launch_yield(a, c->partials, c->yield_blocks, c->stream));
   if (yields && c->n_inst > 1)
@@ -779,7 +848,7 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
       CK(cudaStreamSynchronize(c->stream));
       return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit");
     }
-    if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF)))
+    if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF | TL_ST_LEAFQ)))
       return TRILENS_OK;
     // grow what overflowed (to the largest size a step asked for) and capture again
     TLRunAcc m;
@@ -789,8 +858,9 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
     if (st & TL_ST_HIT_OVF && (rc = grow(c, &c->hits, &c->hit_cap, m.max_hits + m.max_band)))
       return rc;
     if (st & TL_ST_BAND_OVF && (rc = grow(c, &c->band, &c->band_cap, m.max_band))) return rc;
+    if (st & TL_ST_LEAFQ && (rc = grow(c, &c->leaves, &c->leaf_cap, m.max_leaves))) return rc;
     if (st & TL_ST_SPILL_OVF) {  // the queue: larger, and every slot the sentinel again
-      const unsigned long long need = 8 * (m.max_handed + m.max_handed / 4 + 1024);
+      const unsigned long long need = kQueueChunk * (m.max_handed + m.max_handed / 4 + 1024);
       if ((rc = alloc_queue(c, std::max(need, 2 * c->queue_cap)))) return rc;
     }
     if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
@@ -861,7 +931,8 @@ int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const tr
 // ---- tuning ---------------------------------------------------------------
 
 static int apply_tuning(trilens_ctx *c, int bucket, int depth, int warps, int budget) {
-  if (bucket < 1 || bucket > 32 || depth < 64 || depth > 4096 || warps < 1 || warps > 16 ||
+  if (bucket < 1 || bucket > 32 || depth < 64 || depth > 4096 || warps < 1 ||
+      warps > TL_TRAV_MAX_WARPS ||
       budget < 0)
     return fail(c, TRILENS_ERR_INVALID, "tuning out of range");
   int bps = 0;
@@ -874,8 +945,8 @@ static int apply_tuning(trilens_ctx *c, int bucket, int depth, int warps, int bu
   c->trav_blocks = bps * c->n_sm;
   c->budget = budget;
   c->front_target = (unsigned)std::min<long long>(2ll * c->trav_blocks * c->trav_warps, 1 << 16);
-  const unsigned need_front = std::max((unsigned)c->n_inst + 4 * c->front_target + 64,
-                                      c->w[0].cut_cap * c->w[1].cut_cap + 64);
+  unsigned need_front = 0;
+  frontier_sizes(c, &c->widen_target, &need_front);
   if (need_front > c->front_cap) {
     c->front_cap = need_front;
     for (int k = 0; k < 2; ++k) {
@@ -1121,7 +1192,7 @@ int trilens_debug_timing(trilens_ctx *c, int on) {
   if (!c) return TRILENS_ERR_INVALID;
   CK(cudaSetDevice(c->device));
   if (on && !c->ev[0][0][0])
-    for (int ph = 0; ph < 9; ++ph)
+    for (int ph = 0; ph < PH_COUNT; ++ph)
       for (int k = 0; k < 2; ++k)
         for (int e = 0; e < 2; ++e) CK(cudaEventCreate(&c->ev[ph][k][e]));
   c->timing = on ? 1 : 0;
@@ -1130,7 +1201,7 @@ int trilens_debug_timing(trilens_ctx *c, int on) {
 
 int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int reset) {
   if (!c) return TRILENS_ERR_INVALID;
-  for (int ph = 0; ph < 9; ++ph) {
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
     if (out) out[ph] = c->phase_ms[ph];
     if (launches) launches[ph] = c->phase_launches[ph];
     if (reset) {
@@ -1158,10 +1229,12 @@ int trilens_debug_shrink_buffers(trilens_ctx *c, int64_t cap) {
   const unsigned long long n = (unsigned long long)cap;
   cudaFree(c->hits);
   cudaFree(c->band);
-  c->hits = c->band = nullptr;
-  c->hit_cap = c->band_cap = n;
+  cudaFree(c->leaves);
+  c->hits = c->band = c->leaves = nullptr;
+  c->hit_cap = c->band_cap = c->leaf_cap = n;
   CK(dalloc(&c->hits, n));
   CK(dalloc(&c->band, n));
+  CK(dalloc(&c->leaves, n));
   const int rc = alloc_queue(c, n);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->stream));

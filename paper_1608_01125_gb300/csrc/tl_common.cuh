@@ -8,6 +8,9 @@
 #define TL_MEC2 0.51099895000       /* electron rest energy [MeV], CODATA 2018 */
 #define TL_PI 3.14159265358979323846
 
+// most warps per block of the traversal kernel (its launch bounds)
+#define TL_TRAV_MAX_WARPS 8
+
 // keys per radix-sort tile (threads 256 x items 8); the look-back status
 // array holds 256 words per tile
 #define TL_SORT_TILE 2048
@@ -64,7 +67,7 @@ enum {
   TL_ST_SPILL_OVF = 4,  // the traversal queue overflowed (or a slot was not free)
   TL_ST_FRONT_OVF = 8,
   TL_ST_TIMEOUT = 16,
-  TL_ST_LEAFQ = 32
+  TL_ST_LEAFQ = 32  // the leaf-pair list overflowed
 };
 
 // Per-step device counters; zeroed by the step's init kernel.
@@ -78,10 +81,10 @@ struct TLCounters {
   unsigned int counts[32];         // frontier size after each expansion level
   unsigned int frozen;             // frontier expansion finished
   unsigned int final_level;        // level whose frontier the traversal reads
-  unsigned int cursor;             // traversal work cursor
+  unsigned int widen_done;         // blocks finished in the frontier's widening level
   unsigned int status;             // TL_ST_* bits
   unsigned int reduce_done;        // blocks finished in the yield reduction
-  unsigned int pad0;
+  unsigned int hungry;             // traversal warps waiting for a handed-on chunk
   unsigned long long q_head;       // traversal items taken (the frontier's, then the queue's)
   unsigned long long q_done;       // traversal items finished
   // results of the yield reduction for this step
@@ -98,6 +101,7 @@ struct TLRunAcc {
   unsigned long long hsum, hxor;
   unsigned long long narrow_tests, node_tests, leaf_pairs, band;
   unsigned long long max_hits, max_band, max_handed;  // largest per-step list and queue sizes
+  unsigned long long max_leaves;
 };
 
 // FP64 input beam on the device.
@@ -189,9 +193,12 @@ struct TravArgs {
   unsigned long long hit_cap;
   uint2 *band;
   unsigned long long band_cap;
+  uint2 *leaves;  // overlapping leaf-bucket pairs (packed first | (count - 1) << 27)
+  unsigned long long leaf_cap;
   unsigned long long *queue;  // traversal work queue: chunks of 8 (ref A, ref B) pairs
   unsigned long long queue_cap;  // in pairs
   int stack_depth;
+  int leaf_bucket;               // photons per leaf bucket at most
   const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal
   long long spin_limit;          // iteration limit of a warp's wait for queued work
 };

@@ -34,7 +34,7 @@ struct trilens_ctx {
   // traversal workspace
   int n_sm = 0, trav_warps = 4, trav_blocks = 0, expand_blocks = 0;
   int budget = 16;  // traversal iterations per work item before it is handed on
-  unsigned front_target = 0, front_cap = 0;
+  unsigned front_target = 0, front_cap = 0, widen_target = 0;
   uint2 *front[2]{};
   uint2 *queue = nullptr;  // traversal work queue (every free slot holds the sentinel)
   unsigned long long queue_cap = 0;
@@ -42,6 +42,8 @@ struct trilens_ctx {
   unsigned long long hit_cap = 0;
   uint2 *band = nullptr;
   unsigned long long band_cap = 0;
+  uint2 *leaves = nullptr;  // the step's overlapping leaf-bucket pairs
+  unsigned long long leaf_cap = 0;
   TLCounters *ctr = nullptr;
   TLCounters *ctr_host = nullptr;  // pinned
   void *partials = nullptr;
@@ -62,6 +64,10 @@ struct trilens_ctx {
   double *owned[2][8]{};      // concatenated inputs owned by a batch context
   // graph-captured multi-step runs (batch contexts)
   cudaStream_t cap_stream = nullptr;
+  // beam B is built on side_stream, forked from and joined back into the
+  // context's stream (the two builds are independent)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int64_t g_first = -1, g_steps = 0;
   double *g_yields = nullptr;
@@ -70,10 +76,10 @@ struct trilens_ctx {
   unsigned *run_status_host = nullptr;
   // per-phase timing (events on the context's stream) and launch counts
   int timing = 0;
-  cudaEvent_t ev[9][2][2]{};   // [phase][beam or 0][start, end]
-  bool ev_pending[9][2]{};
-  double phase_ms[9]{};
-  int64_t phase_launches[9]{};
+  cudaEvent_t ev[10][2][2]{};   // [phase][beam or 0][start, end]
+  bool ev_pending[10][2]{};
+  double phase_ms[10]{};
+  int64_t phase_launches[10]{};
   SurrogateState *sur = nullptr;  // learned statistical regime (tl_surrogate_host.cu)
   DepState *dep = nullptr;        // depletion workspace (tl_deplete.cu)
   int64_t dep_rounds = 0;         // rounds the last depletion call took

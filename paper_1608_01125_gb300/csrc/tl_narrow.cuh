@@ -27,40 +27,77 @@
 
 enum { TL_MISS = 0, TL_HIT = 1, TL_BAND = 2 };
 
-__device__ __forceinline__ int tl_narrow32(const float4 pa, const float4 da, const float4 pb,
-                                           const float4 db, const TLNarrowConst &k) {
+// The test's prefix: the threshold and the quick miss, with the quantities
+// the rest of the test uses.  early >= 0 is the outcome the prefix already
+// decides (a sure miss, or the band for nearly parallel pairs).
+struct TLNarrowPre {
+  float s, es;
+  bool above;
+  float dd, rdd, tau, d2, SA;
+  int early;
+};
+
+__device__ __forceinline__ TLNarrowPre tl_narrow32_pre(const float4 pa, const float4 da,
+                                                       const float4 pb, const float4 db,
+                                                       const TLNarrowConst &k) {
   const float u = 5.9604644775390625e-8f;  // 2^-24
+  TLNarrowPre r;
+  r.early = -1;
   // --- threshold (Eq. eq.Cond) -------------------------------------------
   const float cs = fmaf(da.x, db.x, fmaf(da.y, db.y, da.z * db.z));
   const float omc = 1.0f - cs;
   const float eek = (pa.w * pb.w) * k.inv2mc4;
-  const float s = eek * omc;
-  const float es = 2.0f * (9.0f * u * s + 6.0f * u * eek);
+  r.s = eek * omc;
+  r.es = 2.0f * (9.0f * u * r.s + 6.0f * u * eek);
   const float thr = 9.5367431640625e-7f;  // 2^-20
-  if (s + es <= 1.0f - thr) return TL_MISS;  // surely s64 <= 1 (covers parallel pairs)
-  const bool above = (s - es) >= 1.0f + thr;
+  if (r.s + r.es <= 1.0f - thr) {  // surely s64 <= 1 (covers parallel pairs)
+    r.early = TL_MISS;
+    return r;
+  }
+  r.above = (r.s - r.es) >= 1.0f + thr;
 
   // --- closest approach -----------------------------------------------------
   const float dpx = pa.x - pb.x, dpy = pa.y - pb.y, dpz = pa.z - pb.z;
   const float ddx = da.x - db.x, ddy = da.y - db.y, ddz = da.z - db.z;
-  const float dd = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-  if (!(dd > 1e-20f)) return TL_BAND;  // nearly parallel yet maybe above threshold
+  r.dd = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+  if (!(r.dd > 1e-20f)) {  // nearly parallel yet maybe above threshold
+    r.early = TL_BAND;
+    return r;
+  }
   const float pd = fmaf(dpx, ddx, fmaf(dpy, ddy, dpz * ddz));
-  const float rdd = __frcp_rn(dd);
-  const float tau = -pd * rdd;
-  const float qx = fmaf(tau, ddx, dpx), qy = fmaf(tau, ddy, dpy), qz = fmaf(tau, ddz, dpz);
-  const float d2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+  r.rdd = __frcp_rn(r.dd);
+  r.tau = -pd * r.rdd;
+  const float qx = fmaf(r.tau, ddx, dpx), qy = fmaf(r.tau, ddy, dpy), qz = fmaf(r.tau, ddz, dpz);
+  r.d2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
 
-  const float SA = (fabsf(pa.x) + fabsf(pb.x)) + (fabsf(pa.y) + fabsf(pb.y)) +
-                   (fabsf(pa.z) + fabsf(pb.z));
+  r.SA = (fabsf(pa.x) + fabsf(pb.x)) + (fabsf(pa.y) + fabsf(pb.y)) + (fabsf(pa.z) + fabsf(pb.z));
   // Quick miss, before the bounds: if |dD|^2 >= 2^-30, |tau| <= 2^10,
   // |q|^2 >= 2^-12 and SA <= 2^18 |q|, every term of dq below is a small
   // fraction of |q| (2u SA <= |q|/32, 4u |q|/|dD| <= |q|/128, 4u |tau| <=
   // |q|/64, 7.1u |tau||dD| <= |q|/18), so dq <= 0.23 |q| and ed2 <= 0.5 d2:
   // d2 >= 2.5 r2max then puts the FP64 distance beyond every radius.
-  if (dd >= 0x1p-30f && fabsf(tau) <= 1024.0f && d2 >= fmaxf(2.5f * k.r2max, 0x1p-12f) &&
-      SA * SA <= 0x1p36f * d2)
-    return TL_MISS;
+  if (r.dd >= 0x1p-30f && fabsf(r.tau) <= 1024.0f && r.d2 >= fmaxf(2.5f * k.r2max, 0x1p-12f) &&
+      r.SA * r.SA <= 0x1p36f * r.d2)
+    r.early = TL_MISS;
+  return r;
+}
+
+// true when the prefix alone makes the pair a sure miss (exactly when
+// tl_narrow32 returns TL_MISS before its error bounds)
+__device__ __forceinline__ bool tl_narrow32_quick_miss(const float4 pa, const float4 da,
+                                                       const float4 pb, const float4 db,
+                                                       const TLNarrowConst &k) {
+  return tl_narrow32_pre(pa, da, pb, db, k).early == TL_MISS;
+}
+
+__device__ __forceinline__ int tl_narrow32(const float4 pa, const float4 da, const float4 pb,
+                                           const float4 db, const TLNarrowConst &k) {
+  const float u = 5.9604644775390625e-8f;  // 2^-24
+  const TLNarrowPre pre = tl_narrow32_pre(pa, da, pb, db, k);
+  if (pre.early >= 0) return pre.early;
+  const float s = pre.s, es = pre.es, dd = pre.dd, rdd = pre.rdd, tau = pre.tau, d2 = pre.d2;
+  const float SA = pre.SA;
+  const bool above = pre.above;
   const float nq = sqrtf(d2);
   // over-estimates of 1/|dD| and |dD| for the bounds: rsqrtf is within 2 ulp
   // (4u relative) of 1/sqrt(dd), so 1 + 8u covers it and the product's rounding

@@ -8,12 +8,15 @@
 // levels of the root pair; then persistent warps take frontier pairs and
 // descend depth first with a stack of node pairs in shared memory, handing
 // large items on to a device work queue (see k_traverse).  Each
-// iteration a warp pops up to 8 pairs and tests the up-to-4 child
-// combinations of each with one lane per combination; survivors are pushed
-// (or, when both sides are leaf buckets, queued) with ballot/popc
-// compaction.  Queued bucket pairs are flattened over the warp's lanes, one
-// photon pair per lane, and given the narrow-phase test; hits leave with one
-// atomic per warp.
+// iteration a warp pops up to 32 pairs, one per lane; a lane loads both
+// node records of its pair once and tests the up-to-4 child combinations
+// (both children of each side); survivors are pushed (or, when both sides
+// are leaf buckets, appended to the step's leaf-pair list in blocks of at
+// least 32) with ballot/popc compaction.  A separate kernel (k_narrow) then
+// flattens the listed bucket pairs over its warps' lanes, one photon pair
+// per lane, and gives them the narrow-phase test; hits leave with one atomic
+// per warp.  Splitting the two keeps each kernel's registers low and its
+// warps many, which hides the latency both are bound by.
 #include "tl_common.cuh"
 #include "tl_exact.cuh"
 #include "tl_narrow.cuh"
@@ -86,6 +89,47 @@ __device__ __forceinline__ bool child_pair(const TLTree &A, const TLTree &B, uin
   sa = side_of(A, pr.x, ia);
   sb = side_of(B, pr.y, ib);
   return true;
+}
+
+// Child i (0 or 1) of one side of a popped pair, from the side's node record
+// rec: for an inner node (ref without FLAG) its child i; for a bucket (ref =
+// FLAG | parent << 1 | slot, rec = the parent's record) the bucket itself
+// (i = 0 only).
+struct Kid {
+  TLBox box;
+  uint32_t sref;  // stack reference
+  uint32_t pack;  // bucket as (first photon | (count - 1) << 27)
+  bool bucket;
+};
+
+__device__ __forceinline__ Kid kid_of(const TLNode &rec, uint32_t ref, int i) {
+  Kid k;
+  uint32_t node, sl;
+  if (ref & TL_FLAG) {
+    node = (ref & ~TL_FLAG) >> 1;
+    sl = ref & 1u;
+  } else {
+    node = ref;
+    sl = (uint32_t)i;
+  }
+  k.box = tl_child_box(rec, (int)sl);
+  const uint32_t cr = (uint32_t)(sl ? rec.c.y : rec.c.x);
+  const uint32_t cnt = (uint32_t)(sl ? rec.c.w : rec.c.z);
+  k.bucket = (cr & TL_FLAG) != 0u;
+  k.pack = pack_bucket(cr & ~TL_FLAG, cnt);
+  k.sref = (ref & TL_FLAG) ? ref : (k.bucket ? (TL_FLAG | (node << 1) | sl) : cr);
+  return k;
+}
+
+__device__ __forceinline__ TLNode node_record(const TLTree &T, uint32_t ref) {
+  const uint32_t node = (ref & TL_FLAG) ? ((ref & ~TL_FLAG) >> 1) : ref;
+  const float4 *f = reinterpret_cast<const float4 *>(T.nodes + node);
+  TLNode v;
+  v.b0 = __ldg(f + 0);
+  v.b1 = __ldg(f + 1);
+  v.b2 = __ldg(f + 2);
+  v.c = __ldg(reinterpret_cast<const int4 *>(f + 3));
+  return v;
 }
 
 // warp-aggregated append of (x, y) for lanes with pred
@@ -255,16 +299,110 @@ __global__ void __launch_bounds__(1024) k_expand(TravArgs a, uint2 *F0, uint2 *F
   }
 }
 
+// One breadth-first level of the frontier across the whole grid.  Launched
+// for a fixed number of levels after the seeds; level `level` acts only if it
+// is the frontier's current level and that frontier has fewer than `target`
+// pairs (and its children cannot overflow the buffer, at most 4 per pair):
+// every pair is replaced by its overlapping child pairs (Eq. CollDet; bucket
+// pairs pass through) and the last block to finish moves the frontier on to
+// level + 1.  The decision reads values earlier launches wrote, so every
+// block takes the same one.  A wide frontier gives every traversal warp
+// full 32-pair items from the start.
+__global__ void __launch_bounds__(256) k_widen(TravArgs a, uint2 *F0, uint2 *F1, unsigned cap,
+                                               unsigned target, int level) {
+  TLCounters *ctr = a.ctr;
+  if (ctr->status & TL_ST_TIMEOUT) return;  // the build failed: nothing to traverse
+  if ((int)ctr->final_level != level || level + 1 >= 32) return;
+  const unsigned nin = ctr->counts[level];
+  if (nin == 0u || nin >= target || 4ull * nin > (unsigned long long)cap) return;
+  const uint2 *in = (level & 1) ? F1 : F0;
+  uint2 *out = (level & 1) ? F0 : F1;
+  unsigned *ocount = &ctr->counts[level + 1];
+  const int lane = threadIdx.x & 31;
+  unsigned long long tests = 0;
+  const unsigned nround = (nin + 31u) & ~31u;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nround;
+       i += gridDim.x * blockDim.x) {
+    const bool valid = i < nin;
+    const uint2 pr = valid ? in[i] : make_uint2(0u, 0u);
+    const bool both_buckets = valid && (pr.x & TL_FLAG) && (pr.y & TL_FLAG);
+    for (int combo = 0; combo < 4; ++combo) {
+      Side sa, sb;
+      bool ok = false;
+      uint2 o = make_uint2(0u, 0u);
+      if (valid && !both_buckets && child_pair(a.A, a.B, pr, combo, sa, sb)) {
+        ++tests;
+        ok = tl_overlap(sa.box, sb.box);
+        o = make_uint2(sa.sref, sb.sref);
+      } else if (both_buckets && combo == 0) {
+        ok = true;  // already tested when it was produced: pass through
+        o = pr;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (m) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(ocount, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) out[base + __popc(m & ((1u << lane) - 1u))] = o;  // < 4 nin <= cap
+      }
+    }
+  }
+  for (int off = 16; off; off >>= 1) tests += __shfl_xor_sync(0xffffffffu, tests, off);
+  if (lane == 0 && tests) atomicAdd(&ctr->node_tests, tests);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's outputs and count before its finish
+    if (atomicAdd(&ctr->widen_done, 1u) == gridDim.x - 1u) {
+      ctr->widen_done = 0u;
+      __threadfence();
+      ctr->final_level = (unsigned)(level + 1);
+    }
+  }
+}
+
 // ------------------------------------------------------------ narrow phase
 
+// a warp's leaf-pair queue: fewer than 32 entries before an iteration, at
+// most 4 new ones per lane in it
+constexpr int kLeafQ = 32 + 4 * 32;
+
 struct WarpSmem {
-  uint2 leafq[64];
+  uint2 leafq[kLeafQ];
+  uint2 pend[64];  // narrow phase: photon pairs the test's prefix left undecided
   int scan[32];
 };
 
+// The full FP32 test of up to 32 pending photon pairs (sorted positions in
+// ws.pend[0 .. cnt)), one per lane; hits and band pairs leave with one
+// atomic per warp each.
+__device__ __forceinline__ void decide_pending(const TravArgs &a, const WarpSmem &ws, int cnt,
+                                               int lane) {
+  int outcome = TL_MISS;
+  uint32_t oi = 0u, oj = 0u;
+  if (lane < cnt) {
+    const uint2 pr = ws.pend[lane];
+    const float4 da = __ldg(a.A.dir + pr.x), db = __ldg(a.B.dir + pr.y);
+    const float4 pa = __ldg(a.A.pos + pr.x), pb = __ldg(a.B.pos + pr.y);
+    oi = __float_as_uint(da.w);
+    oj = __float_as_uint(db.w);
+    outcome = tl_narrow32(pa, da, pb, db, a.nk);
+  }
+  emit(outcome == TL_HIT, oi, oj, a.hits, a.hit_cap, &a.ctr->hits, &a.ctr->status,
+       TL_ST_HIT_OVF, lane);
+  emit(outcome == TL_BAND, oi, oj, a.band, a.band_cap, &a.ctr->band, &a.ctr->status,
+       TL_ST_BAND_OVF, lane);
+}
+
+// The narrow phase of nq leaf pairs in ws.leafq: their photon pairs are
+// flattened over the lanes (a scan of the pairs' sizes, then each lane finds
+// its pair by binary search).  FP64: each photon pair is decided by the
+// definition.  FP32: the test's prefix (threshold, quick miss) runs on every
+// photon pair and decides most of them; the undecided ones are queued in
+// ws.pend (npend of them, warp-uniform) and given the full test 32 at a time,
+// so that the long path runs on full warps.
 template <bool FP64>
 __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, int nq, int lane,
-                                             unsigned long long &tests) {
+                                             unsigned long long &tests, int &npend) {
   const unsigned lt = (1u << lane) - 1u;
   for (int e0 = 0; e0 < nq; e0 += 32) {
     const int m = min(32, nq - e0);
@@ -286,7 +424,8 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
     for (int t0 = 0; t0 < total; t0 += 32) {
       const int t = t0 + lane;
       int outcome = TL_MISS;
-      uint32_t oi = 0u, oj = 0u;
+      bool undecided = false;
+      uint32_t oi = 0u, oj = 0u, si = 0u, sj = 0u;
       if (t < total) {
         // largest entry e with scan[e] <= t
         int lo = 0, hi = m - 1;
@@ -300,52 +439,85 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
         const uint32_t cb = (q.y >> 27) + 1u;
         const uint32_t loc = (uint32_t)(t - ws.scan[lo]);
         const uint32_t ia = loc / cb, jb = loc - ia * cb;
-        const float4 da = __ldg(a.A.dir + fa + ia), db = __ldg(a.B.dir + fb + jb);
-        oi = __float_as_uint(da.w);
-        oj = __float_as_uint(db.w);
+        si = fa + ia;
+        sj = fb + jb;
+        const float4 da = __ldg(a.A.dir + si), db = __ldg(a.B.dir + sj);
         if (FP64) {
+          oi = __float_as_uint(da.w);
+          oj = __float_as_uint(db.w);
           outcome = tl_exact_hit(a.mA, oi, a.mB, oj, a.ct, a.dt, a.kappa) ? TL_HIT : TL_MISS;
         } else {
-          const float4 pa = __ldg(a.A.pos + fa + ia), pb = __ldg(a.B.pos + fb + jb);
-          outcome = tl_narrow32(pa, da, pb, db, a.nk);
+          const float4 pa = __ldg(a.A.pos + si), pb = __ldg(a.B.pos + sj);
+          undecided = !tl_narrow32_quick_miss(pa, da, pb, db, a.nk);
         }
       }
-      emit(outcome == TL_HIT, oi, oj, a.hits, a.hit_cap, &a.ctr->hits, &a.ctr->status,
-           TL_ST_HIT_OVF, lane);
-      if (!FP64)
-        emit(outcome == TL_BAND, oi, oj, a.band, a.band_cap, &a.ctr->band, &a.ctr->status,
-             TL_ST_BAND_OVF, lane);
+      if (FP64) {
+        emit(outcome == TL_HIT, oi, oj, a.hits, a.hit_cap, &a.ctr->hits, &a.ctr->status,
+             TL_ST_HIT_OVF, lane);
+      } else {
+        const unsigned mu = __ballot_sync(0xffffffffu, undecided);
+        if (undecided) ws.pend[npend + __popc(mu & lt)] = make_uint2(si, sj);
+        npend += __popc(mu);
+        __syncwarp();
+        if (npend >= 32) {
+          decide_pending(a, ws, 32, lane);
+          // the rest (fewer than 32) move to the front
+          const int rest = npend - 32;
+          uint2 v = make_uint2(0u, 0u);
+          if (lane < rest) v = ws.pend[32 + lane];
+          __syncwarp();
+          if (lane < rest) ws.pend[lane] = v;
+          __syncwarp();
+          npend = rest;
+        }
+      }
     }
     __syncwarp();
   }
-  (void)lt;
 }
 
 // ------------------------------------------------------------ traversal
 
-// Persistent warps share one work queue.  The frontier's items come first
-// (indices below n0), then the queue's chunks of up to 8 node pairs each (64
-// bytes): a warp that spends `budget` iterations on one item hands the rest of
-// it (its whole stack) on as chunks, which idle warps take at once, popping 8
-// pairs in their first iteration; a warp whose stack is full hands on the pair
-// that does not fit as a chunk of one.  Unused and free entries hold a
-// sentinel.  A writer fills a chunk's entries 1..7, fences, then swaps entry 0
-// in; a taker swaps the sentinel back into entry 0 as it reads it (atomic
-// exchange) and waits while it is still free and work is in flight.  The
-// traversal ends when the chunks finished equal n0 plus the chunks handed on.
-// Every wait is bounded by spin_limit (then TL_ST_TIMEOUT).
+// Persistent warps share one work queue.  Its items come first from the
+// frontier, in groups of up to 32 node pairs (indices below nf), then from
+// the queue's chunks of up to 32 node pairs each (256 bytes).  A warp that
+// has spent `budget` iterations on its item while other warps wait for work
+// (ctr->hungry > 0), or whose stack is nearly full, hands on the bottom of
+// its stack (the shallowest, largest subtrees; all but the top 32 entries,
+// or half of a smaller stack) as chunks that the waiting warps take; a warp
+// whose stack is full hands on the pair that does not fit as a chunk of one.
+// Unused and free entries hold a sentinel.  A writer fills a chunk's entries
+// 1..31, fences, then swaps entry 0 in; a taker swaps the sentinel back into
+// entry 0 as it reads it (atomic exchange) and waits while it is still free
+// and work is in flight.  The traversal ends when the items finished equal
+// nf plus the chunks handed on.  Every wait is bounded by spin_limit (then
+// TL_ST_TIMEOUT).
 constexpr unsigned long long kQFree = 0xffffffffffffffffull;
+constexpr int kGroup = 32;  // frontier pairs per item, node pairs per queue chunk
 
 __device__ __forceinline__ unsigned long long pack2(uint2 v) {
   return (unsigned long long)v.x | ((unsigned long long)v.y << 32);
 }
 
-// (Bounding the registers to 48 for five 256-thread blocks per SM spilled
-// a little and ran the 2 x 1M traversal 2% slower.)
-template <bool FP64>
-__global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, const uint2 *F1,
-                                                  const uint2 *list, unsigned long long list_n,
-                                                  int from_frontier, int budget) {
+// Launch bounds: at most 8 warps per block and registers for 4 such blocks
+// per SM (63 registers, no spills; the narrow phase is a kernel of its own).
+#ifndef TL_TRAV_MINBLOCKS
+#define TL_TRAV_MINBLOCKS 4
+#endif
+// a warp's queued leaf pairs to the step's list (one atomic per warp)
+__device__ __forceinline__ void spill_leaves(const TravArgs &a, const WarpSmem &ws, int nq,
+                                             int lane) {
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(&a.ctr->leaf_pairs, (unsigned long long)nq);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int e = lane; e < nq; e += 32)
+    if (base + e < a.leaf_cap) a.leaves[base + e] = ws.leafq[e];
+  if (lane == 0 && base + nq > a.leaf_cap) atomicOr(&a.ctr->status, (unsigned)TL_ST_LEAFQ);
+}
+
+__global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_traverse(
+    TravArgs a, const uint2 *F0, const uint2 *F1, const uint2 *list, unsigned long long list_n,
+    int from_frontier, int budget) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int D = a.stack_depth;
@@ -363,42 +535,58 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
     src0 = list;
     n0 = list_n;
   }
+  const unsigned long long nf = (n0 + kGroup - 1) / kGroup;  // frontier groups
   unsigned long long *Q = a.queue;
-  const unsigned long long qcap = a.queue_cap >> 3;  // chunks of 8 pairs
+  const unsigned long long qcap = a.queue_cap / kGroup;  // chunks
   const unsigned lt = (1u << lane) - 1u;
   int sp = 0, nq = 0, iters = 0;
   bool holding = false;  // this warp holds an item (counted in flight)
   bool handed = false;   // ... and has handed pieces of it on
-  unsigned long long node_tests = 0, narrow_tests = 0, leaf_pairs = 0;
+  unsigned long long node_tests = 0;
   while (true) {
-    if (sp > 0 && budget > 0 && iters >= budget) {
-      // this item is large: hand the rest of it (the whole stack) on as chunks;
-      // they are counted before this item is counted finished
-      const int nch = (sp + 7) >> 3;
-      unsigned long long base = 0;
-      if (lane == 0) base = atomicAdd(&ctr->q_tail, (unsigned long long)nch);
-      handed = true;
-      base = __shfl_sync(0xffffffffu, base, 0);
-      for (int e = lane; e < nch * 8; e += 32) {  // entries 1..7 of every chunk
-        if ((e & 7) != 0 && base + (e >> 3) < qcap)
-          Q[(base + (e >> 3)) * 8 + (e & 7)] = e < sp ? pack2(stack[e]) : kQFree;
-      }
-      __threadfence();
-      __syncwarp();
-      for (int c = lane; c < nch; c += 32) {  // then entry 0: the chunk is ready
-        if (base + c < qcap) {
-          if (atomicExch(Q + (base + c) * 8, pack2(stack[c * 8])) != kQFree)
-            atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);  // a chunk was not free
-        } else {
-          atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+    if (sp > 1 && budget > 0 && (iters >= budget || sp > D - 4 * 32)) {
+      unsigned h = 0;
+      if (lane == 0) h = *(volatile unsigned *)&ctr->hungry;
+      h = __shfl_sync(0xffffffffu, h, 0);
+      iters = 0;
+      if (h > 0 || sp > D - 4 * 32) {
+        // hand on the bottom of the stack: all but the top 32 entries, or the
+        // bottom half of a smaller stack; the chunks are counted before this
+        // item is counted finished
+        const int give = sp > kGroup ? sp - kGroup : sp / 2;
+        const int nch = (give + kGroup - 1) / kGroup;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctr->q_tail, (unsigned long long)nch);
+        handed = true;
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int e = lane; e < nch * kGroup; e += 32) {  // entries 1..31 of every chunk
+          if ((e % kGroup) != 0 && base + e / kGroup < qcap)
+            Q[(base + e / kGroup) * kGroup + e % kGroup] = e < give ? pack2(stack[e]) : kQFree;
         }
+        __threadfence();
+        __syncwarp();
+        for (int c = lane; c < nch; c += 32) {  // then entry 0: the chunk is ready
+          if (base + c < qcap) {
+            if (atomicExch(Q + (base + c) * kGroup, pack2(stack[c * kGroup])) != kQFree)
+              atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);  // a chunk was not free
+          } else {
+            atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+          }
+        }
+        __syncwarp();
+        // the kept entries (at most 32) move to the bottom
+        const int keep = sp - give;
+        uint2 v = make_uint2(0u, 0u);
+        if (lane < keep) v = stack[give + lane];
+        __syncwarp();
+        if (lane < keep) stack[lane] = v;
+        __syncwarp();
+        sp = keep;
       }
-      __syncwarp();
-      sp = 0;
     }
     if (sp == 0) {
-      int got = 0;  // 1: a frontier item; 2: a queue chunk
-      unsigned long long chunk = 0;
+      int got = 0;  // 1: a frontier group; 2: a queue chunk
+      unsigned long long idx = 0;
       uint2 item = make_uint2(0u, 0u);
       if (lane == 0) {
         if (holding) {
@@ -408,14 +596,15 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
         }
         handed = false;
         const unsigned long long i = atomicAdd(&ctr->q_head, 1ull);
-        if (i < n0) {
-          item = __ldcg(src0 + i);
+        if (i < nf) {
+          idx = i;
           got = 1;
-        } else if (i - n0 < qcap) {
-          chunk = i - n0;
-          unsigned long long *slot = Q + chunk * 8;
+        } else if (i - nf < qcap) {
+          idx = i - nf;
+          unsigned long long *slot = Q + idx * kGroup;
           long long spins = 0;
           unsigned ns = 32;
+          bool waiting = false;
           while (true) {
             const unsigned long long v = atomicExch(slot, kQFree);
             if (v != kQFree) {
@@ -424,12 +613,16 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
               __threadfence();  // entry 0 seen: the chunk's other entries are written
               break;
             }
+            if (!waiting) {  // tell working warps that a warp waits for work
+              waiting = true;
+              atomicAdd(&ctr->hungry, 1u);
+            }
             // finished items first, then hand-ons: equal means nothing was in
             // flight at the first read, so nothing more can come
             const unsigned long long done = *(volatile unsigned long long *)&ctr->q_done;
             __threadfence();
             const unsigned long long tail = *(volatile unsigned long long *)&ctr->q_tail;
-            if (done >= n0 + tail) break;
+            if (done >= nf + tail) break;
             if (*(volatile unsigned *)&ctr->status & (TL_ST_SPILL_OVF | TL_ST_TIMEOUT)) break;
             if (++spins > a.spin_limit) {
               atomicOr(&ctr->status, (unsigned)TL_ST_TIMEOUT);
@@ -438,94 +631,119 @@ __global__ void __launch_bounds__(512) k_traverse(TravArgs a, const uint2 *F0, c
             __nanosleep(ns);
             if (ns < 1024) ns <<= 1;
           }
+          if (waiting) atomicSub(&ctr->hungry, 1u);
         }
         // an index past the queue's end: its producer flagged the overflow
       }
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) break;
-      sp = 1;
-      if (got == 2) {  // entries 1..7 of the chunk: the written ones come first
-        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      if (got == 1) {  // up to 32 frontier pairs
+        const unsigned long long f = idx * kGroup + (unsigned long long)lane;
+        const bool have = f < n0;
+        if (have) stack[lane] = __ldcg(src0 + f);
+        sp = __popc(__ballot_sync(0xffffffffu, have));
+      } else {  // entries 1..31 of the chunk: the written ones come first
         unsigned long long v = kQFree;
-        if (lane >= 1 && lane < 8) v = __ldcg(Q + chunk * 8 + lane);
+        if (lane >= 1) v = __ldcg(Q + idx * kGroup + lane);
         const unsigned mv = __ballot_sync(0xffffffffu, v != kQFree);
         if (v != kQFree) stack[lane] = make_uint2((unsigned)v, (unsigned)(v >> 32));
+        if (lane == 0) stack[0] = item;
         sp = 1 + __popc(mv);
       }
-      if (lane == 0) {
-        stack[0] = item;
-        holding = true;
-      }
+      if (lane == 0) holding = true;
       __syncwarp();
       iters = 0;
     }
     ++iters;
-    const int npop = min(sp, 8);
+    // one popped pair per lane
+    const int npop = min(sp, 32);
     sp -= npop;
-    const int p = lane >> 2, combo = lane & 3;
-    const bool active = p < npop;
-    const uint2 pr = active ? stack[sp + p] : make_uint2(0u, 0u);
+    const bool active = lane < npop;
+    const uint2 pr = active ? stack[sp + lane] : make_uint2(0u, 0u);
     __syncwarp();
-    bool ok = false, leafleaf = false, tested = false;
-    uint2 o = make_uint2(0u, 0u);
+    const bool bka = (pr.x & TL_FLAG) != 0u, bkb = (pr.y & TL_FLAG) != 0u;
+    TLNode ra, rb;
     if (active) {
-      if ((pr.x & TL_FLAG) && (pr.y & TL_FLAG)) {
-        if (combo == 0) {  // a bucket pair taken from the frontier
-          const Side sa = side_of(a.A, pr.x, 0), sb = side_of(a.B, pr.y, 0);
-          ok = leafleaf = true;
-          o = make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt));
-        }
-      } else {
-        Side sa, sb;
-        if (child_pair(a.A, a.B, pr, combo, sa, sb)) {
-          tested = true;
-          ok = tl_overlap(sa.box, sb.box);
-          leafleaf = sa.bucket && sb.bucket;
-          o = leafleaf ? make_uint2(pack_bucket(sa.first, sa.cnt), pack_bucket(sb.first, sb.cnt))
-                       : make_uint2(sa.sref, sb.sref);
-        }
-      }
+      ra = node_record(a.A, pr.x);
+      rb = node_record(a.B, pr.y);
     }
-    const unsigned mtest = __ballot_sync(0xffffffffu, tested);
-    if (lane == 0) node_tests += (unsigned long long)__popc(mtest);
-    const unsigned mpush = __ballot_sync(0xffffffffu, ok && !leafleaf);
-    const unsigned mleaf = __ballot_sync(0xffffffffu, ok && leafleaf);
-    if (sp + __popc(mpush) > D) handed = true;  // (warp-uniform)
-    if (ok && !leafleaf) {
-      const int slot = sp + __popc(mpush & lt);
-      if (slot < D) {
-        stack[slot] = o;
-      } else {  // the stack is full: this pair goes to the queue as a chunk of one
-        const unsigned long long idx = atomicAdd(&ctr->q_tail, 1ull);
-        if (idx < qcap) {
-          for (int k = 1; k < 8; ++k) Q[idx * 8 + k] = kQFree;
-          __threadfence();
-          if (atomicExch(Q + idx * 8, pack2(o)) != kQFree)
+    // a bucket pair taken from the frontier was tested when it was produced
+    const bool pass = active && bka && bkb;
+    int tested = 0;
+#pragma unroll
+    for (int combo = 0; combo < 4; ++combo) {
+      const int ia = combo >> 1, ib = combo & 1;
+      bool ok = false, leaf = false;
+      uint2 o = make_uint2(0u, 0u);
+      if (pass) {
+        if (combo == 0) {
+          const Kid ka = kid_of(ra, pr.x, 0), kb = kid_of(rb, pr.y, 0);
+          ok = leaf = true;
+          o = make_uint2(ka.pack, kb.pack);
+        }
+      } else if (active && !(bka && ia) && !(bkb && ib)) {
+        const Kid ka = kid_of(ra, pr.x, ia), kb = kid_of(rb, pr.y, ib);
+        ++tested;
+        ok = tl_overlap(ka.box, kb.box);
+        leaf = ka.bucket && kb.bucket;
+        o = leaf ? make_uint2(ka.pack, kb.pack) : make_uint2(ka.sref, kb.sref);
+      }
+      const unsigned mpush = __ballot_sync(0xffffffffu, ok && !leaf);
+      const unsigned mleaf = __ballot_sync(0xffffffffu, ok && leaf);
+      if (sp + __popc(mpush) > D) handed = true;  // (warp-uniform)
+      if (ok && !leaf) {
+        const int slot = sp + __popc(mpush & lt);
+        if (slot < D) {
+          stack[slot] = o;
+        } else {  // the stack is full: this pair goes to the queue as a chunk of one
+          const unsigned long long qi = atomicAdd(&ctr->q_tail, 1ull);
+          if (qi < qcap) {
+            for (int k = 1; k < kGroup; ++k) Q[qi * kGroup + k] = kQFree;
+            __threadfence();
+            if (atomicExch(Q + qi * kGroup, pack2(o)) != kQFree)
+              atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+          } else {
             atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
-        } else {
-          atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
+          }
         }
       }
+      sp = min(sp + __popc(mpush), D);
+      if (ok && leaf) ws.leafq[nq + __popc(mleaf & lt)] = o;
+      nq += __popc(mleaf);
     }
-    sp = min(sp + __popc(mpush), D);
-    if (ok && leafleaf) ws.leafq[nq + __popc(mleaf & lt)] = o;
-    nq += __popc(mleaf);
+    for (int off = 16; off; off >>= 1) tested += __shfl_xor_sync(0xffffffffu, tested, off);
+    if (lane == 0) node_tests += (unsigned long long)tested;
     __syncwarp();
     if (nq >= 32) {
-      leaf_pairs += nq;
-      flush_leaves<FP64>(a, ws, nq, lane, narrow_tests);
+      spill_leaves(a, ws, nq, lane);
       nq = 0;
     }
   }
-  if (nq) {
-    leaf_pairs += nq;
-    flush_leaves<FP64>(a, ws, nq, lane, narrow_tests);
+  if (nq) spill_leaves(a, ws, nq, lane);
+  if (lane == 0 && node_tests) atomicAdd(&ctr->node_tests, node_tests);
+}
+
+// The narrow phase of the step's listed leaf pairs: each warp takes 32 of
+// them at a time and flattens their photon pairs over its lanes.
+template <bool FP64>
+__global__ void __launch_bounds__(256) k_narrow(TravArgs a) {
+  __shared__ WarpSmem wsm[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpSmem &ws = wsm[warp];
+  const unsigned long long n = min(a.ctr->leaf_pairs, a.leaf_cap);
+  const unsigned long long stride = (unsigned long long)gridDim.x * (blockDim.x >> 5) * 32ull;
+  unsigned long long tests = 0;
+  int npend = 0;
+  for (unsigned long long base = ((unsigned long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32ull;
+       base < n; base += stride) {
+    const int m = (int)min(32ull, n - base);
+    if (lane < m) ws.leafq[lane] = a.leaves[base + lane];
+    __syncwarp();
+    flush_leaves<FP64>(a, ws, m, lane, tests, npend);
   }
-  if (lane == 0) {
-    if (node_tests) atomicAdd(&ctr->node_tests, node_tests);
-    if (narrow_tests) atomicAdd(&ctr->narrow_tests, narrow_tests);
-    if (leaf_pairs) atomicAdd(&ctr->leaf_pairs, leaf_pairs);
-  }
+  if (!FP64 && npend > 0) decide_pending(a, ws, npend, lane);
+  if (lane == 0 && tests) atomicAdd(&a.ctr->narrow_tests, tests);
 }
 
 // ------------------------------------------------------------ band re-test
@@ -614,6 +832,7 @@ __global__ void k_step_finish(const TLCounters *ctr, unsigned *run_status, TLRun
     if (ctr->hits > acc->max_hits) acc->max_hits = ctr->hits;
     if (ctr->band > acc->max_band) acc->max_band = ctr->band;
     if (ctr->q_tail > acc->max_handed) acc->max_handed = ctr->q_tail;
+    if (ctr->leaf_pairs > acc->max_leaves) acc->max_leaves = ctr->leaf_pairs;
   }
 }
 
@@ -642,21 +861,24 @@ cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap,
   return cudaGetLastError();
 }
 
-cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm) {
-  size_t smem = traverse_smem(warps, depth);
-  cudaError_t e;
-  if (fp64) {
-    if ((e = cudaFuncSetAttribute(k_traverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)))
-      return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_traverse<true>,
-                                                         warps * 32, smem);
+cudaError_t launch_widen(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
+                         int levels, int blocks, cudaStream_t s) {
+  for (int l = 0; l < levels; ++l) {
+    k_widen<<<blocks, 256, 0, s>>>(a, F0, F1, cap, target, l);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  if ((e = cudaFuncSetAttribute(k_traverse<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaSuccess;
+}
+
+cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm) {
+  (void)fp64;  // the traversal is the same for both precisions (the narrow phase differs)
+  const size_t smem = traverse_smem(warps, depth);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_traverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)))
     return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_traverse<false>,
-                                                       warps * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_traverse, warps * 32, smem);
 }
 
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
@@ -665,12 +887,13 @@ cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1,
   // a warp only waits for work that warps holding items (running ones) hand
   // on, so no block needs another to be resident
   const size_t smem = traverse_smem(warps, a.stack_depth);
-  if (a.fp64)
-    k_traverse<true><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier,
-                                                       budget);
-  else
-    k_traverse<false><<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier,
-                                                        budget);
+  k_traverse<<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier, budget);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(const TravArgs &a, int blocks, cudaStream_t s) {
+  if (a.fp64) k_narrow<true><<<blocks, 256, 0, s>>>(a);
+  else k_narrow<false><<<blocks, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

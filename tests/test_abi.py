@@ -61,7 +61,7 @@ def test_invalid_arguments_rejected_on_host(lib):
                                   ctypes.byref(P), None) == binding.ERR_INVALID
     for P in (binding.Params(0.0, 1e16, 0, 0, 0, 0, 0), binding.Params(10.0, -1.0, 0, 0, 0, 0, 0),
               binding.Params(10.0, 1e16, 7, 0, 0, 0, 0), binding.Params(10.0, 1e16, 0, 33, 0, 0, 0),
-              binding.Params(10.0, 1e16, 0, 0, 8, 0, 0), binding.Params(10.0, 1e16, 0, 0, 0, 17, 0),
+              binding.Params(10.0, 1e16, 0, 0, 8, 0, 0), binding.Params(10.0, 1e16, 0, 0, 0, 17, 0), binding.Params(10.0, 1e16, 0, 0, 0, 9, 0),
               binding.Params(10.0, 1e16, 0, 0, 0, 0, -5)):
         assert lib.trilens_create(ctypes.byref(h), ctypes.byref(empty), ctypes.byref(empty),
                                   ctypes.byref(P), None) == binding.ERR_INVALID
