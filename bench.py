@@ -43,7 +43,15 @@ UNIT = "pair-tests/s"
 CPU_STEP_STRIDE = 4
 SINGLE_THREAD_STEPS = (4, 36)
 FALLBACK_HBM_GBS = 6800.0
-PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "band", "yield")
+PHASES = ("propagate", "sort", "gather", "emit", "refit", "expand", "traverse", "narrow", "band",
+          "yield")
+# FP32 operations of the narrow test's prefix (threshold and quick miss), which
+# decides most photon pairs: the invariant s and its bound (13), the relative
+# position and direction and their products (15), the reciprocal and the
+# closest approach (8), the position sum and the quick-miss comparisons (11)
+NARROW_OPS_PER_TEST = 47
+# GB300 FP32 lanes: 152 SMs x 128 per SM at the 2070 MHz maximum SM clock
+FP32_OPS_PEAK = 152 * 128 * 2.07e9
 
 
 def algorithmic_bytes(phase: str, na: int, nb: int, key_bits: tuple, hits: float, band: float):
@@ -60,8 +68,10 @@ def algorithmic_bytes(phase: str, na: int, nb: int, key_bits: tuple, hits: float
         return 8 + 16 + 4, "photon"
     if phase == "refit":       # sorted SoA, parent links and ranges read; two child boxes per node
         return 32 + 8 + 4 + 4 + 48, "photon"
-    if phase == "traverse":    # node records and sorted SoA of both trees once + output pairs
-        return 64 + 32, "photon"
+    if phase == "traverse":    # node records of both trees once + the leaf pairs written
+        return 64, "photon"
+    if phase == "narrow":      # sorted photon records once + the leaf pairs read + output pairs
+        return 32, "photon"
     return 8, "pair"
 
 
@@ -384,6 +394,57 @@ def ip_regime_timing(dev, stream, reps=3, cpu=True):
             "cpu_baseline": cpu_line}
 
 
+def crossing_timing(dev, stream, peak, peak_src, steps=(120, 129, 141, 160)):
+    """The large exact workload (2 x 5e7 photons crossing at 90 degrees, Gamma
+    energies, 2 fs steps): a few of its busy time steps built and collided one
+    at a time with per-phase device times (CUDA events).  Here the two
+    hierarchies (2 x 5e7 x 64 B of node records) are far larger than the L2,
+    so the traversal's HBM fraction is measured where it can matter.  The
+    hit counts of steps 129, 141 and 160 are the oracle's (the GPU tests
+    compare their checksums)."""
+    import torch
+
+    from paper_1608_01125_gb300 import binding
+    wl = synth.crossing90_5e7()
+    a_np, b_np = synth.beams(wl)
+    A, B = binding.to_device(a_np, dev), binding.to_device(b_np, dev)
+    del a_np, b_np
+    col = binding.Collider(A, B, wl.dt, wl.kappa, precision=binding.FP32_BAND, stream=stream)
+    tuned = col.autotune([steps[1]], os.path.join(ROOT, "paper_1608_01125_gb300",
+                                                  "_tuning_cache.json"))
+    col.timing(True)
+    rows = []
+    for k in steps:
+        col.build(k)
+        col.phase_ms(reset=True)
+        col.collide(k)
+        torch.cuda.synchronize()
+        col.phase_ms(reset=True)
+        col.build(k)  # timed: the build and the collision of step k
+        col.collide(k)
+        ph, _ = col.phase_ms(reset=True)
+        st = col.stats()
+        rows.append({"step": k, **{p: round(ph[p], 4) for p in PHASES}, "hits": st["count"],
+                     "narrow_tests": st["narrow_tests"], "node_tests": st["node_tests"],
+                     "leaf_pairs": st["leaf_pairs"]})
+    col.timing(False)
+    col.close()
+    n_ab = wl.a.n + wl.b.n
+    tt = sum(r["traverse"] for r in rows)
+    tbytes = sum(64.0 * n_ab + 8.0 * r["leaf_pairs"] for r in rows)
+    ach = tbytes / (tt / 1e3) / 1e9
+    tot = sum(sum(r[p] for p in PHASES) for r in rows)
+    return {"workload": wl.name, "photons_per_beam": wl.a.n, "time_steps_timed": list(steps),
+            "tuning": tuned, "ms_per_step": tot / len(rows), "per_step": rows,
+            "narrow_tests_per_s": sum(r["narrow_tests"] for r in rows) / (tot / 1e3),
+            "collided_pairs_per_s": sum(r["hits"] for r in rows) / (tot / 1e3),
+            "traverse_roofline": {"bound": "hbm", "achieved": ach, "peak": peak,
+                                  "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak,
+                                  "algorithmic_bytes": tbytes, "ms": tt,
+                                  "unit_of_work": "node records of both trees once, leaf pairs "
+                                                  "written, per step"}}
+
+
 def run_reference(args, wl):
     """The oracle as the reference arm: bench step q times the time steps
     {j, j + 16, j + 32, j + 48} of the run with j = q mod 16, so that 16 bench
@@ -549,7 +610,9 @@ def run_ours(args, wl):
         col.collide(k)
         ph, _ = col.phase_ms(reset=True)
         st = col.stats()
-        per_step.append((k, ph["traverse"], st["narrow_tests"], st["count"], st["band"]))
+        per_step.append(dict(step=k, traverse=ph["traverse"], narrow=ph["narrow"],
+                             tests=st["narrow_tests"], hits=st["count"], band=st["band"],
+                             leaves=st["leaf_pairs"]))
     col.timing(False)
     pairs = pair_products_timing(col, A, B, stream) if rank == 0 else None
     depl = (depletion_timing(col, stream, list(time_steps), *read_peaks(),
@@ -557,6 +620,12 @@ def run_ours(args, wl):
             if rank == 0 and not args.no_depletion else None)
     ipr = (ip_regime_timing(dev, stream, cpu=not args.no_cpu_baseline)
            if rank == 0 and not args.no_ip else None)
+    crossing = (crossing_timing(dev, stream, *read_peaks())
+                if rank == 0 and not args.no_crossing else None)
+    # the learned statistical regime on a 2 x 1e6 sample of the statistical
+    # workload's shape (config 3's full size runs with --workload statistical)
+    stat = (surrogate_eval(1_000_000, 2e13, 14, [1, 2], 0)
+            if rank == 0 and not args.no_statistical else None)
     ms = slowest_rank_ms(ms, world, dev)
     K = args.steps
     value = whole_job_rate(tests, world, ms)
@@ -586,29 +655,60 @@ def run_ours(args, wl):
             dist.destroy_process_group()
         return
     peak, peak_src = read_peaks()
-    # dominant phase and its roofline
-    dom = max(phase_ms, key=lambda p: phase_ms[p])
-    per_unit, unit_name = algorithmic_bytes(dom, wl.a.n, wl.b.n, None, hits / K, band / K)
-    builds = 2 * K * nsteps  # one build per beam and step
-    if dom == "sort":  # the unit is one digit pass over one beam
-        passes = max(launches[dom] - builds, 1)  # minus one scan per build
-        algo = per_unit * (wl.a.n + wl.b.n) / 2
-        launch_ms = phase_ms[dom] / passes
-    elif dom in ("propagate", "gather", "emit", "refit"):  # the unit is one beam's build phase
-        algo = per_unit * (wl.a.n + wl.b.n) / 2
-        launch_ms = phase_ms[dom] / builds
-    else:
-        # the traversal of one step may take several launches (passes over the
-        # pairs a warp handed on); its unit is the step
-        algo = per_unit * (wl.a.n + wl.b.n) + 8.0 * (hits + band) / (K * nsteps)
-        launch_ms = phase_ms[dom] / (K * nsteps)
-    achieved = algo / (launch_ms / 1e3) / 1e9
+    # rooflines of the traversal (HBM: its algorithmic bytes per step), the
+    # narrow phase (FP32 ALU: the test prefix's operations) and the dominant
+    # build phase, each from the per-phase device times of the step-by-step
+    # runs; the dominant one by time is the line's roofline
+    n_ab = wl.a.n + wl.b.n
+    leaves = sum(r["leaves"] for r in per_step)  # one run
+    steps_total = K * nsteps
+    builds = 2 * steps_total  # one build per beam and step
+
+    def hbm(phase, algo, launch_ms, note):
+        ach = algo / (launch_ms / 1e3) / 1e9
+        return {"kernel": phase, "bound": "hbm", "achieved": ach, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "algorithmic_bytes_per_launch": algo, "launch_ms": launch_ms, "unit_of_work": note}
+
+    roofs = {}
+    roofs["traverse"] = hbm("traverse", 64.0 * n_ab + 8.0 * leaves / nsteps,
+                            phase_ms["traverse"] / steps_total,
+                            "one step: node records of both trees once, leaf pairs written")
+    ops = NARROW_OPS_PER_TEST * tests / K / nsteps
+    nms = phase_ms["narrow"] / steps_total
+    roofs["narrow"] = {"kernel": "narrow", "bound": "alu", "unit": "FP32 op/s",
+                       "achieved": ops / (nms / 1e3), "peak": FP32_OPS_PEAK,
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                       "frac": ops / (nms / 1e3) / FP32_OPS_PEAK, "launch_ms": nms,
+                       "ops_per_test": NARROW_OPS_PER_TEST, "traffic": None}
+    for ph in ("sort", "refit", "emit", "propagate"):
+        per_unit, _ = algorithmic_bytes(ph, wl.a.n, wl.b.n, None, 0, 0)
+        if ph == "sort":  # the unit is one digit pass over one beam
+            passes = max(launches[ph] - builds, 1)  # minus one scan per build
+            roofs[ph] = hbm(ph, per_unit * n_ab / 2, phase_ms[ph] / passes, "one pass, one beam")
+        else:
+            roofs[ph] = hbm(ph, per_unit * n_ab / 2, phase_ms[ph] / builds, "one beam's build")
+    dom = max(roofs, key=lambda p: phase_ms[p])
     # busy steps: those with at least 5% of the peak step's narrow-phase tests
-    peak_tests = max(t for _, _, t, _, _ in per_step) if per_step else 0
-    busy = [r for r in per_step if peak_tests and r[2] >= 0.05 * peak_tests]
-    tb = sum(r[1] for r in busy)
-    busy_bytes = sum(per_unit * (wl.a.n + wl.b.n) + 8.0 * (r[3] + r[4]) for r in busy)
-    busy_gbs = busy_bytes / (tb / 1e3) / 1e9 if tb > 0 else None
+    peak_tests = max(r["tests"] for r in per_step) if per_step else 0
+    busy = [r for r in per_step if peak_tests and r["tests"] >= 0.05 * peak_tests]
+    tb = sum(r["traverse"] for r in busy)
+    tn = sum(r["narrow"] for r in busy)
+    busy_bytes = sum(64.0 * n_ab + 8.0 * r["leaves"] for r in busy)
+    busy_ops = NARROW_OPS_PER_TEST * sum(r["tests"] for r in busy)
+    roofs["traverse"]["busy_steps"] = {
+        "steps": [r["step"] for r in busy], "ms": tb, "algorithmic_bytes": busy_bytes,
+        "achieved": busy_bytes / (tb / 1e3) / 1e9 if tb > 0 else None,
+        "frac": busy_bytes / (tb / 1e3) / 1e9 / peak if tb > 0 else None,
+        "per_step_ms": [round(r["traverse"], 4) for r in busy]}
+    roofs["narrow"]["busy_steps"] = {
+        "steps": [r["step"] for r in busy], "ms": tn,
+        "achieved": busy_ops / (tn / 1e3) if tn > 0 else None,
+        "frac": busy_ops / (tn / 1e3) / FP32_OPS_PEAK if tn > 0 else None,
+        "per_step_ms": [round(r["narrow"], 4) for r in busy],
+        "narrow_tests": [r["tests"] for r in busy]}
+    roofline = dict(roofs[dom])
+    roofline["traffic"] = read_traffic(dom)
     cpu = (cpu_baseline(wl, a_np, b_np, first, nsteps)
            if (world == 1 and not args.no_cpu_baseline) else None)
     line = {
@@ -627,20 +727,16 @@ def run_ours(args, wl):
         "phase_source": "the same runs built and collided step by step with CUDA events "
                         "around every phase (after the timed region)",
         "stepwise_ms_per_run": statistics.mean(sw_ms),
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": read_traffic(dom), "algorithmic_bytes_per_launch": algo,
-                     "launch_ms": launch_ms,
-                     "average": "over every launch of the run (most time steps are almost "
-                                "empty: the bunches cross in the first ~10)",
-                     "busy_steps": {"steps": [r[0] for r in busy], "traverse_ms": tb,
-                                    "algorithmic_bytes": busy_bytes, "achieved": busy_gbs,
-                                    "frac": busy_gbs / peak if busy_gbs else None,
-                                    "per_step_ms": [round(r[1], 4) for r in busy],
-                                    "narrow_tests": [r[2] for r in busy]}},
+        "roofline": roofline,
+        "rooflines": roofs,
+        "roofline_note": "per-launch averages over every launch of the run (most time steps "
+                         "are almost empty: the bunches cross in the first ~10); busy_steps "
+                         "gives the steps where they cross",
         "pair_products": pairs,
         "depletion": depl,
         "ip_regime": ipr,
+        "crossing90_2x5e7": crossing,
+        "statistical_2x1e6_sample": stat,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 16},
@@ -693,84 +789,107 @@ def run_batch(args):
     bt.close()
 
 
-def run_statistical(args):
-    """The statistical workload (not the default line): 2 x 1e8 macro-photons,
-    weights U[1,10], Gamma(2, 5 MeV) energies, 32 steps.  A network trained on
-    the draws --train-seeds (all time steps, level L) estimates seed 0's yield;
-    the exact GPU traversal of the same steps is the reference for error and
-    time.  The in-sample error on the first training draw is reported too."""
+def surrogate_eval(n, kappa, L, train_seeds, test_seed, taus=(1e30,), epochs=30,
+                   model=None):
+    """The learned statistical regime on the statistical workload's shape
+    (weights U[1,10], Gamma(2, 5 MeV) energies, head-on Gaussian beams,
+    32 steps of 20 fs) with n macro-photons per beam: a network trained on
+    the draws train_seeds (all steps, level L) estimates the draw test_seed.
+    The exact GPU traversal of the same steps, with autotuned knobs, is the
+    reference for the yield error and the time; beside the network: the
+    paper's ST rate of the same node pairs (no network, no fitted scale) and
+    that rate times the one scale fitted on the training pairs.  Device times
+    with CUDA events: exact = frontier + traversal + narrow phase + band +
+    yield after each step's build; surrogate = cut traversal, features,
+    network, estimate and the exact fallback."""
     import torch
 
     from paper_1608_01125_gb300 import binding
-    torch.cuda.set_device(0)
-    L = args.level
-    n = args.stat_photons
-    model = os.path.join(tempfile.gettempdir(), f"trilens_surrogate_L{L}.bin")
-    seeds = [int(x) for x in str(args.train_seeds).split(",")]
+    model = model or os.path.join(tempfile.gettempdir(), f"trilens_surrogate_L{L}_{n}.bin")
     t0 = time.perf_counter()
-    wl1 = synth.statistical_1e8(n=n, seed=seeds[0])
+    wl1 = synth.statistical_1e8(n=n, seed=train_seeds[0])
     a1, b1 = synth.beams(wl1)
-    train_exact = 0.0
-    with binding.Collider(a1, b1, wl1.dt, wl1.kappa) as col:
+    with binding.Collider(a1, b1, wl1.dt, kappa) as col:
         col.surrogate_collect(list(range(wl1.steps)), L)
-        train_exact = float(col.surrogate_dataset()[1].sum())
-        for sd in seeds[1:]:  # further draws: their labelled pairs join the training set
+        for sd in train_seeds[1:]:  # further draws: their labelled pairs join the training set
             wlx = synth.statistical_1e8(n=n, seed=sd)
             ax, bx = synth.beams(wlx)
-            with binding.Collider(ax, bx, wlx.dt, wlx.kappa) as cx:
+            with binding.Collider(ax, bx, wlx.dt, kappa) as cx:
                 cx.surrogate_collect(list(range(wlx.steps)), L)
                 x, lab, st = cx.surrogate_dataset()
             del ax, bx
             col.surrogate_add_samples(x, lab, st, L)
-        col.surrogate_fit(30, 7)
+        col.surrogate_fit(epochs, 7)
         info = col.surrogate_info()
         col.surrogate_save(model)
-        t_train = time.perf_counter() - t0
-        # in-sample: the first training draw, estimated by the fitted network
-        train_sur = sum(col.surrogate_step(k, L)["yield"] for k in range(wl1.steps))
     del a1, b1
-    wl0 = synth.statistical_1e8(n=n, seed=0)
+    t_train = time.perf_counter() - t0
+    wl0 = synth.statistical_1e8(n=n, seed=test_seed)
     a0, b0 = synth.beams(wl0)
-    taus = [float(t) for t in str(args.tau).split(",")]
     exact = ms_exact = ms_build = 0.0
     acc = {t: dict(sur=0.0, st=0.0, ms=0.0, pairs=0, fb=0) for t in taus}
-    with binding.Collider(a0, b0, wl0.dt, wl0.kappa) as col:
-        col.surrogate_load(model)
+    with binding.Collider(a0, b0, wl0.dt, kappa) as col:
+        trained_knobs = col.tuning()  # the hierarchy the network was trained on
+        tuned = col.autotune([wl0.steps // 2 - 1, wl0.steps // 2, wl0.steps // 2 + 1])
         col.timing(True)
-        for k in range(wl0.steps):
+        for k in range(wl0.steps):  # the exact traversal with the fastest knobs
             col.phase_ms(reset=True)
             col.build(k)
             col.collide(k)
             ph, _ = col.phase_ms()
-            ms_exact += ph["expand"] + ph["traverse"] + ph["band"] + ph["yield"]
+            ms_exact += sum(ph[p] for p in ("expand", "traverse", "narrow", "band", "yield"))
             ms_build += sum(ph[p] for p in ("propagate", "sort", "gather", "emit", "refit"))
             exact += col.stats()["weighted"]
+        col.set_tuning(*[trained_knobs[k] for k in ("leaf_bucket", "stack_depth", "block_shape",
+                                                    "budget")])
+        col.surrogate_load(model)
+        for k in range(wl0.steps):  # the surrogate on the level-L cut it was trained on
             for t in taus:
                 r = col.surrogate_step(k, L, t)
-                a = acc[t]
-                a["sur"] += r["yield"]
-                a["st"] += r["st_yield"]
-                a["ms"] += r["ms"]
-                a["pairs"] += r["pairs"]
-                a["fb"] += r["fallback_pairs"]
+                q = acc[t]
+                q["sur"] += r["yield"]
+                q["st"] += r["st_yield"]
+                q["ms"] += r["ms"]
+                q["pairs"] += r["pairs"]
+                q["fb"] += r["fallback_pairs"]
+        torch.cuda.synchronize()
+    out = []
     for t in taus:
-        a = acc[t]
+        q = acc[t]
+        out.append({"tau": t, "speedup": ms_exact / q["ms"], "yield_error": (q["sur"] - exact) / exact,
+                    "st_rate_error": (q["st"] - exact) / exact,
+                    "st_scaled_error": (info["st_calib"] * q["st"] - exact) / exact,
+                    "st_scale": info["st_calib"], "exact_weighted_yield": exact,
+                    "surrogate_weighted_yield": q["sur"], "exact_traversal_ms": ms_exact,
+                    "surrogate_ms": q["ms"], "build_ms": ms_build, "pairs": q["pairs"],
+                    "fallback_pairs": q["fb"]})
+    return {"photons_per_beam": n, "kappa": kappa, "level_L": L, "time_steps": wl0.steps,
+            "train": f"seeds {list(train_seeds)}, all steps", "test": f"seed {test_seed}, all steps",
+            "train_samples": info["samples"], "train_s": t_train, "exact_tuning": tuned,
+            "results": out}
+
+
+def run_statistical(args):
+    """The statistical workload (not the default line): 2 x 1e8 macro-photons,
+    weights U[1,10], Gamma(2, 5 MeV) energies, 32 steps; see surrogate_eval."""
+    import torch
+    torch.cuda.set_device(0)
+    seeds = [int(x) for x in str(args.train_seeds).split(",")]
+    taus = [float(t) for t in str(args.tau).split(",")]
+    wl = synth.statistical_1e8(n=args.stat_photons)
+    r = surrogate_eval(args.stat_photons, wl.kappa, args.level, seeds, 0, taus)
+    for q in r["results"]:
         line = {"metric": "surrogate vs exact GPU traversal speedup at <=1% yield error",
-                "value": ms_exact / a["ms"], "unit": "x", "n_gpus": 1, "steps": wl0.steps,
-                "warmup": 0, "ms_per_step": a["ms"] / wl0.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32+f64 exact",
-                "data": "synthetic",
-                "config": {"workload": wl0.name, "photons_per_beam": n, "time_steps": wl0.steps,
-                           "level_L": L, "tau": t,
-                           "train": f"seeds {args.train_seeds}, all steps",
-                           "test": "seed 0, all steps"},
-                "yield_error": (a["sur"] - exact) / exact,
-                "st_yield_error": (a["st"] - exact) / exact,
-                "train_draw_yield_error": (train_sur - train_exact) / train_exact,
-                "exact_weighted_yield": exact, "surrogate_weighted_yield": a["sur"],
-                "exact_traversal_ms": ms_exact, "surrogate_ms": a["ms"], "build_ms": ms_build,
-                "pairs": a["pairs"], "fallback_pairs": a["fb"], "train_samples": info["samples"],
-                "train_s": t_train}
+                "value": q["speedup"], "unit": "x", "n_gpus": 1, "steps": wl.steps,
+                "warmup": 0, "ms_per_step": q["surrogate_ms"] / wl.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 network, f32+f64 exact", "data": "synthetic",
+                "config": {"workload": wl.name, "photons_per_beam": args.stat_photons,
+                           "time_steps": wl.steps, "level_L": args.level, "tau": q["tau"],
+                           "train": r["train"], "test": r["test"]},
+                **{k: v for k, v in q.items() if k != "tau"},
+                "train_samples": r["train_samples"], "train_s": r["train_s"],
+                "exact_tuning": r["exact_tuning"]}
         print(json.dumps(line), flush=True)
 
 
@@ -783,6 +902,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depletion", action="store_true",
                     help="skip the depletion leg (run-long depletion after each step)")
+    ap.add_argument("--no-statistical", action="store_true",
+                    help="skip the surrogate leg on a 2 x 1e6 statistical sample")
+    ap.add_argument("--no-crossing", action="store_true",
+                    help="skip the leg on busy steps of the 2 x 5e7 crossing workload")
     ap.add_argument("--no-ip", action="store_true",
                     help="skip the IP-regime leg (swarm split + exact run of real photons)")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
