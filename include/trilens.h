@@ -77,7 +77,7 @@ typedef struct {
   double kappa;        /* cross-section amplification, > 0 (r^2 = kappa sigma / pi) */
   int32_t precision;   /* enum trilens_precision */
   int32_t leaf_bucket; /* photons per hierarchy leaf, 1..32 (0: 4) */
-  int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (0: 256) */
+  int32_t stack_depth; /* traversal stack entries per warp, 64..4096 (0: 512) */
   int32_t block_shape; /* traversal warps per block, 1..8 (0: 4) */
   int64_t spin_limit;  /* iteration limit of every device wait (0: 1<<22) */
 } trilens_params;
@@ -297,7 +297,8 @@ int trilens_collide_batch(const trilens_beam *a, const trilens_beam *b, const tr
 /* ---- tuning -----------------------------------------------------------------
  * The hit set never depends on these knobs; only the time does.
  *   leaf_bucket  photons per hierarchy leaf (1..32)
- *   stack_depth  traversal stack entries per warp, in shared memory (64..4096)
+ *   stack_depth  traversal stack entries per warp in shared memory (64..4096; the
+ *                rest of a warp's stack is its private spill area in global memory)
  *   block_shape  traversal warps per block (1..8)
  *   budget       traversal iterations a warp spends on one work item before it
  *                hands the rest on, as chunks of 8 node pairs, to the step's

@@ -241,6 +241,7 @@ void trilens_destroy(trilens_ctx *c) {
   cudaFree(c->hits);
   cudaFree(c->band);
   cudaFree(c->leaves);
+  cudaFree(c->spill);
   cudaFree(c->ctr);
   cudaFree(c->partials);
   cudaFree(c->build_status);
@@ -289,7 +290,7 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
   c->stream = (cudaStream_t)stream;
   c->p = *p;
   if (c->p.leaf_bucket == 0) c->p.leaf_bucket = 4;
-  if (c->p.stack_depth == 0) c->p.stack_depth = 256;
+  if (c->p.stack_depth == 0) c->p.stack_depth = 512;
   if (c->p.block_shape == 0) c->p.block_shape = 4;
   if (c->p.spin_limit == 0) c->p.spin_limit = 1ll << 22;
   const trilens_beam *bs[2] = {a, b};
@@ -366,15 +367,19 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
       return rcq;
     }
   }
+  if ((rc = alloc_spill(c, c->spill_per_warp, (unsigned long long)c->trav_blocks * c->trav_warps))) {
+    trilens_destroy(c);
+    return rc;
+  }
   c->hit_cap = std::max<unsigned long long>(1 << 16, 2ull * (c->beam[0].n + c->beam[1].n));
   CK(dalloc(&c->hits, c->hit_cap));
   c->band_cap = std::max<unsigned long long>(1 << 16, (c->beam[0].n + c->beam[1].n) / 4);
   CK(dalloc(&c->band, c->band_cap));
-  // leaf pairs: 16 per photon to start (a busy step of 2 x 1M head-on lists
-  // ~2.6e7 with single-photon buckets), at most 2^27 (1 GiB) before a step
-  // asks for more
+  // the leaf-pair list: 16 per photon to start (a busy step of 2 x 1M
+  // head-on lists ~2.6e7 with single-photon buckets), at most 2^29 (4 GiB)
+  // before a step asks for more
   c->leaf_cap = std::min<unsigned long long>(
-      std::max<unsigned long long>(1 << 20, 16ull * (c->beam[0].n + c->beam[1].n)), 1ull << 27);
+      std::max<unsigned long long>(1 << 20, 16ull * (c->beam[0].n + c->beam[1].n)), 1ull << 29);
   CK(dalloc(&c->leaves, c->leaf_cap));
   CK(dalloc(&c->ctr, 1));
   CK(cudaMallocHost((void **)&c->ctr_host, sizeof(TLCounters)));
@@ -494,6 +499,8 @@ tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   a.leaf_cap = c->leaf_cap;
   a.queue = reinterpret_cast<unsigned long long *>(c->queue);
   a.queue_cap = c->queue_cap;
+  a.spill = c->spill;
+  a.spill_per_warp = c->spill_per_warp;
   a.spin_limit = c->p.spin_limit;
   a.stack_depth = c->p.stack_depth;
   a.leaf_bucket = c->p.leaf_bucket;
@@ -578,13 +585,17 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
       if ((rc = grow(c, &c->hits, &c->hit_cap, h.hits + (again ? h.band : 0)))) return rc;
       again = true;
     }
-    if (st & TL_ST_LEAFQ) {
-      if ((rc = grow(c, &c->leaves, &c->leaf_cap, h.leaf_pairs))) return rc;
-      again = true;
-    }
     if (st & TL_ST_SPILL_OVF) {  // the queue: larger, and every slot the sentinel again
       const unsigned long long need = kQueueChunk * (h.q_tail + h.q_tail / 4 + 1024);
       if ((rc = alloc_queue(c, std::max(need, 2 * c->queue_cap)))) return rc;
+      again = true;
+    }
+    if (st & TL_ST_PRIV_OVF) {  // a warp's spill area: twice as large
+      if ((rc = alloc_spill(c, 2 * c->spill_per_warp, c->spill_warps))) return rc;
+      again = true;
+    }
+    if (st & TL_ST_LEAFQ) {  // the leaf-pair list: large enough for this step
+      if ((rc = grow(c, &c->leaves, &c->leaf_cap, h.leaf_pairs))) return rc;
       again = true;
     }
     if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
@@ -848,7 +859,8 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
       CK(cudaStreamSynchronize(c->stream));
       return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit");
     }
-    if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF | TL_ST_LEAFQ)))
+    if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF |
+                TL_ST_PRIV_OVF | TL_ST_LEAFQ)))
       return TRILENS_OK;
     // grow what overflowed (to the largest size a step asked for) and capture again
     TLRunAcc m;
@@ -858,6 +870,8 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
     if (st & TL_ST_HIT_OVF && (rc = grow(c, &c->hits, &c->hit_cap, m.max_hits + m.max_band)))
       return rc;
     if (st & TL_ST_BAND_OVF && (rc = grow(c, &c->band, &c->band_cap, m.max_band))) return rc;
+    if (st & TL_ST_PRIV_OVF && (rc = alloc_spill(c, 2 * c->spill_per_warp, c->spill_warps)))
+      return rc;
     if (st & TL_ST_LEAFQ && (rc = grow(c, &c->leaves, &c->leaf_cap, m.max_leaves))) return rc;
     if (st & TL_ST_SPILL_OVF) {  // the queue: larger, and every slot the sentinel again
       const unsigned long long need = kQueueChunk * (m.max_handed + m.max_handed / 4 + 1024);
@@ -954,6 +968,11 @@ static int apply_tuning(trilens_ctx *c, int bucket, int depth, int warps, int bu
       c->front[k] = nullptr;
       CK(dalloc(&c->front[k], c->front_cap));
     }
+  }
+  const unsigned long long warps_now = (unsigned long long)c->trav_blocks * c->trav_warps;
+  if (warps_now > c->spill_warps) {
+    const int rcs = alloc_spill(c, c->spill_per_warp, warps_now);
+    if (rcs) return rcs;
   }
   const unsigned long long need_queue =
       2ull * c->trav_blocks * c->trav_warps * (unsigned long long)depth;
@@ -1097,16 +1116,20 @@ int trilens_autotune(trilens_ctx *c, const int64_t *steps, int32_t n_steps,
     return TRILENS_OK;
   }
   // coordinate descent over the four knobs, each swept with the others
-  // fixed at the best so far; results never depend on them, only time does
+  // fixed at the best so far (stack depth first: a shallow stack moves work
+  // to the spill areas, which would bias the other sweeps); results never
+  // depend on the knobs, only time does
   int best[4] = {c->p.leaf_bucket, c->p.stack_depth, c->p.block_shape, c->budget};
-  static const int cand[4][5] = {{1, 2, 4, 8, 16}, {128, 256, 512, 0, 0}, {2, 4, 8, 0, 0},
+  static const int cand[4][5] = {{1, 2, 4, 8, 16}, {256, 512, 1024, 0, 0}, {2, 4, 8, 0, 0},
                                  {8, 16, 32, 64, 0}};
+  static const int order[4] = {1, 0, 2, 3};
   double best_ms = 1e30;
   int rc = apply_tuning(c, best[0], best[1], best[2], best[3]);
   if (rc) return rc;
   if ((rc = time_steps(c, steps, n_steps, &best_ms))) return rc;  // warm-up
   if ((rc = time_steps(c, steps, n_steps, &best_ms))) return rc;
-  for (int knob = 0; knob < 4; ++knob) {
+  for (int oi = 0; oi < 4; ++oi) {
+    const int knob = order[oi];
     for (int j = 0; j < 5 && cand[knob][j]; ++j) {
       int t[4] = {best[0], best[1], best[2], best[3]};
       t[knob] = cand[knob][j];
@@ -1235,6 +1258,11 @@ int trilens_debug_shrink_buffers(trilens_ctx *c, int64_t cap) {
   CK(dalloc(&c->hits, n));
   CK(dalloc(&c->band, n));
   CK(dalloc(&c->leaves, n));
+  {  // spill areas of cap entries per warp (at least 64)
+    const int rcs = alloc_spill(c, (unsigned)std::max<int64_t>(64, std::min<int64_t>(cap, 1 << 20)),
+                                c->spill_warps);
+    if (rcs) return rcs;
+  }
   const int rc = alloc_queue(c, n);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->stream));

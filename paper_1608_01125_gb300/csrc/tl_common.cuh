@@ -67,7 +67,8 @@ enum {
   TL_ST_SPILL_OVF = 4,  // the traversal queue overflowed (or a slot was not free)
   TL_ST_FRONT_OVF = 8,
   TL_ST_TIMEOUT = 16,
-  TL_ST_LEAFQ = 32  // the leaf-pair list overflowed
+  TL_ST_LEAFQ = 32,    // the leaf-pair list overflowed
+  TL_ST_PRIV_OVF = 64  // a traversal warp's private spill area overflowed
 };
 
 // Per-step device counters; zeroed by the step's init kernel.
@@ -195,8 +196,10 @@ struct TravArgs {
   unsigned long long band_cap;
   uint2 *leaves;  // overlapping leaf-bucket pairs (packed first | (count - 1) << 27)
   unsigned long long leaf_cap;
-  unsigned long long *queue;  // traversal work queue: chunks of 8 (ref A, ref B) pairs
+  unsigned long long *queue;  // traversal work queue: chunks of 32 (ref A, ref B) pairs
   unsigned long long queue_cap;  // in pairs
+  uint2 *spill;                  // per traversal warp: the bottom of its stack
+  unsigned spill_per_warp;       // entries per warp
   int stack_depth;
   int leaf_bucket;               // photons per leaf bucket at most
   const unsigned *build_status;  // build errors (a timed-out sort) skip the traversal

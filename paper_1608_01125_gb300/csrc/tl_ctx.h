@@ -38,6 +38,9 @@ struct trilens_ctx {
   uint2 *front[2]{};
   uint2 *queue = nullptr;  // traversal work queue (every free slot holds the sentinel)
   unsigned long long queue_cap = 0;
+  uint2 *spill = nullptr;  // traversal warps' private spill areas
+  unsigned spill_per_warp = 8192;
+  unsigned long long spill_warps = 0;  // warps the areas are allocated for
   uint2 *hits = nullptr;
   unsigned long long hit_cap = 0;
   uint2 *band = nullptr;
@@ -115,13 +118,33 @@ static inline cudaError_t dalloc(T **p, size_t count) {
 }
 
 // (re)allocate the traversal queue with cap slots, every slot the sentinel
+// the traversal queue never grows past 2^30 node pairs (8 GiB): a step that
+// asks for more fails with TRILENS_ERR_STACK (deeper stacks hand on less)
 static inline int alloc_queue(trilens_ctx *c, unsigned long long cap) {
+  if (cap > (1ull << 30))
+    return fail(c, TRILENS_ERR_STACK, "the traversal queue would need %llu node pairs",
+                (unsigned long long)cap);
   cudaFree(c->queue);
   c->queue = nullptr;
   c->queue_cap = 0;
   CK(dalloc(&c->queue, (size_t)cap));
   CK(cudaMemsetAsync(c->queue, 0xff, sizeof(uint2) * (size_t)cap, c->stream));
   c->queue_cap = cap;
+  return TRILENS_OK;
+}
+
+// the traversal warps' private spill areas, for blocks x warps warps of
+// per_warp entries each (at most 2^20 per warp)
+static inline int alloc_spill(trilens_ctx *c, unsigned per_warp, unsigned long long warps) {
+  if (per_warp > (1u << 20))
+    return fail(c, TRILENS_ERR_STACK, "a traversal warp's spill area would need %u entries",
+                per_warp);
+  cudaFree(c->spill);
+  c->spill = nullptr;
+  c->spill_warps = 0;
+  CK(dalloc(&c->spill, (size_t)per_warp * warps));
+  c->spill_per_warp = per_warp;
+  c->spill_warps = warps;
   return TRILENS_OK;
 }
 

@@ -481,11 +481,17 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
 // Persistent warps share one work queue.  Its items come first from the
 // frontier, in groups of up to 32 node pairs (indices below nf), then from
 // the queue's chunks of up to 32 node pairs each (256 bytes).  A warp that
-// has spent `budget` iterations on its item while other warps wait for work
-// (ctr->hungry > 0), or whose stack is nearly full, hands on the bottom of
-// its stack (the shallowest, largest subtrees; all but the top 32 entries,
-// or half of a smaller stack) as chunks that the waiting warps take; a warp
-// whose stack is full hands on the pair that does not fit as a chunk of one.
+// waits for a chunk is counted in ctr->hungry while it waits; a warp that
+// has spent `budget` iterations on its item while h > 0 warps wait hands on
+// up to h chunks.  A warp's own stack has two
+// levels: the top in shared memory (D entries), the bottom in its private
+// spill area in global memory.  A warp pops at most P = min(32, D / 8) pairs
+// per iteration (so it pushes at most 4P); when the next iteration's pushes
+// might not fit its shared stack, the bottom of it (up to D / 2 entries)
+// moves to the spill area, and when the shared stack runs dry it is refilled from the
+// spill area's top.  So no work leaves a warp except the chunks it hands on
+// to waiting warps, taken from the bottom of its spill area first (the
+// shallowest pairs it holds), else from the bottom of its shared stack.
 // Unused and free entries hold a sentinel.  A writer fills a chunk's entries
 // 1..31, fences, then swaps entry 0 in; a taker swaps the sentinel back into
 // entry 0 as it reads it (atomic exchange) and waits while it is still free
@@ -499,12 +505,19 @@ __device__ __forceinline__ unsigned long long pack2(uint2 v) {
   return (unsigned long long)v.x | ((unsigned long long)v.y << 32);
 }
 
+// chunks a working warp hands on per waiting warp, at most
+#ifndef TL_DONATE_MAX
+#define TL_DONATE_MAX 1
+#endif
+
 // Launch bounds: at most 8 warps per block and registers for 4 such blocks
 // per SM (63 registers, no spills; the narrow phase is a kernel of its own).
 #ifndef TL_TRAV_MINBLOCKS
 #define TL_TRAV_MINBLOCKS 4
 #endif
-// a warp's queued leaf pairs to the step's list (one atomic per warp)
+// A warp's queued leaf pairs to the step's list (one atomic per warp).  The
+// count keeps every leaf pair; pairs past the list's end are dropped and the
+// step is flagged (TL_ST_LEAFQ): the host grows the list and repeats it.
 __device__ __forceinline__ void spill_leaves(const TravArgs &a, const WarpSmem &ws, int nq,
                                              int lane) {
   unsigned long long base = 0;
@@ -539,49 +552,114 @@ __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_t
   unsigned long long *Q = a.queue;
   const unsigned long long qcap = a.queue_cap / kGroup;  // chunks
   const unsigned lt = (1u << lane) - 1u;
+  // the private spill area: entries [gbot, gtop) hold the stack's bottom
+  uint2 *gs = a.spill + (size_t)(blockIdx.x * (blockDim.x >> 5) + warp) * a.spill_per_warp;
+  const int W = (int)a.spill_per_warp;
+  const int P = min(32, D >> 3);  // pops per iteration at most
+  int gbot = 0, gtop = 0;
   int sp = 0, nq = 0, iters = 0;
   bool holding = false;  // this warp holds an item (counted in flight)
   bool handed = false;   // ... and has handed pieces of it on
   unsigned long long node_tests = 0;
   while (true) {
-    if (sp > 1 && budget > 0 && (iters >= budget || sp > D - 4 * 32)) {
+    // the bottom of a shared stack that could not take the next iteration's
+    // pushes (min(sp, P) pops, 4 pushes each) moves to the spill area
+    if (sp + 3 * min(sp, P) > D) {
+      const int m = min(D >> 1, sp - P);
+      if (gbot > 0 && gtop + m > W) {  // compact the spill area first
+        const int cnt = gtop - gbot;
+        for (int e0 = 0; e0 < cnt; e0 += 32) {
+          uint2 v = make_uint2(0u, 0u);
+          if (e0 + lane < cnt) v = gs[gbot + e0 + lane];
+          __syncwarp();
+          if (e0 + lane < cnt) gs[e0 + lane] = v;
+          __syncwarp();
+        }
+        gtop = cnt;
+        gbot = 0;
+      }
+      if (gtop + m <= W) {
+        for (int e = lane; e < m; e += 32) gs[gtop + e] = stack[e];
+        __syncwarp();
+        for (int e0 = 0; e0 < sp - m; e0 += 32) {
+          uint2 v = make_uint2(0u, 0u);
+          if (e0 + lane < sp - m) v = stack[m + e0 + lane];
+          __syncwarp();
+          if (e0 + lane < sp - m) stack[e0 + lane] = v;
+          __syncwarp();
+        }
+        gtop += m;
+        sp -= m;
+      } else if (lane == 0) {
+        atomicOr(&ctr->status, (unsigned)TL_ST_PRIV_OVF);  // the host grows it, repeats the step
+      }
+    }
+    // the shared stack ran dry: refill it from the spill area's top
+    if (sp == 0 && gtop > gbot) {
+      const int m = min(gtop - gbot, D >> 1);
+      for (int e = lane; e < m; e += 32) stack[e] = gs[gtop - m + e];
+      __syncwarp();
+      gtop -= m;
+      sp = m;
+      if (gtop == gbot) gtop = gbot = 0;
+    }
+    if ((sp > 1 || gtop > gbot) && budget > 0 && iters >= budget) {
       unsigned h = 0;
       if (lane == 0) h = *(volatile unsigned *)&ctr->hungry;
       h = __shfl_sync(0xffffffffu, h, 0);
       iters = 0;
-      if (h > 0 || sp > D - 4 * 32) {
-        // hand on the bottom of the stack: all but the top 32 entries, or the
-        // bottom half of a smaller stack; the chunks are counted before this
-        // item is counted finished
-        const int give = sp > kGroup ? sp - kGroup : sp / 2;
-        const int nch = (give + kGroup - 1) / kGroup;
+      if (h > 0u) {
+        // hand on chunks of 32 to the waiting warps, at most TL_DONATE_MAX
+        // per waiting warp: the spill area's entries (its bottom first), then
+        // all but the top 32 entries of the shared stack (or half of a stack
+        // of at most 64); they are counted (q_tail) before this item is
+        // counted finished
+        // chunks available, each non-empty: the spill area's, then those the
+        // loop below cuts from the shared stack (every reserved chunk must be
+        // published, so the count follows the loop's own cuts)
+        int avail = (gtop - gbot + kGroup - 1) / kGroup;
+        for (int r = sp; ; ) {
+          const int g = min(kGroup, r > 2 * kGroup ? r - kGroup : r / 2);
+          if (g < 1) break;
+          ++avail;
+          r -= g;
+        }
+        const int nch = (int)min((unsigned)avail, (unsigned)TL_DONATE_MAX * h);
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&ctr->q_tail, (unsigned long long)nch);
         handed = true;
         base = __shfl_sync(0xffffffffu, base, 0);
-        for (int e = lane; e < nch * kGroup; e += 32) {  // entries 1..31 of every chunk
-          if ((e % kGroup) != 0 && base + e / kGroup < qcap)
-            Q[(base + e / kGroup) * kGroup + e % kGroup] = e < give ? pack2(stack[e]) : kQFree;
-        }
-        __threadfence();
-        __syncwarp();
-        for (int c = lane; c < nch; c += 32) {  // then entry 0: the chunk is ready
+        for (int c = 0; c < nch; ++c) {
+          const bool fs = gtop > gbot;
+          const int give = fs ? min(kGroup, gtop - gbot)
+                              : min(kGroup, sp > 2 * kGroup ? sp - kGroup : sp / 2);
+          const uint2 *src = fs ? gs + gbot : stack;
           if (base + c < qcap) {
-            if (atomicExch(Q + (base + c) * kGroup, pack2(stack[c * kGroup])) != kQFree)
+            if (lane >= 1)
+              Q[(base + c) * kGroup + lane] = lane < give ? pack2(src[lane]) : kQFree;
+            __threadfence();
+            __syncwarp();
+            if (lane == 0 && atomicExch(Q + (base + c) * kGroup, pack2(src[0])) != kQFree)
               atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);  // a chunk was not free
-          } else {
+          } else if (lane == 0) {
             atomicOr(&ctr->status, (unsigned)TL_ST_SPILL_OVF);
           }
+          __syncwarp();
+          if (fs) {
+            gbot += give;
+            if (gbot == gtop) gbot = gtop = 0;
+          } else {  // the kept entries move to the bottom
+            const int keep = sp - give;
+            for (int e0 = 0; e0 < keep; e0 += 32) {
+              uint2 v = make_uint2(0u, 0u);
+              if (e0 + lane < keep) v = stack[give + e0 + lane];
+              __syncwarp();
+              if (e0 + lane < keep) stack[e0 + lane] = v;
+              __syncwarp();
+            }
+            sp = keep;
+          }
         }
-        __syncwarp();
-        // the kept entries (at most 32) move to the bottom
-        const int keep = sp - give;
-        uint2 v = make_uint2(0u, 0u);
-        if (lane < keep) v = stack[give + lane];
-        __syncwarp();
-        if (lane < keep) stack[lane] = v;
-        __syncwarp();
-        sp = keep;
       }
     }
     if (sp == 0) {
@@ -613,7 +691,7 @@ __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_t
               __threadfence();  // entry 0 seen: the chunk's other entries are written
               break;
             }
-            if (!waiting) {  // tell working warps that a warp waits for work
+            if (!waiting) {  // working warps see that a warp waits for work
               waiting = true;
               atomicAdd(&ctr->hungry, 1u);
             }
@@ -657,7 +735,7 @@ __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_t
     }
     ++iters;
     // one popped pair per lane
-    const int npop = min(sp, 32);
+    const int npop = min(sp, P);
     sp -= npop;
     const bool active = lane < npop;
     const uint2 pr = active ? stack[sp + lane] : make_uint2(0u, 0u);
