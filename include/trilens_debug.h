@@ -24,6 +24,13 @@ extern "C" {
  * normal operation.  INVALID for a NULL context. */
 int trilens_debug_stall_sort(trilens_ctx *c, int on);
 
+/* Do the traversal and narrow phase of every following step in `parts`
+ * slices of its frontier (1..4096), as the library does by itself when a
+ * step's leaf-pair list would exceed its largest size (2^30 pairs).  The hit
+ * set never depends on it.  INVALID for a NULL context or parts outside
+ * 1..4096. */
+int trilens_debug_set_parts(trilens_ctx *c, int32_t parts);
+
 /* Replace the context's spin limit (iterations of every bounded device wait,
  * >= 1).  INVALID for a NULL context or limit < 1. */
 int trilens_debug_set_spin_limit(trilens_ctx *c, int64_t limit);

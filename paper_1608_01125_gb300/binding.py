@@ -126,6 +126,8 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_set_key_bits.restype = ctypes.c_int
         L.trilens_debug_eval64.argtypes = [vp, vp, i64, i32, vp]
         L.trilens_debug_eval64.restype = ctypes.c_int
+        L.trilens_debug_set_parts.argtypes = [vp, i32]
+        L.trilens_debug_set_parts.restype = ctypes.c_int
         L.trilens_debug_band_stress.argtypes = [ctypes.c_uint64, i64, ctypes.c_double,
                                                 ctypes.c_double, vp, vp, i64, vp]
         L.trilens_debug_band_stress.restype = ctypes.c_int
@@ -446,6 +448,9 @@ class Collider:
         _check(lib().trilens_deplete_rounds(self.ctx, ctypes.byref(r)), self.ctx)
         return {"accepted": int(acc.value), "transferred": float(tr.value),
                 "rounds": int(r.value) if n_hits else 0}
+
+    def debug_set_parts(self, parts: int):
+        _check(lib().trilens_debug_set_parts(self.ctx, int(parts)), self.ctx)
 
     def debug_set_spin_limit(self, limit: int):
         _check(lib().trilens_debug_set_spin_limit(self.ctx, int(limit)), self.ctx)

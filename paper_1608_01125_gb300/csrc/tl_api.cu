@@ -28,7 +28,8 @@ cudaError_t launch_widen(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, 
 cudaError_t launch_narrow(const TravArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
                             unsigned long long list_n, int from_frontier, int budget, int blocks,
-                            int warps, cudaStream_t s);
+                            int warps, cudaStream_t s, int part, int nparts);
+cudaError_t launch_part_init(TLCounters *ctr, cudaStream_t s);
 cudaError_t launch_band(const TravArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_yield(const TravArgs &a, void *partials, int blocks, cudaStream_t s);
 size_t partial_bytes();
@@ -53,6 +54,40 @@ enum {
 constexpr int kWidenLevels = 5;
 // node pairs per traversal queue chunk and frontier item (tl_traverse.cu)
 constexpr unsigned long long kQueueChunk = 32;
+// the leaf-pair list never grows past 2^30 pairs (8 GiB): a step that lists
+// more is done in parts, slices of its frontier, each listing at most that
+constexpr unsigned long long kLeafListMax = 1ull << 30;
+
+// after a step overflowed the leaf-pair list (the largest part listed need
+// pairs): a larger list, or more parts
+static int leaves_for(trilens_ctx *c, unsigned long long need) {
+  if (need + need / 4 + 1024 <= kLeafListMax) return grow(c, &c->leaves, &c->leaf_cap, need);
+  if (c->leaf_cap < kLeafListMax) {
+    cudaFree(c->leaves);
+    c->leaves = nullptr;
+    c->leaf_cap = 0;
+    CK(dalloc(&c->leaves, (size_t)kLeafListMax));
+    c->leaf_cap = kLeafListMax;
+  }
+  const unsigned long long per = kLeafListMax / 2;  // room for uneven parts
+  const unsigned long long more = (need + per - 1) / per;
+  if ((unsigned long long)c->parts * more > 4096)
+    return fail(c, TRILENS_ERR_STACK, "a step would need more than 4096 parts");
+  c->parts = (int)(c->parts * more);
+  return TRILENS_OK;
+}
+
+// the traversal and the narrow phase of a step, part by part
+static int traverse_parts(trilens_ctx *c, const tl::TravArgs &a, const uint2 *seeds,
+                          unsigned n_seeds) {
+  for (int p = 0; p < c->parts; ++p) {
+    if (p > 0) CK(tl::launch_part_init(c->ctr, c->stream));
+    CK(tl::launch_traverse(a, c->front[0], c->front[1], seeds, seeds ? n_seeds : 0, seeds ? 0 : 1,
+                           c->budget, c->trav_blocks, c->trav_warps, c->stream, p, c->parts));
+    CK(tl::launch_narrow(a, 8 * c->n_sm, c->stream));
+  }
+  return TRILENS_OK;
+}
 
 // the frontier widening target: 64 pairs per resident traversal warp, two
 // full items each; and the frontier buffers' capacity for every start
@@ -537,18 +572,23 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
     }
     tmark(c, PH_EXPAND, 0, 1);
     c->phase_launches[PH_EXPAND] += seeds ? 1 : 2;
-    tmark(c, PH_TRAV, 0, 0);
-    if (seeds)
-      CK(tl::launch_traverse(a, c->front[0], c->front[1], seeds, n_seeds, 0, c->budget,
-                             c->trav_blocks, c->trav_warps, c->stream));
-    else
-      CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->budget, c->trav_blocks,
-                             c->trav_warps, c->stream));
-    tmark(c, PH_TRAV, 0, 1);
+    if (c->parts == 1) {
+      tmark(c, PH_TRAV, 0, 0);
+      CK(tl::launch_traverse(a, c->front[0], c->front[1], seeds, seeds ? n_seeds : 0,
+                             seeds ? 0 : 1, c->budget, c->trav_blocks, c->trav_warps, c->stream,
+                             0, 1));
+      tmark(c, PH_TRAV, 0, 1);
+      tmark(c, PH_NARROW, 0, 0);
+      CK(tl::launch_narrow(a, 8 * c->n_sm, c->stream));
+      tmark(c, PH_NARROW, 0, 1);
+    } else {  // parts: traversal and narrow phase timed together
+      tmark(c, PH_TRAV, 0, 0);
+      int rcp = traverse_parts(c, a, seeds, n_seeds);
+      if (rcp) return rcp;
+      tmark(c, PH_TRAV, 0, 1);
+      c->phase_launches[PH_TRAV] += 2 * (c->parts - 1);
+    }
     c->phase_launches[PH_TRAV] += 1;
-    tmark(c, PH_NARROW, 0, 0);
-    CK(tl::launch_narrow(a, 8 * c->n_sm, c->stream));
-    tmark(c, PH_NARROW, 0, 1);
     c->phase_launches[PH_NARROW] += 1;
     if (!a.fp64) {
       tmark(c, PH_BAND, 0, 0);
@@ -594,8 +634,8 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
       if ((rc = alloc_spill(c, 2 * c->spill_per_warp, c->spill_warps))) return rc;
       again = true;
     }
-    if (st & TL_ST_LEAFQ) {  // the leaf-pair list: large enough for this step
-      if ((rc = grow(c, &c->leaves, &c->leaf_cap, h.leaf_pairs))) return rc;
+    if (st & TL_ST_LEAFQ) {  // the leaf-pair list: larger, or the step in more parts
+      if ((rc = leaves_for(c, h.max_part_leaves))) return rc;
       again = true;
     }
     if (st & TL_ST_FRONT_OVF) return fail(c, TRILENS_ERR_STACK, "frontier overflow");
@@ -786,9 +826,10 @@ static int graph_collide(trilens_ctx *c, int64_t step, double *yields) {
     CK(tl::launch_expand(a, c->front[0], c->front[1], c->front_cap, c->front_target, kMaxLevels,
                          c->stream));
   }
-  CK(tl::launch_traverse(a, c->front[0], c->front[1], nullptr, 0, 1, c->budget, c->trav_blocks,
-                         c->trav_warps, c->stream));
-  CK(tl::launch_narrow(a, 8 * c->n_sm, c->stream));
+  {
+    const int rcp = traverse_parts(c, a, nullptr, 0);
+    if (rcp) return rcp;
+  }
   if (!a.fp64) CK(tl::launch_band(a, c->n_sm * 4, c->stream));
   CK(tl::launch_yield(a, c->partials, c->yield_blocks, c->stream));
   if (yields && c->n_inst > 1)
@@ -872,7 +913,7 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
     if (st & TL_ST_BAND_OVF && (rc = grow(c, &c->band, &c->band_cap, m.max_band))) return rc;
     if (st & TL_ST_PRIV_OVF && (rc = alloc_spill(c, 2 * c->spill_per_warp, c->spill_warps)))
       return rc;
-    if (st & TL_ST_LEAFQ && (rc = grow(c, &c->leaves, &c->leaf_cap, m.max_leaves))) return rc;
+    if (st & TL_ST_LEAFQ && (rc = leaves_for(c, m.max_leaves))) return rc;
     if (st & TL_ST_SPILL_OVF) {  // the queue: larger, and every slot the sentinel again
       const unsigned long long need = kQueueChunk * (m.max_handed + m.max_handed / 4 + 1024);
       if ((rc = alloc_queue(c, std::max(need, 2 * c->queue_cap)))) return rc;
@@ -1231,6 +1272,16 @@ int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int r
       c->phase_ms[ph] = 0.0;
       c->phase_launches[ph] = 0;
     }
+  }
+  return TRILENS_OK;
+}
+
+int trilens_debug_set_parts(trilens_ctx *c, int32_t parts) {
+  if (!c || parts < 1 || parts > 4096) return TRILENS_ERR_INVALID;
+  c->parts = parts;
+  if (c->gexec) {  // a captured run holds the old part count
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
   }
   return TRILENS_OK;
 }

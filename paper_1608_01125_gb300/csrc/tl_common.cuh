@@ -92,6 +92,10 @@ struct TLCounters {
   unsigned long long count;
   double weighted;
   unsigned long long hsum, hxor;
+  // a step done in parts (slices of its frontier): the leaf-pair count at
+  // the start of the current part, and the largest part's leaf pairs
+  unsigned long long leaf_base;
+  unsigned long long max_part_leaves;
 };
 
 // Totals of a captured multi-step run (accumulated on the device, step by

@@ -47,6 +47,7 @@ struct trilens_ctx {
   unsigned long long band_cap = 0;
   uint2 *leaves = nullptr;  // the step's overlapping leaf-bucket pairs
   unsigned long long leaf_cap = 0;
+  int parts = 1;  // a step's traversal in this many slices of its frontier
   TLCounters *ctr = nullptr;
   TLCounters *ctr_host = nullptr;  // pinned
   void *partials = nullptr;

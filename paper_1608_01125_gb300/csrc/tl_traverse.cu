@@ -515,13 +515,14 @@ __device__ __forceinline__ unsigned long long pack2(uint2 v) {
 #ifndef TL_TRAV_MINBLOCKS
 #define TL_TRAV_MINBLOCKS 4
 #endif
-// A warp's queued leaf pairs to the step's list (one atomic per warp).  The
-// count keeps every leaf pair; pairs past the list's end are dropped and the
-// step is flagged (TL_ST_LEAFQ): the host grows the list and repeats it.
+// A warp's queued leaf pairs to the step's list (one atomic per warp), from
+// the current part's start lbase.  The count keeps every leaf pair; pairs
+// past the list's end are dropped and the step is flagged (TL_ST_LEAFQ): the
+// host grows the list, or splits the step into more parts, and repeats it.
 __device__ __forceinline__ void spill_leaves(const TravArgs &a, const WarpSmem &ws, int nq,
-                                             int lane) {
+                                             int lane, unsigned long long lbase) {
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(&a.ctr->leaf_pairs, (unsigned long long)nq);
+  if (lane == 0) base = atomicAdd(&a.ctr->leaf_pairs, (unsigned long long)nq) - lbase;
   base = __shfl_sync(0xffffffffu, base, 0);
   for (int e = lane; e < nq; e += 32)
     if (base + e < a.leaf_cap) a.leaves[base + e] = ws.leafq[e];
@@ -530,7 +531,7 @@ __device__ __forceinline__ void spill_leaves(const TravArgs &a, const WarpSmem &
 
 __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_traverse(
     TravArgs a, const uint2 *F0, const uint2 *F1, const uint2 *list, unsigned long long list_n,
-    int from_frontier, int budget) {
+    int from_frontier, int budget, int part, int nparts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int D = a.stack_depth;
@@ -548,6 +549,14 @@ __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_t
     src0 = list;
     n0 = list_n;
   }
+  {  // this launch's part of the frontier: every leaf pair lies below exactly
+     // one frontier pair, so the parts split the step's work
+    const unsigned long long lo = n0 * (unsigned long long)part / (unsigned long long)nparts;
+    const unsigned long long hi = n0 * (unsigned long long)(part + 1) / (unsigned long long)nparts;
+    src0 += lo;
+    n0 = hi - lo;
+  }
+  const unsigned long long lbase = ctr->leaf_base;  // the list of this part starts here
   const unsigned long long nf = (n0 + kGroup - 1) / kGroup;  // frontier groups
   unsigned long long *Q = a.queue;
   const unsigned long long qcap = a.queue_cap / kGroup;  // chunks
@@ -794,11 +803,11 @@ __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_t
     if (lane == 0) node_tests += (unsigned long long)tested;
     __syncwarp();
     if (nq >= 32) {
-      spill_leaves(a, ws, nq, lane);
+      spill_leaves(a, ws, nq, lane, lbase);
       nq = 0;
     }
   }
-  if (nq) spill_leaves(a, ws, nq, lane);
+  if (nq) spill_leaves(a, ws, nq, lane, lbase);
   if (lane == 0 && node_tests) atomicAdd(&ctr->node_tests, node_tests);
 }
 
@@ -809,7 +818,9 @@ __global__ void __launch_bounds__(256) k_narrow(TravArgs a) {
   __shared__ WarpSmem wsm[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpSmem &ws = wsm[warp];
-  const unsigned long long n = min(a.ctr->leaf_pairs, a.leaf_cap);
+  const unsigned long long listed = a.ctr->leaf_pairs - a.ctr->leaf_base;  // this part's
+  const unsigned long long n = min(listed, a.leaf_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&a.ctr->max_part_leaves, listed);
   const unsigned long long stride = (unsigned long long)gridDim.x * (blockDim.x >> 5) * 32ull;
   unsigned long long tests = 0;
   int npend = 0;
@@ -910,7 +921,7 @@ __global__ void k_step_finish(const TLCounters *ctr, unsigned *run_status, TLRun
     if (ctr->hits > acc->max_hits) acc->max_hits = ctr->hits;
     if (ctr->band > acc->max_band) acc->max_band = ctr->band;
     if (ctr->q_tail > acc->max_handed) acc->max_handed = ctr->q_tail;
-    if (ctr->leaf_pairs > acc->max_leaves) acc->max_leaves = ctr->leaf_pairs;
+    if (ctr->max_part_leaves > acc->max_leaves) acc->max_leaves = ctr->max_part_leaves;
   }
 }
 
@@ -961,11 +972,25 @@ cudaError_t traverse_config(int fp64, int warps, int depth, int *blocks_per_sm) 
 
 cudaError_t launch_traverse(const TravArgs &a, const uint2 *F0, const uint2 *F1, const uint2 *list,
                             unsigned long long list_n, int from_frontier, int budget, int blocks,
-                            int warps, cudaStream_t s) {
+                            int warps, cudaStream_t s, int part, int nparts) {
   // a warp only waits for work that warps holding items (running ones) hand
   // on, so no block needs another to be resident
   const size_t smem = traverse_smem(warps, a.stack_depth);
-  k_traverse<<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier, budget);
+  k_traverse<<<blocks, warps * 32, smem, s>>>(a, F0, F1, list, list_n, from_frontier, budget,
+                                              part, nparts);
+  return cudaGetLastError();
+}
+
+// Before part p > 0 of a step: the leaf list starts again (at the count so
+// far) and the work queue's counters are cleared for the next traversal.
+__global__ void k_part_init(TLCounters *ctr) {
+  ctr->leaf_base = ctr->leaf_pairs;
+  ctr->q_head = ctr->q_done = ctr->q_tail = 0ull;
+  ctr->hungry = 0u;
+}
+
+cudaError_t launch_part_init(TLCounters *ctr, cudaStream_t s) {
+  k_part_init<<<1, 1, 0, s>>>(ctr);
   return cudaGetLastError();
 }
 

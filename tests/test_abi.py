@@ -71,6 +71,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.trilens_collide_step(None, 0, None, 0, None) == binding.ERR_INVALID
     assert lib.trilens_debug_eval64(None, None, -1, 0, None) == binding.ERR_INVALID
     assert lib.trilens_run(None, 0, 1, None) == binding.ERR_INVALID
+    assert lib.trilens_debug_set_parts(None, 2) == binding.ERR_INVALID
     for name in ("trilens_debug_set_cut_cap", "trilens_debug_set_key_bits"):
         assert getattr(lib, name)(None, 8) == binding.ERR_INVALID
     assert lib.trilens_debug_shrink_buffers(None, 64) == binding.ERR_INVALID
