@@ -6,7 +6,8 @@
 // time; each layer is one 128 x N x K tile product issued by one thread, its
 // FP32 result is read back row per thread (tcgen05.ld), biased, activated and
 // written as the next layer's BF16 operand.  Weight gradients (a reduction
-// over the batch) and the optimiser run on the CUDA cores.
+// over the batch) run on the tensor cores too, with the batch as the
+// reduction dimension (k_mlp_wgrad_tc); the optimiser on the CUDA cores.
 //
 // Outputs per row: mu and s (log variance) of a Gaussian over
 // y = log1p(sum of w_i w_j of a node pair).  Loss 0.5 (s + (y - mu)^2 e^-s),
@@ -369,55 +370,124 @@ __global__ void __launch_bounds__(128, 1)
 
 // ---------------------------------------------------------------- weight gradients
 
-// dW[o][i] += sum_r G[r][o] H[r][i] and db[o] += sum_r G[r][o] over a range of
-// rows, for one 32 x 32 output tile per block (grid.x: o tiles, grid.y: i
-// tiles, grid.z: row chunks).  G is BF16 [M][ldg] or FP32 dout [M][2]; H is the
-// normalised input features (layer 1) or GELU of a BF16 pre-activation.
-template <int HKIND>  // 0: features x (FP32 [M][24]); 1: GELU(Z) (BF16 [M][128])
-__global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16 *Gb, const float *Gf,
-                                                   int ldg, int O, const float *x,
-                                                   const __nv_bfloat16 *Z, const float *norm,
-                                                   int I, int64_t M, int64_t chunk, float *dW,
-                                                   float *db) {
-  __shared__ float sG[32][33];
-  __shared__ float sH[32][33];
-  const int o0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
-  const int64_t r0 = blockIdx.z * chunk, r1 = min(M, r0 + chunk);
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 rows of 32 threads
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  float bacc = 0.0f;
-  for (int64_t rb = r0; rb < r1; rb += 32) {
-    for (int q = ty; q < 32; q += 8) {
-      const int64_t r = rb + q;
-      const int o = o0 + tx, i = i0 + tx;
-      float g = 0.0f, h = 0.0f;
-      if (r < r1 && o < O) g = Gf ? Gf[r * 2 + o] : __bfloat162float(Gb[r * ldg + o]);
-      if (r < r1 && i < I) {
-        if (HKIND == 0) h = (x[r * kIn + i] - norm[i]) * norm[kIn + i];
-        else h = gelu(__bfloat162float(Z[r * kH + i]));
+// Weight gradients on the tensor cores: dW[o][i] = sum_r G[r][o] H[r][i] is a
+// 128 x N x K tile product with the batch rows as K.  A block reduces a range
+// of rows, 128 at a time: it stages A = G^T (one output per tile row) and
+// B = H^T (one input per tile row) as K-major core tiles, and one thread
+// issues the MMAs into an FP32 accumulator in tensor memory that stays there
+// for all of the block's rows; the block then adds its partial dW to the
+// gradient (FP32 atomics).  H is what the forward products consumed: the
+// BF16 normalised features (layer 1) or BF16 GELU(Z) (layers 2-4).  The bias
+// gradient db[o] = sum_r G[r][o] is summed from the staged tile.  Layer 4 has
+// 2 outputs, too few for a 128-row tile, so its product runs transposed:
+// A = GELU(Z3)^T (the 128 inputs as tile rows), B = dout^T (2 outputs padded
+// to 16), and the block writes dW4 transposed back.
+struct WgSmem {
+  __nv_bfloat16 A[128 * 128];
+  __nv_bfloat16 B[128 * 128];
+  uint64_t mbar;
+  uint32_t tmem;
+  int err;
+};
+
+// MODE 0: layer 1 (G = dZ1, H = features, N = 32); MODE 1: layers 2 and 3
+// (G = dZ, H = GELU(Z), N = 128); MODE 2: layer 4 (transposed, N = 16).
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+    k_mlp_wgrad_tc(const __nv_bfloat16 *G, const float *dout, const __nv_bfloat16 *Z,
+                   const float *x, const float *norm, int64_t M, int64_t chunk, float *dW,
+                   float *db, int *err, long long spin) {
+  constexpr int N = MODE == 0 ? kInP : (MODE == 1 ? kH : kOutP);
+  extern __shared__ unsigned char smem_raw[];
+  WgSmem &S = *align1k<WgSmem>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t r0 = blockIdx.x * chunk, r1 = min(M, r0 + chunk);
+  if (tid == 0) {
+    S.err = 0;
+    mbar_init(&S.mbar, 1);
+  }
+  if (warp == 0) {
+    tmem_alloc(&S.tmem, 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem;
+  uint32_t phase = 0;
+  bool ok = true;
+  float bacc = 0.0f;  // bias gradient of output tid (MODE 0, 1) or tid < 2 (MODE 2)
+  for (int64_t rb = r0; rb < r1; rb += 128) {
+    // thread tid stages batch row k = tid of this chunk: column k of both tiles
+    const int64_t row = rb + tid;
+    const bool valid = row < r1;
+    if (MODE == 2) {
+      // A[i][k] = GELU(Z3[row][i]), B[o][k] = dout[row][o] (o < 2)
+      for (int i = 0; i < kH; ++i)
+        S.A[core_idx(i, tid, 128)] =
+            __float2bfloat16(valid ? gelu(__bfloat162float(Z[row * kH + i])) : 0.0f);
+      for (int o = 0; o < kOutP; ++o)
+        S.B[core_idx(o, tid, 128)] = __float2bfloat16(valid && o < 2 ? dout[row * 2 + o] : 0.0f);
+    } else {
+      for (int o = 0; o < kH; ++o)
+        S.A[core_idx(o, tid, 128)] = valid ? G[row * kH + o] : __float2bfloat16(0.0f);
+      if (MODE == 0) {
+        for (int i = 0; i < kInP; ++i)
+          S.B[core_idx(i, tid, 128)] = __float2bfloat16(
+              valid && i < kIn ? (x[row * kIn + i] - norm[i]) * norm[kIn + i] : 0.0f);
+      } else {
+        for (int i = 0; i < kH; ++i)
+          S.B[core_idx(i, tid, 128)] =
+              __float2bfloat16(valid ? gelu(__bfloat162float(Z[row * kH + i])) : 0.0f);
       }
-      sG[q][tx] = g;
-      sH[q][tx] = h;
     }
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    // thread (ty, tx): outputs o = o0 + ty + 8 j, i = i0 + tx
-#pragma unroll 8
-    for (int q = 0; q < 32; ++q) {
-      const float h = sH[q][tx];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] += sG[q][ty + 8 * j] * h;
+    tc_fence_after();
+    if (tid == 0) {
+      gemm_tile(tmem, S.A, S.B, 128, N, rb > r0);
+      mma_commit(&S.mbar);
     }
-    if (blockIdx.y == 0 && ty == 0)
-      for (int q = 0; q < 32; ++q) bacc += sG[q][tx];
-    __syncthreads();
+    // the bias gradient from the staged G while the tensor cores work
+    if (MODE == 2) {
+      if (tid < 2)
+        for (int k = 0; k < 128; ++k) bacc += __bfloat162float(S.B[core_idx(tid, k, 128)]);
+    } else {
+      for (int k = 0; k < 128; ++k) bacc += __bfloat162float(S.A[core_idx(tid, k, 128)]);
+    }
+    ok = mbar_wait(&S.mbar, phase, spin) && ok;
+    phase ^= 1u;
+    tc_fence_after();
+    __syncthreads();  // the tiles are free again
   }
-  const int i = i0 + tx;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int o = o0 + ty + 8 * j;
-    if (o < O && i < I) atomicAdd(&dW[o * I + i], acc[j]);
+  // the block's partial dW: thread tid holds accumulator row tid (warp w: rows 32w..)
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  if (MODE == 2) {
+    uint32_t r[16];
+    TL_TMEM_LD_X16(trow, r);
+    tmem_wait_ld();
+    if (r1 > r0)
+      for (int o = 0; o < 2; ++o) atomicAdd(&dW[o * kH + tid], __uint_as_float(r[o]));
+    if (tid < 2 && r1 > r0) atomicAdd(&db[tid], bacc);
+  } else {
+    constexpr int I = MODE == 0 ? kIn : kH;
+#pragma unroll 1
+    for (int c = 0; c < N; c += 32) {
+      uint32_t r[32];
+      TL_TMEM_LD_X32(trow + (uint32_t)c, r);
+      tmem_wait_ld();
+      if (r1 > r0)
+        for (int j = 0; j < 32; ++j)
+          if (c + j < I) atomicAdd(&dW[tid * I + c + j], __uint_as_float(r[j]));
+    }
+    if (r1 > r0) atomicAdd(&db[tid], bacc);
   }
-  if (blockIdx.y == 0 && ty == 0 && o0 + tx < O) atomicAdd(&db[o0 + tx], bacc);
+  if (!ok) S.err = 1;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+  if (tid == 0 && S.err) atomicOr(err, 1);
 }
 
 // ---------------------------------------------------------------- optimiser
@@ -445,11 +515,21 @@ __global__ void k_adamw(float *prm, const float *grad, float *m, float *v, int n
 
 size_t mlp_fwd_smem() { return sizeof(FwdSmem) + 1024; }
 size_t mlp_bwd_smem() { return sizeof(BwdSmem) + 1024; }
+size_t mlp_wg_smem() { return sizeof(WgSmem) + 1024; }
 
 cudaError_t mlp_prepare() {
   cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)mlp_fwd_smem());
   if (e) return e;
+  if ((e = cudaFuncSetAttribute(k_mlp_wgrad_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mlp_wg_smem())))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_mlp_wgrad_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mlp_wg_smem())))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_mlp_wgrad_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)mlp_wg_smem())))
+    return e;
   return cudaFuncSetAttribute(k_mlp_dgrad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)mlp_bwd_smem());
 }
@@ -497,18 +577,19 @@ cudaError_t mlp_grad(const float *prm, const float *norm, const MLPWork &w, cons
                                                st, st_scale);
   k_mlp_dgrad<<<g, 128, mlp_bwd_smem(), s>>>(P, w.dout, w.Z[0], w.Z[1], w.Z[2], w.dZ[0], w.dZ[1],
                                              w.dZ[2], M, w.err, spin);
-  const int64_t chunk = 2048;
+  // weight gradients on the tensor cores: blocks of 512 batch rows
+  const int64_t chunk = 512;
   const unsigned gz = (unsigned)((M + chunk - 1) / chunk);
   float *G = w.grad;
-  // layer 4: G = dout (2 outputs), H = GELU(Z3)
-  k_mlp_wgrad<1><<<dim3(1, kH / 32, gz), 256, 0, s>>>(nullptr, w.dout, 2, 2, nullptr, w.Z[2],
-                                                      norm, kH, M, chunk, G + kOffW4, G + kOffB4);
-  k_mlp_wgrad<1><<<dim3(kH / 32, kH / 32, gz), 256, 0, s>>>(
-      w.dZ[2], nullptr, kH, kH, nullptr, w.Z[1], norm, kH, M, chunk, G + kOffW3, G + kOffB3);
-  k_mlp_wgrad<1><<<dim3(kH / 32, kH / 32, gz), 256, 0, s>>>(
-      w.dZ[1], nullptr, kH, kH, nullptr, w.Z[0], norm, kH, M, chunk, G + kOffW2, G + kOffB2);
-  k_mlp_wgrad<0><<<dim3(kH / 32, 1, gz), 256, 0, s>>>(w.dZ[0], nullptr, kH, kH, x, nullptr, norm,
-                                                     kIn, M, chunk, G + kOffW1, G + kOffB1);
+  const size_t sm = mlp_wg_smem();
+  k_mlp_wgrad_tc<2><<<gz, 128, sm, s>>>(nullptr, w.dout, w.Z[2], nullptr, norm, M, chunk,
+                                         G + kOffW4, G + kOffB4, w.err, spin);
+  k_mlp_wgrad_tc<1><<<gz, 128, sm, s>>>(w.dZ[2], nullptr, w.Z[1], nullptr, norm, M, chunk,
+                                         G + kOffW3, G + kOffB3, w.err, spin);
+  k_mlp_wgrad_tc<1><<<gz, 128, sm, s>>>(w.dZ[1], nullptr, w.Z[0], nullptr, norm, M, chunk,
+                                         G + kOffW2, G + kOffB2, w.err, spin);
+  k_mlp_wgrad_tc<0><<<gz, 128, sm, s>>>(w.dZ[0], nullptr, nullptr, x, norm, M, chunk,
+                                         G + kOffW1, G + kOffB1, w.err, spin);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,14 @@
 """The tensor-core surrogate network against the FP64 CPU reference
 (oracle/mlp.py): forward outputs, the loss and every parameter gradient,
-within BF16 tolerances."""
+element by element, within BF16 tolerances.
+
+The bounds come from the arithmetic: the operands of every product are BF16
+(8 significant bits, relative rounding 2^-9), the accumulators FP32.  A
+forward output carries a few roundings of 2^-9 per layer; a gradient element
+is a sum over the batch of products of a BF16 activation and a BF16 upstream
+gradient, each off by ~1% after four layers, so an element is within 5% of
+itself plus 1% of its tensor's largest element (the absolute part covers
+sums that cancel)."""
 import numpy as np
 import pytest
 
@@ -50,18 +58,44 @@ def test_normalisation_is_applied():
     assert np.allclose(a, b, atol=0.05 * np.abs(b).max())
 
 
-def test_gradients_match_fp64_reference():
-    m = 4096
+def _check_grads(gv, gref):
+    for k, _ in binding.MLP_ORDER:
+        a, r = gv[k].reshape(-1), gref[k].reshape(-1)
+        top = np.abs(r).max()
+        assert top > 0, k
+        err = np.abs(a - r)
+        bad = err > 0.05 * np.abs(r) + 0.01 * top
+        assert not bad.any(), (k, int(bad.sum()), float(err.max() / top))
+        rel = np.linalg.norm(a - r) / np.linalg.norm(r)
+        assert rel < 0.02, (k, rel)
+
+
+# 1 and 130 rows: one partial 128-row tile; 4096: eight full 512-row blocks;
+# 5077: a ragged last block and a ragged last tile
+@pytest.mark.parametrize("m", [1, 130, 4096, 5077])
+def test_gradients_match_fp64_reference(m):
     p, x, y, P, N, X, Y = _setup(m, 5)
     g, loss = binding.mlp_grad(P, N, X, Y)
     L, gref = mlp.loss_and_grads(p, x, y)
     assert abs(float(loss.item()) / m - L) <= 0.03 * abs(L) + 1e-3
-    gv = binding.mlp_unflatten(g.cpu().numpy().astype(np.float64))
-    for k, _ in binding.MLP_ORDER:
-        a, r = gv[k].reshape(-1), gref[k].reshape(-1)
-        rel = np.linalg.norm(a - r) / (np.linalg.norm(r) + 1e-12)
-        cos = float(a @ r) / (np.linalg.norm(a) * np.linalg.norm(r) + 1e-30)
-        assert rel < 0.08 and cos > 0.995, (k, rel, cos)
+    _check_grads(binding.mlp_unflatten(g.cpu().numpy().astype(np.float64)), gref)
+
+
+def test_gradients_add_over_batch_splits():
+    """The mean gradient of m rows is the row-weighted mean of the gradients
+    of two parts (split at 700, inside a block and inside a tile); only the
+    BF16 rounding of the 1/m-scaled upstream gradient and the FP32 summation
+    order differ."""
+    m, k = 3000, 700
+    p, x, y, P, N, X, Y = _setup(m, 7)
+    g = binding.mlp_grad(P, N, X, Y)[0].cpu().numpy().astype(np.float64)
+    g1 = binding.mlp_grad(P, N, X[:k].contiguous(), Y[:k].contiguous())[0].cpu().numpy()
+    g2 = binding.mlp_grad(P, N, X[k:].contiguous(), Y[k:].contiguous())[0].cpu().numpy()
+    s = (k * g1.astype(np.float64) + (m - k) * g2.astype(np.float64)) / m
+    gv, sv = binding.mlp_unflatten(g), binding.mlp_unflatten(s)
+    for name, _ in binding.MLP_ORDER:
+        a, r = gv[name].reshape(-1), sv[name].reshape(-1)
+        assert np.all(np.abs(a - r) <= 0.01 * np.abs(r) + 0.005 * np.abs(r).max()), name
 
 
 def test_surrogate_objective_gradients_match_fp64_reference():
@@ -79,9 +113,4 @@ def test_surrogate_objective_gradients_match_fp64_reference():
     L = mlp.loss_mean(out, lab, B)
     gref = mlp.backward(p, cache, mlp.loss_mean_grad(out, lab, B))
     assert abs(float(loss.item()) / m - L) <= 0.03 * abs(L) + 1e-3
-    gv = binding.mlp_unflatten(g.cpu().numpy().astype(np.float64))
-    for k, _ in binding.MLP_ORDER:
-        a, r = gv[k].reshape(-1), gref[k].reshape(-1)
-        rel = np.linalg.norm(a - r) / (np.linalg.norm(r) + 1e-12)
-        cos = float(a @ r) / (np.linalg.norm(a) * np.linalg.norm(r) + 1e-30)
-        assert rel < 0.08 and cos > 0.995, (k, rel, cos)
+    _check_grads(binding.mlp_unflatten(g.cpu().numpy().astype(np.float64)), gref)
