@@ -20,7 +20,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -246,12 +245,17 @@ DEP_BYTES_PER_HIT = (8 + 96 + 16 + 17) + (3 * 17 + 16 + 24 + 24 + 8) + 8
 
 
 def depletion_timing(col, stream, steps, peak, peak_src, host=None):
-    """Depletion in time order over a whole run (trilens_deplete_step after each
-    step's collision, unit weights, what is left carried from step to step):
-    device time of the depletion calls with CUDA events (the collisions are not
-    timed).  The run is done twice; the second is reported.  With host = (beam a,
-    beam b, dt, kappa) as numpy, the oracle then depletes the same hit lists on the
-    host cores (timed, and its pairs compared with the GPU's)."""
+    """Depletion in time order over a whole run (unit weights, what is left
+    carried from step to step).  The run's hit lists are made first (every step
+    built and collided, not timed) and stay on the device.  Then the depletion
+    of every step with hits is enqueued back to back (trilens_deplete_step_async,
+    one record per step, read after the run) between two CUDA events on the
+    launching stream: the device time of the run's depletion.  Beside it the
+    synchronous call (trilens_deplete_step) step by step, each between two
+    events: it waits for its result, so that sum holds a host round trip per
+    step.  Each is done three times; the last is reported.  With host = (beam a,
+    beam b, dt, kappa) as numpy, the oracle then depletes the same hit lists on
+    the host cores (timed, and its pairs compared with the GPU's)."""
     import torch
 
     from paper_1608_01125_gb300 import binding
@@ -259,51 +263,68 @@ def depletion_timing(col, stream, steps, peak, peak_src, host=None):
     na, nb = col.a["px"].numel(), col.b["px"].numel()
     cap = 1 << 21
     buf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
-    delta = torch.empty(cap, dtype=torch.float64, device=dev)
-    for rep in range(2):
+    lists = []
+    for k in steps:
+        col.build(k)
+        while True:
+            try:
+                n = col.collide(k, buf)
+                break
+            except binding.TrilensError as e:
+                if e.code != binding.ERR_CAPACITY:
+                    raise
+                cap = e.needed + 1024
+                buf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+        if n:
+            lists.append((k, buf[:n].clone(), n))
+    hits = sum(n for _, _, n in lists)
+    delta = torch.empty(max([n for _, _, n in lists] + [1]), dtype=torch.float64, device=dev)
+    out = torch.zeros((max(len(lists), 1), 4), dtype=torch.int64, device=dev)
+    for rep in range(3):
         ra = torch.ones(na, dtype=torch.float64, device=dev)
         rb = torch.ones(nb, dtype=torch.float64, device=dev)
-        ms = wall = made = 0.0
-        hits = acc = 0
-        rounds = []
-        lists = []
-        for k in steps:
-            col.build(k)
-            while True:
-                try:
-                    n = col.collide(k, buf)
-                    break
-                except binding.TrilensError as e:
-                    if e.code != binding.ERR_CAPACITY:
-                        raise
-                    cap = e.needed + 1024
-                    buf = torch.empty((cap, 2), dtype=torch.int32, device=dev)
-                    delta = torch.empty(cap, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for q, (k, h, n) in enumerate(lists):
+            col.deplete_step_async(k, h, n, ra, rb, delta, out[q])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    recs = binding.deplete_record(out)[: len(lists)]
+    assert all(r["status"] == 0 for r in recs), recs
+    used = int((ra == 0).sum().item())
+    acc = sum(r["accepted"] for r in recs)
+    made = sum(r["transferred"] for r in recs)
+    rounds = [r["rounds"] for r in recs]
+    for rep in range(3):
+        ra = torch.ones(na, dtype=torch.float64, device=dev)
+        rb = torch.ones(nb, dtype=torch.float64, device=dev)
+        sync_ms = wall = 0.0
+        sync_acc = 0
+        for k, h, n in lists:
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             t0 = time.perf_counter()
             e0.record(stream)
-            r = col.deplete_step(k, buf, n, ra, rb, delta)
+            r = col.deplete_step(k, h, n, ra, rb, delta)
             e1.record(stream)
             torch.cuda.synchronize()
             wall += 1e3 * (time.perf_counter() - t0)
-            ms += e0.elapsed_time(e1)
-            hits += n
-            acc += r["accepted"]
-            made += r["transferred"]
-            rounds.append(r["rounds"])
-            if rep == 1 and host is not None:
-                lists.append(buf[:n].cpu().numpy().view(np.uint32).copy())
-    used = int((ra == 0).sum().item())
+            sync_ms += e0.elapsed_time(e1)
+            sync_acc += r["accepted"]
+    assert sync_acc == acc
     cpu = None
     if host is not None:
         import oracle
         a_np, b_np, dt, kappa = host
         o_ra, o_rb = np.ones(na), np.ones(nb)
         o_made = 0
+        host_lists = [(k, h.cpu().numpy().view(np.uint32)) for k, h, _ in lists]
         t0 = time.perf_counter()
-        for k, h in zip(steps, lists):
+        for k, h in host_lists:
             t = oracle.hit_times(a_np, b_np, k, dt, kappa, h)
             d, o_ra, o_rb = oracle.deplete(k, t, h, o_ra, o_rb)
             o_made += int((d > 0).sum())
@@ -314,12 +335,13 @@ def depletion_timing(col, stream, steps, peak, peak_src, host=None):
                          "time-ordered sweep)"}
     achieved = DEP_BYTES_PER_HIT * hits / (ms / 1e3) / 1e9
     return {"time_steps": len(steps), "hits": hits, "pairs_made": acc, "transferred": made,
-            "photons_used_up_a": used, "ms_per_run": ms, "wall_ms_per_run": wall,
-            "hits_per_s": hits / (ms / 1e3), "rounds_max": max(rounds),
-            "rounds_per_step_with_hits": statistics.mean([x for x in rounds if x > 0] or [0]),
-            "steps_with_hits": sum(1 for x in rounds if x > 0),
-            # init, clear, two sums, and batches of 8 rounds of 3 kernels
-            "launches_per_run": sum(4 + 24 * math.ceil(x / 8) for x in rounds if x > 0),
+            "photons_used_up_a": used, "ms_per_run": ms, "hits_per_s": hits / (ms / 1e3),
+            "sync_ms_per_run": sync_ms, "sync_wall_ms_per_run": wall,
+            "rounds_max": max(rounds or [0]),
+            "rounds_per_step_with_hits": statistics.mean(rounds or [0]),
+            "steps_with_hits": len(lists),
+            # one cooperative launch (and a 16-byte memset) per step with hits
+            "launches_per_run": len(lists),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "bytes_per_hit": DEP_BYTES_PER_HIT},

@@ -185,11 +185,14 @@ int trilens_pair_products(const trilens_beam *a, const trilens_beam *b, const ui
  * the sum of delta, i.e. the pairs made (summed in a fixed order, so the
  * value is reproducible).
  *
- * Runs on the context's stream and returns when the step is done (the host
- * reads a counter after every 8 rounds of 3 kernels; a step needs as many
- * rounds as its longest chain of hits that wait on one another).  Allocates
- * its workspace on the first call (24 bytes per photon of both beams, 17 per
- * hit, growing with n_hits).  INVALID (nothing changed except delta, which
+ * Runs on the context's stream as one cooperative launch (every round inside
+ * it, the open hits compacted after each round; a step needs as many rounds
+ * as its longest chain of hits that wait on one another) and returns when the
+ * step is done, after one 48-byte read-back.  Allocates its workspace on the
+ * first call (96 bytes per photon of both beams, 25 per hit, growing with
+ * n_hits).  TIMEOUT (rem_a, rem_b and delta then unspecified; the photon
+ * slots are cleared on the device by the next call) if a grid-wide barrier
+ * wait inside the launch reaches the context's spin_limit.  INVALID (nothing changed except delta, which
  * may hold zeros) for a NULL context, a negative step, n_hits < 0 or >= 2^32,
  * NULL hits/rem arrays with n_hits > 0, an index out of range or a negative
  * or NaN rem of a listed photon.  A pair listed twice is not supported. */
@@ -197,9 +200,35 @@ int trilens_deplete_step(trilens_ctx *c, int64_t step, const uint32_t *hits, int
                          double *rem_a, double *rem_b, double *delta, int64_t *n_accepted,
                          double *transferred);
 
+/* Record of one asynchronous depletion call, written to device memory when the
+ * call completes on the context's stream. */
+typedef struct trilens_deplete_out {
+  double transferred; /* the sum of delta: the pairs made */
+  int64_t accepted;   /* hits with delta > 0 */
+  int64_t rounds;     /* rounds that had open hits */
+  int64_t status;     /* TRILENS_OK; TRILENS_ERR_INVALID (an index out of range or a
+                         negative or NaN rem: nothing changed except delta);
+                         TRILENS_ERR_TIMEOUT (a barrier wait reached spin_limit:
+                         rem_a, rem_b and delta unspecified); the other fields are 0
+                         unless the status is TRILENS_OK */
+} trilens_deplete_out;
+
+/* trilens_deplete_step without the wait: the call is enqueued on the context's
+ * stream and returns; what the synchronous call returns on the host (and its
+ * status) goes to `out` (device, caller-owned, 8-byte aligned, one record)
+ * when the call completes.  Calls for consecutive steps may be enqueued back
+ * to back, each with its own hit list, and `out` read once at the end.  A call
+ * whose status is not OK leaves the photon slots marked for clearing; the next
+ * call clears them first, on the device.  Same arguments and workspace as
+ * trilens_deplete_step; n_hits == 0 writes an all-zero record (status OK).
+ * INVALID (nothing enqueued) for the argument errors trilens_deplete_step
+ * reports before it launches, or an unaligned or NULL out. */
+int trilens_deplete_step_async(trilens_ctx *c, int64_t step, const uint32_t *hits,
+                               int64_t n_hits, double *rem_a, double *rem_b, double *delta,
+                               trilens_deplete_out *out);
+
 /* Rounds that had open hits in the last successful trilens_deplete_step call
- * (the longest chain of hits waiting on one another; the kernels run in
- * batches of 8 rounds). */
+ * (the longest chain of hits waiting on one another). */
 int trilens_deplete_rounds(trilens_ctx *c, int64_t *rounds);
 
 /* IP regime (Sec. 2.2): macro-photons (MPs) of integer weight w split into

@@ -173,6 +173,8 @@ def lib() -> ctypes.CDLL:
         L.trilens_deplete_step.argtypes = [vp, i64, vp, i64, vp, vp, vp, ctypes.POINTER(i64),
                                            ctypes.POINTER(dbl)]
         L.trilens_deplete_step.restype = ctypes.c_int
+        L.trilens_deplete_step_async.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp]
+        L.trilens_deplete_step_async.restype = ctypes.c_int
         L.trilens_deplete_rounds.argtypes = [vp, ctypes.POINTER(i64)]
         L.trilens_deplete_rounds.restype = ctypes.c_int
         L.trilens_swarm_mark.argtypes = [ctypes.POINTER(Beam), ctypes.POINTER(Beam), dbl, dbl,
@@ -449,6 +451,27 @@ class Collider:
         return {"accepted": int(acc.value), "transferred": float(tr.value),
                 "rounds": int(r.value) if n_hits else 0}
 
+    def deplete_step_async(self, step: int, hits, n_hits: int, rem_a, rem_b, delta, out):
+        """trilens_deplete_step_async: enqueue the depletion of step `step` on the
+        context's stream; its record goes to `out`, a CUDA int64 tensor of >= 4
+        entries (see deplete_record).  Same arguments as deplete_step."""
+        n_hits = int(n_hits)
+        if not (out.is_cuda and out.dtype == self._torch.int64 and out.is_contiguous()
+                and out.numel() >= 4):
+            raise TrilensError(ERR_INVALID, "out: need >= 4 contiguous int64 on the GPU")
+        na, nb = int(self.a["px"].numel()), int(self.b["px"].numel())
+        for name, t, n in (("rem_a", rem_a, na), ("rem_b", rem_b, nb)):
+            if not (t.is_cuda and t.dtype == self._torch.float64 and t.is_contiguous()
+                    and t.numel() == n):
+                raise TrilensError(ERR_INVALID, f"{name}: need {n} contiguous float64 on the GPU")
+        if n_hits > 0 and not (hits.is_cuda and hits.element_size() == 4 and hits.is_contiguous()
+                               and hits.numel() >= 2 * n_hits):
+            raise TrilensError(ERR_INVALID, "hits: need >= 2*n_hits contiguous 32-bit entries")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        _check(lib().trilens_deplete_step_async(self.ctx, int(step), ptr(hits) if n_hits else None,
+                                                n_hits, ptr(rem_a), ptr(rem_b), ptr(delta),
+                                                ptr(out)), self.ctx)
+
     def debug_set_parts(self, parts: int):
         _check(lib().trilens_debug_set_parts(self.ctx, int(parts)), self.ctx)
 
@@ -691,6 +714,16 @@ def mlp_forward(params, norm, x, stream=None):
     _check(lib().trilens_mlp_forward(_ptr(params), _ptr(norm), _ptr(x), x.shape[0], _ptr(out),
                                      ctypes.c_void_p(st.cuda_stream)))
     return out
+
+
+def deplete_record(out) -> dict:
+    """The record(s) trilens_deplete_step_async wrote: `out` an int64 tensor of
+    shape (4,) or (m, 4) -> dict (or list of dicts) with transferred, accepted,
+    rounds and status (0 = OK, else a TRILENS_ERR_* code)."""
+    a = np.ascontiguousarray(out.cpu().numpy().astype(np.int64).reshape(-1, 4))
+    recs = [{"transferred": float(r[:1].view(np.float64)[0]), "accepted": int(r[1]),
+             "rounds": int(r[2]), "status": int(r[3])} for r in a]
+    return recs[0] if out.dim() == 1 else recs
 
 
 def mlp_grad(params, norm, x, y, stream=None, kind=0, baseline=None, scale=1.0):

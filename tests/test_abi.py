@@ -88,6 +88,11 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.trilens_deplete_step(None, 0, None, 0, None, None, None, ctypes.byref(n),
                                     ctypes.byref(x)) == binding.ERR_INVALID
     assert lib.trilens_deplete_rounds(None, ctypes.byref(n)) == binding.ERR_INVALID
+    rec = (ctypes.c_int64 * 5)()
+    da = lib.trilens_deplete_step_async
+    assert da(None, 0, None, 0, None, None, None, None) == binding.ERR_INVALID
+    assert da(None, 0, None, 0, None, None, None, ctypes.addressof(rec)) == binding.ERR_INVALID
+    assert da(None, 0, None, 0, None, None, None, ctypes.addressof(rec) + 4) == binding.ERR_INVALID
     # swarm split (IP regime): bad beams, sizes or parameters never reach the device
     P = binding.Params(10.0, 1e16, 0, 0, 0, 0, 0)
     sm = lib.trilens_swarm_mark

@@ -200,3 +200,141 @@ def test_edges():
         r = col.deplete_step(0, hits, len(h), torch.zeros_like(ra), torch.zeros_like(rb), delta)
         assert r["accepted"] == 0 and r["transferred"] == 0.0 and r["rounds"] == 1
         assert (delta == 0).all()
+
+
+
+def test_dense_hit_list_many_rounds():
+    """2 x 4096 photons at kappa 5e16: ~330,000 hits, ~80 per photon, with real
+    weights U[0.5, 3], so hits wait on one another over many rounds and the
+    open hits are compacted again and again; bit for bit against the oracle."""
+    import torch
+    wl = synth.tiny_headon(n=4096, seed=31)
+    a, b = synth.beams(wl)
+    n = len(a["E"])
+    rng = np.random.default_rng(8)
+    w_a, w_b = rng.uniform(0.5, 3.0, n), rng.uniform(0.5, 3.0, n)
+    A, B = binding.to_device(a), binding.to_device(b)
+    ra, rb = torch.as_tensor(w_a, device="cuda"), torch.as_tensor(w_b, device="cuda")
+    with binding.Collider(A, B, wl.dt, 5e16) as col:
+        hits, h = step_hits_dev(col, 0)
+        delta = torch.empty(len(h), dtype=torch.float64, device="cuda")
+        r = col.deplete_step(0, hits, len(h), ra, rb, delta)
+    assert len(h) > 200_000
+    t = oracle.hit_times(a, b, 0, wl.dt, 5e16, h)
+    d_ref, ra_ref, rb_ref = oracle.deplete(0, t, h, w_a.copy(), w_b.copy())
+    assert r["rounds"] > 8
+    assert np.array_equal(delta.cpu().numpy(), d_ref)
+    assert np.array_equal(ra.cpu().numpy(), ra_ref)
+    assert np.array_equal(rb.cpu().numpy(), rb_ref)
+    assert r["accepted"] == int((d_ref > 0).sum())
+
+
+def test_barrier_wait_that_runs_out_returns_timeout():
+    """A depletion call is one cooperative launch whose phases meet at grid-wide
+    barriers with bounded waits.  With a spin limit of 1 the first blocks to
+    arrive give up: the call returns TIMEOUT, the kernel ends, and the next
+    call (normal limit, fresh weights) gives the oracle's answer."""
+    import torch
+    wl = synth.tiny_headon(n=4096, seed=32)
+    a, b = synth.beams(wl)
+    n = len(a["E"])
+    A, B = binding.to_device(a), binding.to_device(b)
+    with binding.Collider(A, B, wl.dt, 5e16) as col:
+        hits, h = step_hits_dev(col, 0)
+        delta = torch.empty(len(h), dtype=torch.float64, device="cuda")
+        ra = torch.ones(n, dtype=torch.float64, device="cuda")
+        rb = torch.ones(n, dtype=torch.float64, device="cuda")
+        col.debug_set_spin_limit(1)
+        with pytest.raises(binding.TrilensError) as e:
+            col.deplete_step(0, hits, len(h), ra, rb, delta)
+        assert e.value.code == binding.ERR_TIMEOUT
+        col.debug_set_spin_limit(1 << 22)
+        ra.fill_(1.0)
+        rb.fill_(1.0)
+        col.deplete_step(0, hits, len(h), ra, rb, delta)
+    t = oracle.hit_times(a, b, 0, wl.dt, 5e16, h)
+    d_ref, ra_ref, _ = oracle.deplete(0, t, h, np.ones(n), np.ones(n))
+    assert np.array_equal(delta.cpu().numpy(), d_ref)
+    assert np.array_equal(ra.cpu().numpy(), ra_ref)
+
+
+def test_async_calls_back_to_back_equal_the_oracle():
+    """trilens_deplete_step_async: the steps of a dense small run (unit weights)
+    enqueued back to back with no wait between them, each with its own hit list
+    and record, read once at the end: every record, delta and remainder equal to
+    the oracle's; a step with no hits writes an all-zero record."""
+    import torch
+    wl = synth.tiny_headon(n=4096, seed=33)
+    a, b = synth.beams(wl)
+    n = len(a["E"])
+    kappa = 2e16
+    A, B = binding.to_device(a), binding.to_device(b)
+    with binding.Collider(A, B, wl.dt, kappa) as col:
+        lists = [step_hits_dev(col, k) for k in range(3)]
+        lists.append((torch.zeros((0, 2), dtype=torch.int32, device="cuda"),
+                      np.zeros((0, 2), np.uint32)))
+        ra = torch.ones(n, dtype=torch.float64, device="cuda")
+        rb = torch.ones(n, dtype=torch.float64, device="cuda")
+        out = torch.full((len(lists), 4), -7, dtype=torch.int64, device="cuda")
+        deltas = [torch.empty(max(len(h), 1), dtype=torch.float64, device="cuda")
+                  for _, h in lists]
+        for k, ((hits, h), d) in enumerate(zip(lists, deltas)):
+            col.deplete_step_async(k, hits, len(h), ra, rb, d, out[k])
+        torch.cuda.synchronize()
+        recs = binding.deplete_record(out)
+    o_ra, o_rb = np.ones(n), np.ones(n)
+    for k, ((_, h), d, rec) in enumerate(zip(lists, deltas, recs)):
+        assert rec["status"] == 0
+        if len(h) == 0:
+            assert rec == {"transferred": 0.0, "accepted": 0, "rounds": 0, "status": 0}
+            continue
+        t = oracle.hit_times(a, b, k, wl.dt, kappa, h)
+        d_ref, o_ra, o_rb = oracle.deplete(k, t, h, o_ra, o_rb)
+        assert np.array_equal(d[: len(h)].cpu().numpy(), d_ref)
+        assert rec["accepted"] == int((d_ref > 0).sum())
+        assert rec["transferred"] == float(d_ref.sum())
+        assert rec["rounds"] >= 1
+    assert np.array_equal(ra.cpu().numpy(), o_ra)
+    assert np.array_equal(rb.cpu().numpy(), o_rb)
+
+
+def test_async_failures_are_recorded_and_cleared_on_the_device():
+    """Async calls report failures in their record, not on the host: a bad
+    index gives status INVALID (weights untouched), a barrier wait that runs
+    out gives TIMEOUT; the next call, enqueued behind them with no host check,
+    clears the photon slots on the device first and equals the oracle."""
+    import torch
+    wl = synth.tiny_headon(n=4096, seed=34)
+    a, b = synth.beams(wl)
+    n = len(a["E"])
+    A, B = binding.to_device(a), binding.to_device(b)
+    with binding.Collider(A, B, wl.dt, 5e16) as col:
+        hits, h = step_hits_dev(col, 0)
+        delta = torch.empty(len(h), dtype=torch.float64, device="cuda")
+        out = torch.zeros((3, 4), dtype=torch.int64, device="cuda")
+        ra = torch.ones(n, dtype=torch.float64, device="cuda")
+        rb = torch.ones(n, dtype=torch.float64, device="cuda")
+        bad = hits.clone()
+        bad[len(h) // 2, 1] = n
+        col.deplete_step_async(0, bad, len(h), ra, rb, delta, out[0])
+        torch.cuda.synchronize()
+        assert (ra == 1).all() and (rb == 1).all()
+        col.debug_set_spin_limit(1)
+        col.deplete_step_async(0, hits, len(h), ra, rb, delta, out[1])
+        col.debug_set_spin_limit(1 << 22)
+        ra2 = torch.ones(n, dtype=torch.float64, device="cuda")
+        rb2 = torch.ones(n, dtype=torch.float64, device="cuda")
+        col.deplete_step_async(0, hits, len(h), ra2, rb2, delta, out[2])
+        torch.cuda.synchronize()
+        recs = binding.deplete_record(out)
+        with pytest.raises(binding.TrilensError):
+            col.deplete_step_async(0, hits, len(h), ra, rb, delta, out[0, :3])
+    assert recs[0]["status"] == binding.ERR_INVALID
+    assert recs[1]["status"] == binding.ERR_TIMEOUT
+    assert recs[2]["status"] == 0
+    t = oracle.hit_times(a, b, 0, wl.dt, 5e16, h)
+    d_ref, ra_ref, rb_ref = oracle.deplete(0, t, h, np.ones(n), np.ones(n))
+    assert np.array_equal(delta.cpu().numpy(), d_ref)
+    assert np.array_equal(ra2.cpu().numpy(), ra_ref)
+    assert np.array_equal(rb2.cpu().numpy(), rb_ref)
+    assert recs[2]["accepted"] == int((d_ref > 0).sum())
