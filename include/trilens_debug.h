@@ -89,7 +89,8 @@ int trilens_debug_phase_ms(trilens_ctx *c, double *out, int64_t *launches, int r
  *   4    closest-approach time t* = +-2^-e dt (the window's start)
  *   5    t* = dt (1 +- 2^-e) (the window's end)
  *   6    invariant s = 1 +- 2^-e (the threshold), e in 1..52
- *   7    d^2 uniform in [0, 4 r_max^2), t* in [-0.1 dt, 1.1 dt) (quick miss)
+ *   7    d^2 uniform in [0, 4 r_max^2), t* in [-0.1 dt, 1.1 dt) (the quick
+ *        miss's margin 2.5 r^2, with r^2 bounded over the pair's bin of s)
  * with a random time step 0..63, beam axes at a random angle, 5 mrad spread,
  * and the meeting point anywhere within +-100 um.  counts (device,
  * TRILENS_STRESS_CATEGORIES x TRILENS_STRESS_FIELDS uint64, accumulated: zero

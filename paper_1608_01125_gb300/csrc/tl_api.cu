@@ -16,7 +16,8 @@
 
 namespace tl {
 cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t sb, int nonempty,
-                             const unsigned *build_status, cudaStream_t s);
+                             const unsigned *build_status, const unsigned *run_status,
+                             cudaStream_t s);
 cudaError_t launch_expand(const TravArgs &a, uint2 *F0, uint2 *F1, unsigned cap, unsigned target,
                           int max_levels, cudaStream_t s);
 cudaError_t launch_seed_cut(const TravArgs &a, const uint32_t *cutA, const unsigned *cntA,
@@ -128,15 +129,18 @@ static double host_sigma(double s) {
   return 0.5 * TL_PI * TL_RE * TL_RE / s * ((3.0 - b * b * b * b) * lg - 2.0 * b * (2.0 - b * b));
 }
 
-static double host_sigma_max() {
+// s where Eq. BWcross peaks (golden-section search; sigma is unimodal)
+static double host_sigma_peak_s() {
   double lo = 1.2, hi = 4.0, g = 0.5 * (sqrt(5.0) - 1.0);
   for (int it = 0; it < 200; ++it) {
     double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
     if (host_sigma(x1) < host_sigma(x2)) lo = x1;
     else hi = x2;
   }
-  return host_sigma(0.5 * (lo + hi));
+  return 0.5 * (lo + hi);
 }
+
+static double host_sigma_max() { return host_sigma(host_sigma_peak_s()); }
 
 // an upper bound of Eq. BWcross over s (for conservative tests elsewhere)
 double tl_sigma_max_bound() { return host_sigma_max() * (1.0 + 1e-6); }
@@ -164,6 +168,21 @@ TLNarrowConst tl_narrow_const(double dt_fs, double kappa) {
   nk.kr = (float)(1e12 * kappa / TL_PI);
   nk.inv2mc4 = (float)(1.0 / (2.0 * TL_MEC2 * TL_MEC2));
   nk.pref = (float)(0.5 * TL_PI * TL_RE * TL_RE);
+  // sure-miss radius per bin of s: sigma's largest value over the bin (at the
+  // end nearer the peak, or the peak itself), with a relative margin
+  const double s_peak = host_sigma_peak_s();
+  nk.sbin[0] = 0.0f;
+  for (int i = 1; i < TL_SBINS; ++i) {
+    const int e = (i - 1) / TL_SBIN_OCT, k = (i - 1) % TL_SBIN_OCT;
+    const double a = ldexp(1.0 + (double)k / TL_SBIN_OCT, e);
+    const double b = ldexp(1.0 + (double)(k + 1) / TL_SBIN_OCT, e);
+    double sig;
+    if (i == TL_SBINS - 1) sig = host_sigma(a);  // [a, inf): sigma falls beyond the peak
+    else if (b <= s_peak) sig = host_sigma(b);
+    else if (a >= s_peak) sig = host_sigma(a);
+    else sig = sigma_max;
+    nk.sbin[i] = round_up(1e12 * kappa * std::min(sig * (1.0 + 1e-5), sigma_max) / TL_PI);
+  }
   return nk;
 }
 
@@ -507,6 +526,30 @@ int trilens_build(trilens_ctx *c, int64_t step) {
 
 }  // extern "C"
 
+// A step's (or a captured run's) failure from its traversal and build status
+// words, or TRILENS_OK.  After a wait that expired or an invalid hierarchy the
+// sort's status words are cleared before the next sort, the queue is reset to
+// the sentinel (a traversal cut short may leave items in it) and the build
+// status is cleared.
+static int status_failure(trilens_ctx *c, unsigned trav_st, unsigned build_st) {
+  if (!((trav_st | build_st) & (TL_ST_TIMEOUT | TL_ST_BADTREE))) return TRILENS_OK;
+  c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
+  CK(cudaMemsetAsync(c->queue, 0xff, sizeof(uint2) * (size_t)c->queue_cap, c->stream));
+  CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (build_st & TL_ST_TIMEOUT)
+    return fail(c, TRILENS_ERR_TIMEOUT,
+                "a device wait reached spin_limit=%lld (the radix sort's look-back)",
+                (long long)c->p.spin_limit);
+  if (trav_st & TL_ST_TIMEOUT)
+    return fail(c, TRILENS_ERR_TIMEOUT,
+                "a device wait reached spin_limit=%lld (a traversal warp waiting for work)",
+                (long long)c->p.spin_limit);
+  return fail(c, TRILENS_ERR_CUDA,
+              "the refit met a node reference out of range: the step's hierarchy is invalid "
+              "(internal error)");
+}
+
 tl::TravArgs trav_args(trilens_ctx *c, double ct) {
   tl::TravArgs a;
   memset(&a, 0, sizeof(a));
@@ -555,7 +598,7 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
     tmark(c, PH_EXPAND, 0, 0);
     CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super,
                             (c->n_inst > 1 || seeds || use_cut) ? 0 : nonempty, c->build_status,
-                            c->stream));
+                            nullptr, c->stream));
     if (use_cut) {
       CK(tl::launch_seed_cut(a, c->w[0].cut, c->w[0].cut_n, c->w[0].cut_cap, c->w[1].cut,
                              c->w[1].cut_n, c->w[1].cut_cap, c->front[0], c->front_cap,
@@ -606,15 +649,7 @@ int run_exact(trilens_ctx *c, double ct, const uint2 *seeds, unsigned n_seeds, i
     CK(cudaStreamSynchronize(c->stream));
     tcollect(c);
     const unsigned st = h.status | *c->build_status_host;
-    if (st & TL_ST_TIMEOUT) {
-      c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
-      // a traversal cut short may leave items in the queue
-      CK(cudaMemsetAsync(c->queue, 0xff, sizeof(uint2) * (size_t)c->queue_cap, c->stream));
-      CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
-      CK(cudaStreamSynchronize(c->stream));
-      return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit=%lld",
-                  (long long)c->p.spin_limit);
-    }
+    if (int rf = status_failure(c, h.status, *c->build_status_host)) return rf;
     bool again = false;
     int rc;
     if (st & TL_ST_BAND_OVF) {
@@ -812,7 +847,8 @@ static int graph_collide(trilens_ctx *c, int64_t step, double *yields) {
   tl::TravArgs a = trav_args(c, ct);
   const bool use_cut = c->n_inst <= 1 && c->w[0].cut_S && c->w[1].cut_S;
   CK(tl::launch_step_init(c->ctr, c->front[0], a.A.super, a.B.super,
-                          (c->n_inst > 1 || use_cut) ? 0 : nonempty, c->build_status, c->stream));
+                          (c->n_inst > 1 || use_cut) ? 0 : nonempty, c->build_status,
+                          c->run_status, c->stream));
   if (use_cut) {
     CK(tl::launch_seed_cut(a, c->w[0].cut, c->w[0].cut_n, c->w[0].cut_cap, c->w[1].cut,
                            c->w[1].cut_n, c->w[1].cut_cap, c->front[0], c->front_cap,
@@ -892,14 +928,7 @@ static int replay_run(trilens_ctx *c, int64_t first_step, int64_t steps, double 
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     const unsigned st = *c->run_status_host | *c->build_status_host;
-    if (st & TL_ST_TIMEOUT) {
-      c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
-      // a traversal cut short may leave items in the queue
-      CK(cudaMemsetAsync(c->queue, 0xff, sizeof(uint2) * (size_t)c->queue_cap, c->stream));
-      CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
-      CK(cudaStreamSynchronize(c->stream));
-      return fail(c, TRILENS_ERR_TIMEOUT, "a device wait reached spin_limit");
-    }
+    if (int rf = status_failure(c, *c->run_status_host, *c->build_status_host)) return rf;
     if (!(st & (TL_ST_HIT_OVF | TL_ST_BAND_OVF | TL_ST_SPILL_OVF | TL_ST_FRONT_OVF |
                 TL_ST_PRIV_OVF | TL_ST_LEAFQ)))
       return TRILENS_OK;

@@ -599,7 +599,7 @@ __global__ void __launch_bounds__(kRTile) k_refit_tile(
     seg_axis(ps.y, d.y, Llo, Lhi, half, b.v[1], b.v[4]);
     seg_axis(ps.z, d.z, Llo, Lhi, half, b.v[2], b.v[5]);
     if ((lref >> 1) <= super) write_slot(nodes, lref >> 1, lref & 1u, to_box(b));
-    else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+    else atomicOr(build_status, (unsigned)TL_ST_BADTREE);
   }
 #pragma unroll
   for (int q = 0; q < 6; ++q) tab[q * kRTile + t] = b.v[q];
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(kRTile) k_refit_tile(
     if ((nref >> 1) <= super && f <= l)
       write_slot(nodes, nref >> 1, nref & 1u,
                  to_box(tab_query<kRTile, kRTileLev>(tab, (int)(f - base), (int)(l - base))));
-    else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+    else atomicOr(build_status, (unsigned)TL_ST_BADTREE);
   }
 }
 
@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(256) k_refit_cross(int64_t n, TLNode *nodes,
     const int64_t t0 = f >> 8, t1 = l >> 8;
     if (t0 == t1) continue;  // finished by its tile
     if (f < 0 || l >= n || f > l) {
-      atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+      atomicOr(build_status, (unsigned)TL_ST_BADTREE);
       continue;
     }
     if (cut_S && l - f + 1 > (int64_t)cut_S) {
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(256) k_refit_cross(int64_t n, TLNode *nodes,
     if (t1 - t0 >= 2) join6(b, tiles_union(stab, t0 + 1, t1 - 1));
     const uint32_t ref = parent_node[x];
     if ((ref >> 1) <= super) write_slot(nodes, ref >> 1, ref & 1u, to_box(b));
-    else atomicOr(build_status, (unsigned)TL_ST_TIMEOUT);
+    else atomicOr(build_status, (unsigned)TL_ST_BADTREE);
   }
 }
 

@@ -68,7 +68,8 @@ enum {
   TL_ST_FRONT_OVF = 8,
   TL_ST_TIMEOUT = 16,
   TL_ST_LEAFQ = 32,    // the leaf-pair list overflowed
-  TL_ST_PRIV_OVF = 64  // a traversal warp's private spill area overflowed
+  TL_ST_PRIV_OVF = 64,  // a traversal warp's private spill area overflowed
+  TL_ST_BADTREE = 128   // the refit met a node reference out of range (an internal error)
 };
 
 // Per-step device counters; zeroed by the step's init kernel.
@@ -125,6 +126,21 @@ struct TLTree {
 };
 
 // Conservative constants of the FP32 narrow phase (see tl_narrow.cuh).
+// Bins of the invariant s for the narrow phase's sure-miss radius: bin 0
+// holds s < 1 (below threshold); bin 1 + 8 e + k holds s in
+// [2^e (1 + k/8), 2^e (1 + (k+1)/8)) for e = 0..23; the last bin also holds
+// every larger s.  A bin's index is read off the FP32 bits of s exactly.
+constexpr int TL_SBIN_OCT = 8;
+constexpr int TL_SBIN_EMAX = 24;
+constexpr int TL_SBINS = 1 + TL_SBIN_OCT * TL_SBIN_EMAX;
+
+__device__ __forceinline__ int tl_sbin(float s) {
+  if (s < 1.0f) return 0;
+  const unsigned b = __float_as_uint(s);
+  const int i = 1 + ((int)(b >> 23) - 127) * TL_SBIN_OCT + (int)((b >> 20) & 7u);
+  return i < TL_SBINS - 1 ? i : TL_SBINS - 1;
+}
+
 struct TLNarrowConst {
   float L;        // c dt [um], rounded to nearest
   float L_in;     // L (1 - 8u): t* surely inside when tau + err < L_in
@@ -133,6 +149,9 @@ struct TLNarrowConst {
   float kr;       // 1e12 kappa / pi in FP32
   float inv2mc4;  // 1 / (2 m_e^2 c^4) [MeV^-2]
   float pref;     // (pi/2) r_e^2 [m^2]
+  // per bin of s (tl_sbin): an upper bound on r^2 = 1e12 kappa sigma(s) / pi
+  // over the bin [um^2] (sigma rises up to its peak near s = 1.97, then falls)
+  float sbin[TL_SBINS];
 };
 
 // Build-time launch helpers (defined in the .cu files).

@@ -33,13 +33,15 @@ enum { TL_MISS = 0, TL_HIT = 1, TL_BAND = 2 };
 struct TLNarrowPre {
   float s, es;
   bool above;
-  float dd, rdd, tau, d2, SA;
+  float dd, rdd, tau, d2, SA, r2ub;
   int early;
 };
 
+// sbin: the table k.sbin (a copy in shared memory: its lookups diverge)
 __device__ __forceinline__ TLNarrowPre tl_narrow32_pre(const float4 pa, const float4 da,
                                                        const float4 pb, const float4 db,
-                                                       const TLNarrowConst &k) {
+                                                       const TLNarrowConst &k,
+                                                       const float *sbin) {
   const float u = 5.9604644775390625e-8f;  // 2^-24
   TLNarrowPre r;
   r.early = -1;
@@ -71,12 +73,20 @@ __device__ __forceinline__ TLNarrowPre tl_narrow32_pre(const float4 pa, const fl
   r.d2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
 
   r.SA = (fabsf(pa.x) + fabsf(pb.x)) + (fabsf(pa.y) + fabsf(pb.y)) + (fabsf(pa.z) + fabsf(pb.z));
-  // Quick miss, before the bounds: if |dD|^2 >= 2^-30, |tau| <= 2^10,
-  // |q|^2 >= 2^-12 and SA <= 2^18 |q|, every term of dq below is a small
-  // fraction of |q| (2u SA <= |q|/32, 4u |q|/|dD| <= |q|/128, 4u |tau| <=
-  // |q|/64, 7.1u |tau||dD| <= |q|/18), so dq <= 0.23 |q| and ed2 <= 0.5 d2:
-  // d2 >= 2.5 r2max then puts the FP64 distance beyond every radius.
-  if (r.dd >= 0x1p-30f && fabsf(r.tau) <= 1024.0f && r.d2 >= fmaxf(2.5f * k.r2max, 0x1p-12f) &&
+  // The largest radius^2 of any s the FP64 invariant can take: s64 lies in
+  // [s - es, s + es], which meets at most two adjacent bins of s when es is
+  // small (else every s counts).
+  const int b0 = tl_sbin(__fsub_rd(r.s, r.es)), b1 = tl_sbin(__fadd_ru(r.s, r.es));
+  r.r2ub = b1 - b0 <= 1 ? fmaxf(sbin[b0], sbin[b1]) : k.r2max;
+  // Quick miss, before the bounds: if |dD|^2 >= 2^-30, SA <= 2^18 |q| and
+  // either |tau| <= 2^10 and |q|^2 >= 2^-12, or |tau| <= 4 and |q|^2 >= 2^-26,
+  // every term of dq below is a small fraction of |q| (2u SA <= |q|/32,
+  // 4u |q|/|dD| <= |q|/128, 4u |tau| <= |q|/64, 7.1u |tau||dD| <= |q|/18), so
+  // dq <= 0.23 |q| and ed2 <= 0.5 d2: d2 >= 2.5 r2ub then puts the FP64
+  // distance beyond the radius of every s the pair can have.
+  const float at = fabsf(r.tau);
+  const float floor2 = at <= 4.0f ? 0x1p-26f : 0x1p-12f;
+  if (r.dd >= 0x1p-30f && at <= 1024.0f && r.d2 >= fmaxf(2.5f * r.r2ub, floor2) &&
       r.SA * r.SA <= 0x1p36f * r.d2)
     r.early = TL_MISS;
   return r;
@@ -86,14 +96,16 @@ __device__ __forceinline__ TLNarrowPre tl_narrow32_pre(const float4 pa, const fl
 // tl_narrow32 returns TL_MISS before its error bounds)
 __device__ __forceinline__ bool tl_narrow32_quick_miss(const float4 pa, const float4 da,
                                                        const float4 pb, const float4 db,
-                                                       const TLNarrowConst &k) {
-  return tl_narrow32_pre(pa, da, pb, db, k).early == TL_MISS;
+                                                       const TLNarrowConst &k,
+                                                       const float *sbin) {
+  return tl_narrow32_pre(pa, da, pb, db, k, sbin).early == TL_MISS;
 }
 
 __device__ __forceinline__ int tl_narrow32(const float4 pa, const float4 da, const float4 pb,
-                                           const float4 db, const TLNarrowConst &k) {
+                                           const float4 db, const TLNarrowConst &k,
+                                           const float *sbin) {
   const float u = 5.9604644775390625e-8f;  // 2^-24
-  const TLNarrowPre pre = tl_narrow32_pre(pa, da, pb, db, k);
+  const TLNarrowPre pre = tl_narrow32_pre(pa, da, pb, db, k, sbin);
   if (pre.early >= 0) return pre.early;
   const float s = pre.s, es = pre.es, dd = pre.dd, rdd = pre.rdd, tau = pre.tau, d2 = pre.d2;
   const float SA = pre.SA;
@@ -113,8 +125,8 @@ __device__ __forceinline__ int tl_narrow32(const float4 pa, const float4 da, con
   // window 0 <= t* < dt (half open)
   if (tau + et < 0.0f || tau - et >= k.L_out) return TL_MISS;
   const bool win_in = (tau - et > 0.0f) && (tau + et < k.L_in);
-  // farther than the largest radius of any s
-  if (d2 - ed2 >= k.r2max) return TL_MISS;
+  // farther than the largest radius of any s the pair can have
+  if (d2 - ed2 >= pre.r2ub) return TL_MISS;
   if (!above) return TL_BAND;  // too close to threshold for the FP32 sigma
 
   // --- sigma(s) (Eq. BWcross) in FP32 with its bound -------------------------

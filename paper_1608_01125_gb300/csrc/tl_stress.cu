@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(kThreads) k_band_stress(unsigned long long bas
                                                           unsigned long long *counts,
                                                           double *sample, int64_t n_sample) {
   __shared__ unsigned long long sc[kCats * kFields];
+  __shared__ float sbin[TL_SBINS];
   for (int t = threadIdx.x; t < kCats * kFields; t += kThreads) sc[t] = 0ull;
+  for (int t = threadIdx.x; t < TL_SBINS; t += kThreads) sbin[t] = nk.sbin[t];
   __syncthreads();
   const double two_m2 = (2.0 * TL_MEC2) * TL_MEC2;
   for (int64_t q = q0 + blockIdx.x * (int64_t)kThreads + threadIdx.x; q < q0 + n;
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(kThreads) k_band_stress(unsigned long long bas
     else t = g.u() * dt;
     double d2;
     if (cat < 4) d2 = r2 * (1.0 + g.tiny(1, 50));
-    else if (cat == 7) d2 = 4.0 * g.u() * (double)nk.r2max;
+    else if (cat == 7) d2 = 4.0 * g.u() * (double)nk.r2max;  // spans 2.5 r^2 bound of every s
     else d2 = 0.9 * g.u() * r2;
     // meeting point M anywhere within +-100 um; offset q perpendicular to the
     // relative velocity, so that the two photons are closest at t
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_band_stress(unsigned long long bas
                                   __double2float_rn(dzi), 0.0f);
     const float4 db = make_float4(__double2float_rn(dxj), __double2float_rn(dyj),
                                   __double2float_rn(dzj), 0.0f);
-    const int r32 = tl_narrow32(pa, da, pb, db, nk);
+    const int r32 = tl_narrow32(pa, da, pb, db, nk, sbin);
     unsigned long long *c = sc + cat * kFields;
     atomicAdd(c + 0, 1ull);
     if (hit) atomicAdd(c + 1, 1ull);

@@ -230,11 +230,14 @@ static int sur_cut(trilens_ctx *c, int L, unsigned *ncut) {
     CK(cudaMemcpyAsync(c->build_status_host, c->build_status, sizeof(unsigned),
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (*c->build_status_host & TL_ST_TIMEOUT) {  // the hierarchy of this step is invalid
+    const unsigned bst = *c->build_status_host;
+    if (bst & (TL_ST_TIMEOUT | TL_ST_BADTREE)) {  // the hierarchy of this step is invalid
       c->w[0].sort_epoch = c->w[1].sort_epoch = 0;
       CK(cudaMemsetAsync(c->build_status, 0, sizeof(unsigned), c->stream));
       CK(cudaStreamSynchronize(c->stream));
-      return fail(c, TRILENS_ERR_TIMEOUT, "a device wait of the build reached spin_limit");
+      if (bst & TL_ST_TIMEOUT)
+        return fail(c, TRILENS_ERR_TIMEOUT, "a device wait of the build reached spin_limit");
+      return fail(c, TRILENS_ERR_CUDA, "the refit met a node reference out of range (internal error)");
     }
     if (left > 0) return fail(c, TRILENS_ERR_STACK, "cut traversal did not finish");
     if (!(st & TL_ST_FRONT_OVF)) {

@@ -150,17 +150,23 @@ __device__ __forceinline__ void emit(bool pred, uint32_t x, uint32_t y, uint2 *b
 
 // ------------------------------------------------------------ init
 
+// run_status (captured runs, else NULL): a queue overflow or an expired wait
+// in an earlier step of the run carries over, so that no later step runs on
+// a queue that may still hold chunks nobody takes (the host repeats the run)
 __global__ void k_step_init(TLCounters *ctr, uint2 *F0, uint32_t superA, uint32_t superB,
-                            int nonempty, const unsigned *build_status) {
+                            int nonempty, const unsigned *build_status,
+                            const unsigned *run_status) {
   unsigned *w = reinterpret_cast<unsigned *>(ctr);
   for (int i = threadIdx.x; i < (int)(sizeof(TLCounters) / 4); i += blockDim.x) w[i] = 0u;
   if (threadIdx.x == 0) F0[0] = make_uint2(superA, superB);
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned bs = *build_status & (unsigned)TL_ST_TIMEOUT;
-    ctr->status = bs;
+    const unsigned rs =
+        run_status ? *run_status & (unsigned)(TL_ST_SPILL_OVF | TL_ST_TIMEOUT) : 0u;
+    ctr->status = bs | rs;
     // after a failed build there is nothing valid to traverse
-    ctr->counts[0] = (nonempty && !bs) ? 1u : 0u;
+    ctr->counts[0] = (nonempty && !bs && !rs) ? 1u : 0u;
   }
 }
 
@@ -169,7 +175,7 @@ __global__ void k_step_init(TLCounters *ctr, uint2 *F0, uint32_t superA, uint32_
 __global__ void k_seed_instances(TLCounters *ctr, uint2 *F0, const uint32_t *rootA,
                                  const uint32_t *rootB, int n_inst) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n_inst || (ctr->status & TL_ST_TIMEOUT)) return;
+  if (q >= n_inst || (ctr->status & (TL_ST_TIMEOUT | TL_ST_SPILL_OVF))) return;
   const uint32_t ra = rootA[q], rb = rootB[q];
   if (ra == TL_NONE || rb == TL_NONE) return;
   const unsigned idx = atomicAdd(&ctr->counts[0], 1u);
@@ -188,7 +194,8 @@ __global__ void __launch_bounds__(256) k_seed_cut(TravArgs a, const uint32_t *cu
                                                   const uint32_t *cutB, const unsigned *cntB,
                                                   uint32_t capB, uint2 *F0, unsigned cap) {
   TLCounters *ctr = a.ctr;
-  if (ctr->status & TL_ST_TIMEOUT) return;  // the build failed: nothing to traverse
+  // the build failed, or the queue overflowed earlier in a captured run: nothing to traverse
+  if (ctr->status & (TL_ST_TIMEOUT | TL_ST_SPILL_OVF)) return;
   const unsigned na = *cntA, nb = *cntB;
   if (na > capA || nb > capB) {  // a list overflowed: start from the root pair
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -311,7 +318,8 @@ __global__ void __launch_bounds__(1024) k_expand(TravArgs a, uint2 *F0, uint2 *F
 __global__ void __launch_bounds__(256) k_widen(TravArgs a, uint2 *F0, uint2 *F1, unsigned cap,
                                                unsigned target, int level) {
   TLCounters *ctr = a.ctr;
-  if (ctr->status & TL_ST_TIMEOUT) return;  // the build failed: nothing to traverse
+  // the build failed, or the queue overflowed earlier in a captured run: nothing to traverse
+  if (ctr->status & (TL_ST_TIMEOUT | TL_ST_SPILL_OVF)) return;
   if ((int)ctr->final_level != level || level + 1 >= 32) return;
   const unsigned nin = ctr->counts[level];
   if (nin == 0u || nin >= target || 4ull * nin > (unsigned long long)cap) return;
@@ -376,7 +384,7 @@ struct WarpSmem {
 // ws.pend[0 .. cnt)), one per lane; hits and band pairs leave with one
 // atomic per warp each.
 __device__ __forceinline__ void decide_pending(const TravArgs &a, const WarpSmem &ws, int cnt,
-                                               int lane) {
+                                               int lane, const float *sbin) {
   int outcome = TL_MISS;
   uint32_t oi = 0u, oj = 0u;
   if (lane < cnt) {
@@ -385,7 +393,7 @@ __device__ __forceinline__ void decide_pending(const TravArgs &a, const WarpSmem
     const float4 pa = __ldg(a.A.pos + pr.x), pb = __ldg(a.B.pos + pr.y);
     oi = __float_as_uint(da.w);
     oj = __float_as_uint(db.w);
-    outcome = tl_narrow32(pa, da, pb, db, a.nk);
+    outcome = tl_narrow32(pa, da, pb, db, a.nk, sbin);
   }
   emit(outcome == TL_HIT, oi, oj, a.hits, a.hit_cap, &a.ctr->hits, &a.ctr->status,
        TL_ST_HIT_OVF, lane);
@@ -402,7 +410,8 @@ __device__ __forceinline__ void decide_pending(const TravArgs &a, const WarpSmem
 // so that the long path runs on full warps.
 template <bool FP64>
 __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, int nq, int lane,
-                                             unsigned long long &tests, int &npend) {
+                                             unsigned long long &tests, int &npend,
+                                             const float *sbin) {
   const unsigned lt = (1u << lane) - 1u;
   for (int e0 = 0; e0 < nq; e0 += 32) {
     const int m = min(32, nq - e0);
@@ -448,7 +457,7 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
           outcome = tl_exact_hit(a.mA, oi, a.mB, oj, a.ct, a.dt, a.kappa) ? TL_HIT : TL_MISS;
         } else {
           const float4 pa = __ldg(a.A.pos + si), pb = __ldg(a.B.pos + sj);
-          undecided = !tl_narrow32_quick_miss(pa, da, pb, db, a.nk);
+          undecided = !tl_narrow32_quick_miss(pa, da, pb, db, a.nk, sbin);
         }
       }
       if (FP64) {
@@ -460,7 +469,7 @@ __device__ __forceinline__ void flush_leaves(const TravArgs &a, WarpSmem &ws, in
         npend += __popc(mu);
         __syncwarp();
         if (npend >= 32) {
-          decide_pending(a, ws, 32, lane);
+          decide_pending(a, ws, 32, lane, sbin);
           // the rest (fewer than 32) move to the front
           const int rest = npend - 32;
           uint2 v = make_uint2(0u, 0u);
@@ -539,6 +548,12 @@ __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_t
   WarpSmem &ws = reinterpret_cast<WarpSmem *>(
       smem_raw + sizeof(uint2) * (size_t)D * (blockDim.x >> 5))[warp];
   TLCounters *ctr = a.ctr;
+  // After a queue overflow or an expired wait in this step (an earlier part)
+  // or this run, the queue may hold chunks that no warp will take: a warp
+  // taking one would count an item the counters never handed on, and the
+  // step's end would no longer be seen.  The host repeats the step (or run)
+  // with the queue reset, so nothing more is traversed here.
+  if (*(volatile unsigned *)&ctr->status & (TL_ST_SPILL_OVF | TL_ST_TIMEOUT)) return;
   const uint2 *src0;
   unsigned long long n0;
   if (from_frontier) {
@@ -816,8 +831,11 @@ __global__ void __launch_bounds__(TL_TRAV_MAX_WARPS * 32, TL_TRAV_MINBLOCKS) k_t
 template <bool FP64>
 __global__ void __launch_bounds__(256) k_narrow(TravArgs a) {
   __shared__ WarpSmem wsm[8];
+  __shared__ float sbin[TL_SBINS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpSmem &ws = wsm[warp];
+  for (int i = threadIdx.x; i < TL_SBINS; i += blockDim.x) sbin[i] = a.nk.sbin[i];
+  __syncthreads();
   const unsigned long long listed = a.ctr->leaf_pairs - a.ctr->leaf_base;  // this part's
   const unsigned long long n = min(listed, a.leaf_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&a.ctr->max_part_leaves, listed);
@@ -829,9 +847,9 @@ __global__ void __launch_bounds__(256) k_narrow(TravArgs a) {
     const int m = (int)min(32ull, n - base);
     if (lane < m) ws.leafq[lane] = a.leaves[base + lane];
     __syncwarp();
-    flush_leaves<FP64>(a, ws, m, lane, tests, npend);
+    flush_leaves<FP64>(a, ws, m, lane, tests, npend, sbin);
   }
-  if (!FP64 && npend > 0) decide_pending(a, ws, npend, lane);
+  if (!FP64 && npend > 0) decide_pending(a, ws, npend, lane, sbin);
   if (lane == 0 && tests) atomicAdd(&a.ctr->narrow_tests, tests);
 }
 
@@ -932,8 +950,9 @@ size_t traverse_smem(int warps, int depth) {
 }
 
 cudaError_t launch_step_init(TLCounters *ctr, uint2 *F0, uint32_t sa, uint32_t sb, int nonempty,
-                             const unsigned *build_status, cudaStream_t s) {
-  k_step_init<<<1, 128, 0, s>>>(ctr, F0, sa, sb, nonempty, build_status);
+                             const unsigned *build_status, const unsigned *run_status,
+                             cudaStream_t s) {
+  k_step_init<<<1, 128, 0, s>>>(ctr, F0, sa, sb, nonempty, build_status, run_status);
   return cudaGetLastError();
 }
 
