@@ -158,41 +158,31 @@ __device__ __forceinline__ void block_sum(double &s, unsigned long long &c, doub
   }
 }
 
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
-               : "memory");
-  return old;
-}
-__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid-wide barrier of the cooperative launch.  Thread 0 of each block
-// arrives on a counter (release-acquire); the last one resets it and advances
-// the generation the others wait on (release; the waiters acquire).  The wait
-// is bounded: on a timeout (or when another block already gave up) the block
-// sets kFlagBarrier, marks the slots dirty and the call returns false, after
-// which the block leaves the kernel; the others then give up at their next
-// barrier.
+// Grid-wide barrier of the cooperative launch.  Every thread makes its writes
+// visible at device scope (a fence) before the block arrives; thread 0 then
+// arrives on a counter, the last one to arrive resets it and advances the
+// generation the others wait on, and every waiter fences again after it sees
+// the new generation.  The wait is bounded: on a timeout (or when another
+// block already gave up) the block sets kFlagBarrier, marks the slots dirty
+// and the call returns false, after which the block leaves the kernel; the
+// others then give up at their next barrier.
 __device__ bool grid_sync(const DepArgs &g) {
   __shared__ int ok_s;
+  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
     DepCtl *ctl = g.ctl;
-    const unsigned g0 = ld_acquire(&ctl->gen);
-    if (atom_add_acq_rel(&ctl->arrive, 1u) == gridDim.x - 1) {
-      *(volatile unsigned *)&ctl->arrive = 0;
-      red_add_release(&ctl->gen, 1u);
+    volatile unsigned *gen = &ctl->gen;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1) {
+      atomicExch(&ctl->arrive, 0u);
+      __threadfence();
+      atomicAdd(&ctl->gen, 1u);
     } else {
       long long it = 0;
-      while (ld_acquire(&ctl->gen) == g0) {
+      while (*gen == g0) {
         if ((*(volatile int *)&ctl->flag & kFlagBarrier) || ++it > g.spin) {
           atomicOr(&ctl->flag, kFlagBarrier);
           atomicExch(g.dirty, 1);
@@ -202,6 +192,7 @@ __device__ bool grid_sync(const DepArgs &g) {
         __nanosleep(64);
       }
     }
+    __threadfence();
     ok_s = ok;
   }
   __syncthreads();
@@ -237,7 +228,8 @@ __global__ void k_dep_pack(TLBeam A, TLBeam B, DepPhoton *pa, DepPhoton *pb) {
 // block's own barrier once block 0 runs the tail alone.
 template <bool kBlock>
 __device__ __forceinline__ bool phase_sync(const DepArgs &g) {
-  if (kBlock) {
+  if (kBlock) {  // reads go through L2 (__ldcg): the block's writes first reach it
+    __threadfence();
     __syncthreads();
     return true;
   }
@@ -262,8 +254,10 @@ __device__ int run_rounds(const DepArgs &g, long long &nr, const unsigned *&cur,
     int *tie = b ? &ctl->tie[1] : &ctl->tie[0];
     // the list written this round goes to list[nb]; its count held the list
     // of round r - 1, which every thread has finished reading; the same holds
-    // for the other parity's tie flag
-    if (tid0 == 0) {
+    // for the other parity's tie flag.  Round 0's are zero from the launch's
+    // start: a reset here would race with R3's appends when R2 is skipped (no
+    // barrier between them), so only later rounds reset, before R1's barrier.
+    if (tid0 == 0 && r > 0) {
       *cntn = 0;
       *(b ? &ctl->tie[0] : &ctl->tie[1]) = 0;
     }
@@ -287,7 +281,7 @@ __device__ int run_rounds(const DepArgs &g, long long &nr, const unsigned *&cur,
     // R2
     for (long long i = tid0; ties && i < nr; i += stride) {
       const unsigned e = cur ? __ldcg(cur + i) : (unsigned)i;
-      if (g.state[e] != kOpen) continue;
+      if (__ldcg(g.state + e) != kOpen) continue;
       const uint2 h = g.hits[e];
       const unsigned long long k = __ldcg(g.key + e);
       if (__ldcg(&g.sA[h.x].t[b]) == k) atomicMin(&g.sA[h.x].p[b], h.y);
@@ -301,7 +295,7 @@ __device__ int run_rounds(const DepArgs &g, long long &nr, const unsigned *&cur,
       unsigned e = 0;
       if (i < nr) {
         e = cur ? __ldcg(cur + i) : (unsigned)i;
-        if (g.state[e] == kOpen) {
+        if (__ldcg(g.state + e) == kOpen) {
           const uint2 h = g.hits[e];
           const unsigned long long k = __ldcg(g.key + e);
           DepSlot *qa = g.sA + h.x, *qb = g.sB + h.y;
