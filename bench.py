@@ -96,16 +96,20 @@ def src_hash() -> str:
 
 
 def read_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    sources have not changed since it was taken."""
+    """(DRAM bytes per launch, the time steps the launches were) from the
+    committed ncu summary, if the kernel sources have not changed since it was
+    taken; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     cur = src_hash()
     for line in open(p):
+        if line.startswith("#"):
+            continue
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("phase") == kernel and f.get("src") == cur and "bytes_per_launch" in f:
-            return float(f["bytes_per_launch"])
+            lo, hi = (int(x) for x in f.get("steps", "0-0").split("-"))
+            return float(f["bytes_per_launch"]), list(range(lo, hi + 1))
     return None
 
 
@@ -729,8 +733,22 @@ def run_ours(args, wl):
         "frac": busy_ops / (tn / 1e3) / FP32_OPS_PEAK if tn > 0 else None,
         "per_step_ms": [round(r["narrow"], 4) for r in busy],
         "narrow_tests": [r["tests"] for r in busy]}
+    # DRAM traffic of the traversal, captured on busy steps (profiles/traffic.txt):
+    # compared with the algorithmic bytes of the same steps; the run-average
+    # roofline above has no traffic of its own
+    tr = read_traffic("traverse")
+    if tr is not None:
+        cap = [r for r in per_step if r["step"] in tr[1]]
+        algo = (sum(64.0 * n_ab + 8.0 * r["leaves"] for r in cap) / len(cap)) if cap else None
+        roofs["traverse"]["busy_steps"]["traffic"] = {
+            "steps": tr[1], "dram_bytes_per_launch": tr[0],
+            "algorithmic_bytes_per_launch": algo,
+            "dram_over_algorithmic": tr[0] / algo if algo else None}
     roofline = dict(roofs[dom])
-    roofline["traffic"] = read_traffic(dom)
+    roofline["traffic"] = None
+    roofline["traffic_note"] = ("DRAM bytes were captured on busy steps only "
+                                "(rooflines.traverse.busy_steps.traffic)"
+                                if dom == "traverse" else "not captured for this kernel")
     cpu = (cpu_baseline(wl, a_np, b_np, first, nsteps)
            if (world == 1 and not args.no_cpu_baseline) else None)
     line = {
