@@ -96,9 +96,10 @@ def src_hash() -> str:
 
 
 def read_traffic(kernel: str):
-    """(DRAM bytes per launch, the time steps the launches were) from the
-    committed ncu summary, if the kernel sources have not changed since it was
-    taken; else None."""
+    """The fields of the committed ncu summary's line for `kernel` (DRAM bytes
+    per launch, and what the capture was: time steps, knobs, the algorithmic
+    bytes of the same launches), if the kernel sources have not changed since it
+    was taken; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
@@ -108,8 +109,7 @@ def read_traffic(kernel: str):
             continue
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("phase") == kernel and f.get("src") == cur and "bytes_per_launch" in f:
-            lo, hi = (int(x) for x in f.get("steps", "0-0").split("-"))
-            return float(f["bytes_per_launch"]), list(range(lo, hi + 1))
+            return f
     return None
 
 
@@ -733,22 +733,23 @@ def run_ours(args, wl):
         "frac": busy_ops / (tn / 1e3) / FP32_OPS_PEAK if tn > 0 else None,
         "per_step_ms": [round(r["narrow"], 4) for r in busy],
         "narrow_tests": [r["tests"] for r in busy]}
-    # DRAM traffic of the traversal, captured on busy steps (profiles/traffic.txt):
-    # compared with the algorithmic bytes of the same steps; the run-average
-    # roofline above has no traffic of its own
+    # DRAM traffic from profiles/traffic.txt: the traversal's on busy steps (with
+    # the capture's own algorithmic bytes: the leaf-pair count depends on the
+    # knobs), the build kernels' per launch like their rooflines
     tr = read_traffic("traverse")
     if tr is not None:
-        cap = [r for r in per_step if r["step"] in tr[1]]
-        algo = (sum(64.0 * n_ab + 8.0 * r["leaves"] for r in cap) / len(cap)) if cap else None
+        dram, algo = float(tr["bytes_per_launch"]), float(tr["algorithmic_bytes_per_launch"])
         roofs["traverse"]["busy_steps"]["traffic"] = {
-            "steps": tr[1], "dram_bytes_per_launch": tr[0],
-            "algorithmic_bytes_per_launch": algo,
-            "dram_over_algorithmic": tr[0] / algo if algo else None}
+            "steps": tr["steps"], "knobs": tr["knobs"], "dram_bytes_per_launch": dram,
+            "algorithmic_bytes_per_launch": algo, "dram_over_algorithmic": dram / algo}
     roofline = dict(roofs[dom])
-    roofline["traffic"] = None
-    roofline["traffic_note"] = ("DRAM bytes were captured on busy steps only "
-                                "(rooflines.traverse.busy_steps.traffic)"
-                                if dom == "traverse" else "not captured for this kernel")
+    td = read_traffic(dom) if dom != "traverse" else None
+    roofline["traffic"] = float(td["bytes_per_launch"]) if td is not None else None
+    roofline["traffic_note"] = (
+        "DRAM bytes were captured on busy steps only (rooflines.traverse.busy_steps.traffic)"
+        if dom == "traverse" else
+        ("dram__bytes_read.sum + dram__bytes_write.sum per launch, profiles/traffic.txt"
+         if td is not None else "not captured for this kernel"))
     cpu = (cpu_baseline(wl, a_np, b_np, first, nsteps)
            if (world == 1 and not args.no_cpu_baseline) else None)
     line = {

@@ -109,6 +109,17 @@ int trilens_debug_band_stress(uint64_t seed, int64_t n_pairs, double dt_fs, doub
                               unsigned long long *counts, double *sample, int64_t n_sample,
                               trilens_stream_t stream);
 
+/* The FP32 narrow phase's sure-miss radii per bin of the invariant s (host
+ * only, no GPU): bin 0 holds s < 1; bin 1 + 8 e + k holds s in
+ * [2^e (1 + k/8), 2^e (1 + (k+1)/8)) for e = 0..23, the last bin also every
+ * larger s.  out (host, n >= TRILENS_NARROW_BINS floats) receives for each bin
+ * an upper bound [um^2] on r^2 = 1e12 kappa sigma(s) / pi (Eq. BWcross) over
+ * the bin, as the narrow phase of a context with these dt_fs and kappa uses
+ * it; *r2max (host, may be NULL) the bound over every s.  Returns the number of
+ * bins, or INVALID for non-positive dt_fs or kappa, a NULL out or n too small. */
+#define TRILENS_NARROW_BINS 193
+int trilens_debug_narrow_bins(double dt_fs, double kappa, float *out, int32_t n, float *r2max);
+
 #ifdef __cplusplus
 }
 #endif

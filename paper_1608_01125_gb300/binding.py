@@ -131,6 +131,9 @@ def lib() -> ctypes.CDLL:
         L.trilens_debug_band_stress.argtypes = [ctypes.c_uint64, i64, ctypes.c_double,
                                                 ctypes.c_double, vp, vp, i64, vp]
         L.trilens_debug_band_stress.restype = ctypes.c_int
+        L.trilens_debug_narrow_bins.argtypes = [ctypes.c_double, ctypes.c_double, vp, i32,
+                                                ctypes.POINTER(ctypes.c_float)]
+        L.trilens_debug_narrow_bins.restype = ctypes.c_int
         L.trilens_debug_timing.argtypes = [vp, ctypes.c_int]
         L.trilens_debug_timing.restype = ctypes.c_int
         L.trilens_debug_phase_ms.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), ctypes.c_int]
@@ -714,6 +717,23 @@ def mlp_forward(params, norm, x, stream=None):
     _check(lib().trilens_mlp_forward(_ptr(params), _ptr(norm), _ptr(x), x.shape[0], _ptr(out),
                                      ctypes.c_void_p(st.cuda_stream)))
     return out
+
+
+#: bins of s of the narrow phase's sure-miss radii (trilens_debug_narrow_bins)
+NARROW_BINS = 193
+
+
+def narrow_bins(dt_fs: float, kappa: float):
+    """(upper bounds of r^2 per bin of s [um^2], as float32, and the bound over every
+    s): the table the FP32 narrow phase's quick miss uses (host only)."""
+    out = np.zeros(NARROW_BINS, dtype=np.float32)
+    r2max = ctypes.c_float(0.0)
+    rc = lib().trilens_debug_narrow_bins(float(dt_fs), float(kappa),
+                                         ctypes.c_void_p(out.ctypes.data), NARROW_BINS,
+                                         ctypes.byref(r2max))
+    if rc != NARROW_BINS:
+        raise TrilensError(rc, status_str(rc))
+    return out, float(r2max.value)
 
 
 def deplete_record(out) -> dict:

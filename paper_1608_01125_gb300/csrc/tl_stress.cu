@@ -175,3 +175,14 @@ extern "C" int trilens_debug_band_stress(uint64_t seed, int64_t n_pairs, double 
   }
   return TRILENS_OK;
 }
+
+static_assert(TRILENS_NARROW_BINS == TL_SBINS, "the bin count of the ABI and of the kernels");
+
+extern "C" int trilens_debug_narrow_bins(double dt_fs, double kappa, float *out, int32_t n,
+                                         float *r2max) {
+  if (!(dt_fs > 0.0) || !(kappa > 0.0) || !out || n < TL_SBINS) return TRILENS_ERR_INVALID;
+  const TLNarrowConst nk = tl_narrow_const(dt_fs, kappa);
+  for (int i = 0; i < TL_SBINS; ++i) out[i] = nk.sbin[i];
+  if (r2max) *r2max = nk.r2max;
+  return TL_SBINS;
+}
