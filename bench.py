@@ -57,8 +57,8 @@ def algorithmic_bytes(phase: str, na: int, nb: int, key_bits: tuple, hits: float
     """Bytes one launch of a phase must move at least (per beam launches use
     that beam's size; traversal and later phases cover both beams)."""
     n = na + nb
-    if phase == "propagate":   # 7 doubles in; float4 x2 + key + index out
-        return 56 + 32 + 12, "photon"
+    if phase == "propagate":   # p0, d (6 doubles) and the FP32 direction in; x, y, z + key + index out
+        return 48 + 16 + 12 + 12, "photon"
     if phase == "sort":        # per pass: key + index read and written
         return 24, "photon-pass"
     if phase == "gather":      # index, random float4 x2 read, float4 x2 written

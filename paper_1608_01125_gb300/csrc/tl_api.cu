@@ -374,6 +374,8 @@ int trilens_create(trilens_ctx **out, const trilens_beam *a, const trilens_beam 
       return rc;
     }
     c->w[k].build_status = c->build_status;
+    // the step-invariant FP32 direction, index and energy, once
+    CK(tl::launch_static_soa(c->beam[k], c->w[k], c->stream));
     int64_t n = std::max<int64_t>(c->beam[k].n, 2);
     int lg = 0;
     while ((1ll << lg) < n) ++lg;

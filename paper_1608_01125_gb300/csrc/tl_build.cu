@@ -210,6 +210,27 @@ __device__ __forceinline__ unsigned quant(float c, float lo, float scale, unsign
   return (unsigned)f;
 }
 
+// The step-invariant part of the unsorted FP32 SoA, written once per context:
+// the direction rounded to FP32 with the photon's index in w (dir_u), and the
+// energy in FP32 (pos_u's w; the propagation rewrites only x, y, z).  GB300's
+// FP64 pipe is narrow, and these conversions were half of the propagation's
+// FP64 instructions.
+__global__ void __launch_bounds__(256) k_static_soa(TLBeam b, float4 *pos_u, float4 *dir_u) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    dir_u[i] = make_float4(__double2float_rn(b.dx[i]), __double2float_rn(b.dy[i]),
+                           __double2float_rn(b.dz[i]), __int_as_float((int)i));
+    pos_u[i] = make_float4(0.0f, 0.0f, 0.0f, __double2float_rn(b.E[i]));
+  }
+}
+
+cudaError_t launch_static_soa(const TLBeam &b, BuildBufs &w, cudaStream_t s) {
+  if (b.n <= 0) return cudaSuccess;
+  const int64_t nb = (b.n + 255) / 256;
+  k_static_soa<<<(unsigned)(nb < 8 * 152 ? nb : 8 * 152), 256, 0, s>>>(b, w.pos_u, w.dir_u);
+  return cudaGetLastError();
+}
+
 // Propagate p = p0 + c t_k d in FP64 (closed form), round to the FP32 SoA,
 // and key every photon by the Morton code of its swept box's centre in the
 // box (lo, scale) -- with several instances, its instance's box, and the
@@ -245,12 +266,12 @@ __global__ void __launch_bounds__(256) k_propagate(TLBeam b, double ct, float ha
     const double Px = __dadd_rn(b.px[i], __dmul_rn(ct, dx));
     const double Py = __dadd_rn(b.py[i], __dmul_rn(ct, dy));
     const double Pz = __dadd_rn(b.pz[i], __dmul_rn(ct, dz));
-    const float4 p = make_float4(__double2float_rn(Px), __double2float_rn(Py),
-                                 __double2float_rn(Pz), __double2float_rn(b.E[i]));
-    const float4 d = make_float4(__double2float_rn(dx), __double2float_rn(dy),
-                                 __double2float_rn(dz), __int_as_float((int)i));
-    pos_u[i] = p;
-    dir_u[i] = d;
+    const float3 p = make_float3(__double2float_rn(Px), __double2float_rn(Py),
+                                 __double2float_rn(Pz));
+    const float4 d = dir_u[i];  // the FP32 direction, written once (k_static_soa)
+    float *pu = reinterpret_cast<float *>(pos_u + i);  // x, y, z; w holds the energy
+    *reinterpret_cast<float2 *>(pu) = make_float2(p.x, p.y);
+    pu[2] = p.z;
     const unsigned qx = quant(fmaf(halfL, d.x, p.x), l3.x, s3.x, maxq),
                    qy = quant(fmaf(halfL, d.y, p.y), l3.y, s3.y, maxq),
                    qz = quant(fmaf(halfL, d.z, p.z), l3.z, s3.z, maxq);

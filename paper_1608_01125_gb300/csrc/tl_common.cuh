@@ -232,6 +232,7 @@ struct TravArgs {
 cudaError_t launch_propagate(const TLBeam &b, double ct, float L, const float box_lo[3],
                              const float box_scale[3], int bits, BuildBufs &w,
                              const float4 *inst_box, int passes, cudaStream_t s);
+cudaError_t launch_static_soa(const TLBeam &b, BuildBufs &w, cudaStream_t s);
 cudaError_t launch_beam_moments(const TLBeam &b, double *out15, double *scratch, cudaStream_t s);
 cudaError_t sort_prepare();
 cudaError_t launch_sort(BuildBufs &w, int64_t n, int key_bits, long long spin_limit,

@@ -22,6 +22,7 @@ namespace tl {
 
 constexpr int kIn = 24, kInP = 32, kH = 128, kOutP = 16;
 // flat FP32 parameter vector: W1 (128x24), b1, W2 (128x128), b2, W3, b3, W4 (2x128), b4
+constexpr int64_t kWgChunk = 512;  // batch rows per weight-gradient block
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * kIn, kOffW2 = kOffB1 + kH,
               kOffB2 = kOffW2 + kH * kH, kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kH,
               kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + 2 * kH, kParams = kOffB4 + 2;
@@ -375,8 +376,10 @@ __global__ void __launch_bounds__(128, 1)
 // of rows, 128 at a time: it stages A = G^T (one output per tile row) and
 // B = H^T (one input per tile row) as K-major core tiles, and one thread
 // issues the MMAs into an FP32 accumulator in tensor memory that stays there
-// for all of the block's rows; the block then adds its partial dW to the
-// gradient (FP32 atomics).  H is what the forward products consumed: the
+// for all of the block's rows; the block then writes its partial dW to its
+// own slice of a partials buffer, and k_mlp_wsum adds the slices in block
+// order, so the gradient (and training) is reproducible bit for bit.  H is
+// what the forward products consumed: the
 // BF16 normalised features (layer 1) or BF16 GELU(Z) (layers 2-4).  The bias
 // gradient db[o] = sum_r G[r][o] is summed from the staged tile.  Layer 4 has
 // 2 outputs, too few for a 128-row tile, so its product runs transposed:
@@ -401,6 +404,8 @@ __global__ void __launch_bounds__(128, 1)
   extern __shared__ unsigned char smem_raw[];
   WgSmem &S = *align1k<WgSmem>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5;
+  dW += (size_t)blockIdx.x * kParams;  // this block's slice of the partials
+  db += (size_t)blockIdx.x * kParams;
   const int64_t r0 = blockIdx.x * chunk, r1 = min(M, r0 + chunk);
   if (tid == 0) {
     S.err = 0;
@@ -467,9 +472,8 @@ __global__ void __launch_bounds__(128, 1)
     uint32_t r[16];
     TL_TMEM_LD_X16(trow, r);
     tmem_wait_ld();
-    if (r1 > r0)
-      for (int o = 0; o < 2; ++o) atomicAdd(&dW[o * kH + tid], __uint_as_float(r[o]));
-    if (tid < 2 && r1 > r0) atomicAdd(&db[tid], bacc);
+    for (int o = 0; o < 2; ++o) dW[o * kH + tid] = __uint_as_float(r[o]);
+    if (tid < 2) db[tid] = bacc;
   } else {
     constexpr int I = MODE == 0 ? kIn : kH;
 #pragma unroll 1
@@ -477,17 +481,26 @@ __global__ void __launch_bounds__(128, 1)
       uint32_t r[32];
       TL_TMEM_LD_X32(trow + (uint32_t)c, r);
       tmem_wait_ld();
-      if (r1 > r0)
-        for (int j = 0; j < 32; ++j)
-          if (c + j < I) atomicAdd(&dW[tid * I + c + j], __uint_as_float(r[j]));
+      for (int j = 0; j < 32; ++j)
+        if (c + j < I) dW[tid * I + c + j] = __uint_as_float(r[j]);
     }
-    if (r1 > r0) atomicAdd(&db[tid], bacc);
+    db[tid] = bacc;
   }
   if (!ok) S.err = 1;
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 128);
   if (tid == 0 && S.err) atomicOr(err, 1);
+}
+
+// grad[p] = sum over the blocks b (in order) of part[b * kParams + p]: every
+// block writes every parameter's entry of its slice
+__global__ void __launch_bounds__(256) k_mlp_wsum(const float *part, int blocks, float *grad) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= kParams) return;
+  float acc = 0.0f;
+  for (int b = 0; b < blocks; ++b) acc += part[(size_t)b * kParams + p];
+  grad[p] = acc;
 }
 
 // ---------------------------------------------------------------- optimiser
@@ -577,10 +590,12 @@ cudaError_t mlp_grad(const float *prm, const float *norm, const MLPWork &w, cons
                                                st, st_scale);
   k_mlp_dgrad<<<g, 128, mlp_bwd_smem(), s>>>(P, w.dout, w.Z[0], w.Z[1], w.Z[2], w.dZ[0], w.dZ[1],
                                              w.dZ[2], M, w.err, spin);
-  // weight gradients on the tensor cores: blocks of 512 batch rows
-  const int64_t chunk = 512;
+  // weight gradients on the tensor cores: blocks of kWgChunk batch rows, each
+  // into its own slice of w.wpart, then summed in block order
+  if (M > w.cap) return cudaErrorInvalidValue;
+  const int64_t chunk = kWgChunk;
   const unsigned gz = (unsigned)((M + chunk - 1) / chunk);
-  float *G = w.grad;
+  float *G = w.wpart;
   const size_t sm = mlp_wg_smem();
   k_mlp_wgrad_tc<2><<<gz, 128, sm, s>>>(nullptr, w.dout, w.Z[2], nullptr, norm, M, chunk,
                                          G + kOffW4, G + kOffB4, w.err, spin);
@@ -590,6 +605,7 @@ cudaError_t mlp_grad(const float *prm, const float *norm, const MLPWork &w, cons
                                          G + kOffW2, G + kOffB2, w.err, spin);
   k_mlp_wgrad_tc<0><<<gz, 128, sm, s>>>(w.dZ[0], nullptr, nullptr, x, norm, M, chunk,
                                          G + kOffW1, G + kOffB1, w.err, spin);
+  k_mlp_wsum<<<(kParams + 255) / 256, 256, 0, s>>>(w.wpart, (int)gz, w.grad);
   return cudaGetLastError();
 }
 
@@ -620,6 +636,8 @@ cudaError_t mlp_work_alloc(MLPWork &w, int64_t rows) {
       if ((e = cudaMalloc((void **)&w.dZ[l], sizeof(__nv_bfloat16) * kH * rows))) return e;
     }
     if ((e = cudaMalloc((void **)&w.dout, sizeof(float) * 2 * rows))) return e;
+    const int64_t blocks = (rows + kWgChunk - 1) / kWgChunk;
+    if ((e = cudaMalloc((void **)&w.wpart, sizeof(float) * kParams * (size_t)blocks))) return e;
   }
   return cudaSuccess;
 }
@@ -637,6 +655,7 @@ void mlp_work_free(MLPWork &w) {
     cudaFree(w.dZ[l]);
   }
   cudaFree(w.dout);
+  cudaFree(w.wpart);
   memset(&w, 0, sizeof(w));
 }
 

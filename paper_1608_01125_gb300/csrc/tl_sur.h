@@ -38,6 +38,7 @@ struct MLPWork {
   __nv_bfloat16 *W1, *W2, *W3, *W4;
   __nv_bfloat16 *Z[3], *dZ[3];
   float *dout;
+  float *wpart;  // per-block partial weight gradients (rows / 512 slices of all parameters)
   float *grad;
   float *loss;
   int *err;

@@ -114,3 +114,14 @@ def test_surrogate_objective_gradients_match_fp64_reference():
     gref = mlp.backward(p, cache, mlp.loss_mean_grad(out, lab, B))
     assert abs(float(loss.item()) / m - L) <= 0.03 * abs(L) + 1e-3
     _check_grads(binding.mlp_unflatten(g.cpu().numpy().astype(np.float64)), gref)
+
+
+def test_gradients_are_reproducible_bit_for_bit():
+    """The weight gradients are summed over the batch in a fixed order (per-block
+    slices added in block order, no atomics), so two calls on the same inputs
+    give the same bits, and so does training."""
+    m = 5077
+    p, x, y, P, N, X, Y = _setup(m, 9)
+    g1, l1 = binding.mlp_grad(P, N, X, Y)
+    g2, l2 = binding.mlp_grad(P, N, X, Y)
+    assert np.array_equal(g1.cpu().numpy(), g2.cpu().numpy())
