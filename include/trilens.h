@@ -188,7 +188,7 @@ int trilens_pair_products(const trilens_beam *a, const trilens_beam *b, const ui
  * Runs on the context's stream as one cooperative launch (every round inside
  * it, the open hits compacted after each round; a step needs as many rounds
  * as its longest chain of hits that wait on one another) and returns when the
- * step is done, after one 48-byte read-back.  Allocates its workspace on the
+ * step is done, after one 32-byte read-back.  Allocates its workspace on the
  * first call (96 bytes per photon of both beams, 25 per hit, growing with
  * n_hits).  TIMEOUT (rem_a, rem_b and delta then unspecified; the photon
  * slots are cleared on the device by the next call) if a grid-wide barrier
